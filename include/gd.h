@@ -1,0 +1,237 @@
+/*
+ * gd.h -- C ABI of the GB300 (sm_103a) gradient-enhanced damage library.
+ *
+ * The library computes the monolithic Newton iteration of the gradient-enhanced
+ * damage model with input-convex neural network (ICNN) constitutive laws of
+ * arxiv 2604.03411 (Wilkinson, Amiri-Hezaveh, Buganza Tepole): per quadrature
+ * point the deformation gradient, C - I without cancellation, the invariants,
+ * the ICNN strain energy with first and second derivatives, the ICNN yield
+ * function with the local damage/history update, the degraded stress and the
+ * non-local fluxes; per element the coupled residual and consistent tangent,
+ * scattered into a CSR matrix through a precomputed slot map; and the global
+ * Newton iteration with a Jacobi-preconditioned Krylov solver on the device.
+ *
+ * Conventions
+ *  - Every call returns gd_status; after a non-OK status gd_last_error() gives a
+ *    message and the handle stays usable at its last committed load step.
+ *  - Unless stated otherwise, array arguments of gd_create/gd_set_state/
+ *    gd_get_fields are HOST pointers, copied during the call (the caller keeps
+ *    ownership).  Arguments documented as "device" are borrowed for the duration
+ *    of the call only and must be resident on the handle's device.
+ *  - All device work is issued on gd_options.cuda_stream (NULL: the legacy
+ *    default stream).  Calls that return results to host memory synchronise
+ *    that stream.
+ *  - One handle must not be used from two host threads at once.
+ *  - Sizes: nnz of the global matrix must stay below 2^31 (int32 column
+ *    indices and slot map); larger meshes are rejected with GD_ERR_ARG.
+ *
+ * Degrees of freedom are node-major: dof (node n, component c) has index
+ * n * ndof + c, ndof = dim + 1, components 0..dim-1 are the displacement and
+ * component dim is the non-local damage phi (Sec. 3.1, Table kernel_inputs).
+ */
+#ifndef GD_H
+#define GD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gd_status {
+    GD_OK = 0,
+    GD_ERR_ARG = 1,            /* invalid argument or size                          */
+    GD_ERR_MESH = 2,           /* bad connectivity, node id, or Jacobian <= 0       */
+    GD_ERR_CUDA = 3,           /* a CUDA runtime call failed                        */
+    GD_ERR_OOM = 4,            /* device allocation failed                          */
+    GD_ERR_NOT_CONVERGED = 5,  /* Newton did not converge after all step cuts       */
+    GD_ERR_NAN = 6,            /* non-finite residual                               */
+    GD_ERR_KRYLOV = 7,         /* Krylov breakdown or iteration cap                 */
+    GD_ERR_LOCAL_SOLVE = 8,    /* local kappa update hit its iteration cap          */
+    GD_ERR_TIMEOUT = 9,        /* a bounded device wait gave up                     */
+    GD_ERR_STATE = 10          /* call not valid in the handle's current state      */
+} gd_status;
+
+enum { GD_ENERGY_ICNN_RAW = 0,   /* psi-ICNN of (I1-3, I2-3, J-1)                          */
+       GD_ENERGY_ICNN_ISO = 1,   /* psi-ICNN of (I1G-3, I2G-3, J-1), Eq. (dd_0)            */
+       GD_ENERGY_NEO_HOOKE = 2 };/* closed-form compressible Neo-Hookean, Sec. 4.1         */
+enum { GD_FP64 = 0, GD_MIXED = 1 };
+enum { GD_BICGSTAB = 0, GD_GMRES = 1 };
+enum { GD_ASM_RESIDUAL = 0, GD_ASM_TANGENT = 1 };
+
+/* Mesh and boundary data (Sec. 3.1, Table kernel_inputs; Dirichlet data of the
+ * incremental load, Sec. 3.2).
+ *   dim 2: plane-strain bilinear Q4, 2x2 Gauss, nodes counter-clockwise;
+ *   dim 3: trilinear HEX8, 2x2x2 Gauss, nodes (-,-,-) (+,-,-) (+,+,-) (-,+,-) then z = +.
+ * Quadrature points are ordered lexicographically, reference coordinate xi fastest.
+ * Prescribed dof (bc_node[i], bc_comp[i]) takes bc_scale[i] * load(t); bc_comp < dim
+ * (phi has the natural zero-flux condition on the whole boundary, Sec. 2.1).
+ * The reaction of a step is the sum of the internal force components react_comp
+ * over react_node, taken before the prescribed rows are eliminated. */
+typedef struct gd_mesh {
+    int32_t dim;
+    int64_t n_nodes, n_elems;
+    const double *coords;      /* [n_nodes * dim]  reference coordinates              */
+    const int32_t *conn;       /* [n_elems * nen]  nen = 4 (dim 2) or 8 (dim 3)       */
+    int64_t n_bc;
+    const int32_t *bc_node;    /* [n_bc] */
+    const int8_t *bc_comp;     /* [n_bc] */
+    const double *bc_scale;    /* [n_bc] */
+    int64_t n_react;
+    const int32_t *react_node; /* [n_react] */
+    int32_t react_comp;
+} gd_mesh;
+
+/* Two-layer softplus ICNN with input skips (Sec. 4.2, Eqs. (dd_0), (Gq_NN)).
+ * params packs W1[w][n_in] b1[w] W2[w][w] A2[w][n_in] b2[w] w3[w] a3[n_in]:
+ *   N(x) = w3 . sp(W2 sp(W1 x + b1) + A2 x + b2) + a3 . x,  sp = softplus.
+ * W1, W2, A2, w3, a3 must be >= 0 (convex, non-decreasing); biases are free.
+ * n_in = 3 for the energy network, 1 for the yield network.  width 0 for the
+ * yield network selects G(q) = q (the closed-form loading function of
+ * Eq. (ostwald_potential)); widths up to 64. */
+typedef struct gd_icnn {
+    int32_t n_in;
+    int32_t width;
+    const double *params;
+} gd_icnn;
+
+/* Constants of Sec. 4: f_d(kappa) = exp(-eta_d <kappa - kappa_d>_+) (Eq. (degradation_function)),
+ * gradient energy c_d/2 gradphi.C^-1.gradphi, penalty beta_d/2 (phi - kappa)^2,
+ * q = psi_e + gamma_d beta_d (phi - kappa) / (eta_d f_d(kappa)) (Eq. (ostwald_potential)).
+ * Energy psi_e = mu_e [N(x) - N(0) - n (J-1)] + lambda_e (J + 1/J - 2)^2 with n fixed
+ * by S(C = I) = 0; for GD_ENERGY_NEO_HOOKE mu_e, lambda_e are the Lame constants.
+ * eta_d must be > 0. */
+typedef struct gd_material {
+    double mu_e, lambda_e, eta_d, kappa_d, beta_d, c_d, gamma_d;
+    int32_t energy;
+} gd_material;
+
+/* Quasi-static incremental load (Sec. 3.2): step s prescribes bc_scale * load[s]. */
+typedef struct gd_load_path {
+    int32_t n_steps;
+    const double *load;        /* [n_steps] */
+} gd_load_path;
+
+typedef struct gd_options {
+    int32_t precision;         /* GD_FP64 or GD_MIXED                                  */
+    double newton_rtol;        /* ||R_free|| <= max(rtol max(||R0_free||, ||R_fixed||), atol) */
+    double newton_atol;
+    int32_t newton_max;        /* Newton iterations per step                           */
+    int32_t line_search_max;   /* backtracking halvings per Newton direction           */
+    int32_t krylov;            /* GD_BICGSTAB (GD_GMRES reserved)                      */
+    double krylov_rtol;        /* relative residual of each linear solve               */
+    int32_t krylov_max;
+    int32_t gmres_m;
+    int32_t local_max;         /* local kappa iterations (the paper caps at 100, Sec. 5.3) */
+    int32_t checkpoint_every;  /* adjoint checkpoint interval in load steps            */
+    int32_t max_step_cuts;     /* nested load-step halvings after a failed step        */
+    void *cuda_stream;         /* cudaStream_t or NULL                                 */
+} gd_options;
+
+typedef struct gd_newton_report {
+    int32_t converged;
+    int32_t iterations;        /* Newton directions taken                               */
+    int32_t krylov_iterations; /* summed over the step                                  */
+    int32_t line_search_cuts;
+    int32_t local_failures;
+    int32_t loading_points;    /* qps on the loading branch at convergence              */
+    int32_t step_cuts;
+    double residual0, residual, reaction, max_damage;
+} gd_newton_report;
+
+typedef struct gd_path_report {
+    int32_t steps_done;
+    int32_t total_newton;
+    int32_t total_krylov;
+    int32_t step_cuts;
+    int32_t assemblies;
+    double assembly_ms;        /* device time of the assembly kernels (CUDA events)     */
+    double krylov_ms;          /* device time of the linear solves                      */
+    double total_ms;
+} gd_path_report;
+
+typedef struct gd_handle gd_handle;
+
+/* Fills *opt with the defaults: FP64, newton_rtol 1e-10, newton_atol 1e-12,
+ * newton_max 25, line_search_max 12, BiCGStab with krylov_rtol 1e-12 and
+ * krylov_max 20000, local_max 100, checkpoint_every 5, max_step_cuts 4,
+ * default stream. */
+void gd_default_options(gd_options *opt);
+
+/* Creates a problem (Sec. 3.1 kernel inputs, Sec. 3.2 load path): copies and
+ * validates the mesh (node ids, positive Jacobians at every qp), builds the CSR
+ * pattern of the node graph with ndof x ndof blocks, the per-element slot map
+ * and the Dirichlet masks, stages the ICNN weights and their normalising
+ * constants N(0), n, N_k(0), 1/N_k'(0) on the device, and zeroes the state
+ * (u = 0, phi = 0, kappa = 0).  The handle owns all device memory.
+ * Errors: GD_ERR_ARG (null/size/width), GD_ERR_MESH, GD_ERR_OOM, GD_ERR_CUDA. */
+gd_status gd_create(const gd_mesh *mesh, const gd_icnn *psi, const gd_icnn *yield,
+                    const gd_material *mat, const gd_load_path *path, const gd_options *opt,
+                    gd_handle **out);
+
+/* Replaces the network weights (same widths) from host or device memory
+ * (cudaMemcpyDefault) and recomputes the normalising constants on the device. */
+gd_status gd_set_params(gd_handle *h, const double *theta_psi, const double *theta_yield);
+
+/* CSR pattern of the global matrix: n_rows = n_nodes * ndof rows; the block of
+ * node n has ndof consecutive rows with identical column lists (every dof of
+ * every neighbour node, neighbours ascending).  rowptr [n_rows + 1] and colidx
+ * [nnz] are host buffers (either may be NULL to query the sizes only). */
+gd_status gd_csr_pattern(gd_handle *h, int64_t *n_rows, int64_t *nnz, int32_t *rowptr, int32_t *colidx);
+
+/* Host-only helper (no GPU needed): validates the mesh exactly as gd_create
+ * does and returns the CSR pattern described at gd_csr_pattern plus the slot
+ * map that the assembly kernel scatters through: slot [n_elems * nen * nen],
+ * slot[(e*nen + a)*nen + b] = position in colidx/values of the entry (row dof 0
+ * of node conn[e][a], column dof 0 of node conn[e][b]); the entry of row dof i,
+ * column dof k is at slot + i * rowlen + k with rowlen = rowptr[r+1] - rowptr[r]
+ * of that node's first row r.  Any output may be NULL (query sizes first). */
+gd_status gd_build_pattern(const gd_mesh *mesh, int64_t *n_rows, int64_t *nnz, int32_t *rowptr, int32_t *colidx,
+                           int32_t *slot);
+
+/* One assembly pass (Sec. 3.1 residual, Sec. 3.2 monolithic tangent), every
+ * pointer on the device:
+ *   dofs        [n_nodes*ndof] FP64  current u and phi
+ *   kappa_n     [n_elems*nq]   FP64  committed history (NULL: the handle's)
+ *   R           [n_nodes*ndof] FP64  out: assembled residual (all dofs, no elimination)
+ *   csr_vals    [nnz] out: consistent tangent values (FP64 in GD_FP64 precision,
+ *               FP32 in GD_MIXED), NULL or mode GD_ASM_RESIDUAL to skip the tangent
+ *   kappa_trial [n_elems*nq]   FP64  out: kappa_{n+1} at every qp (may be NULL)
+ *   loading     [n_elems*nq]   int8  out: 1 where the qp is on the loading branch (may be NULL)
+ * Returns GD_ERR_LOCAL_SOLVE when a local solve hit local_max (outputs still written). */
+gd_status gd_assemble(gd_handle *h, const double *dofs, const double *kappa_n, double *R,
+                      void *csr_vals, double *kappa_trial, int8_t *loading, int32_t mode);
+
+/* Advances the next load step of the path to convergence (monolithic Newton,
+ * Sec. 3.2, with a line search and nested step halving on failure); commits
+ * kappa and the fields on success.  rep may be NULL. */
+gd_status gd_newton_step(gd_handle *h, gd_newton_report *rep);
+
+/* Runs every remaining step of the load path; reaction [n_steps] (host, may be
+ * NULL) receives the reaction of each step.  rep may be NULL. */
+gd_status gd_run_load_path(gd_handle *h, double *reaction, gd_path_report *rep);
+
+/* Gradient of a loss of the reaction curve with respect to the network weights
+ * through the whole load path (discrete adjoint with checkpoints every
+ * checkpoint_every steps and recomputation in between).
+ *   dL_dreaction [n_steps] host; dL_dtheta [n_psi + n_yield] host out. */
+gd_status gd_backward(gd_handle *h, const double *dL_dreaction, double *dL_dtheta);
+
+/* Copies the committed fields to host: dofs [n_nodes*ndof], kappa [n_elems*nq]
+ * (either may be NULL). */
+gd_status gd_get_fields(gd_handle *h, double *dofs, double *kappa);
+
+/* Overwrites the committed state from host arrays and sets the next step index. */
+gd_status gd_set_state(gd_handle *h, const double *dofs, const double *kappa, int32_t next_step);
+
+/* Message for the last non-OK status of this handle (or of gd_create when h is NULL). */
+const char *gd_last_error(const gd_handle *h);
+
+/* Frees every device and host resource of the handle (NULL is a no-op). */
+void gd_destroy(gd_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GD_H */

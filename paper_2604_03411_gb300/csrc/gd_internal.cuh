@@ -1,0 +1,147 @@
+// gd_internal.cuh -- internal declarations shared by the translation units of
+// the CUDA library (handle layout, kernel argument blocks, launchers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "gd.h"
+
+namespace gd {
+
+constexpr int kMaxWidth = 64;   // widest supported ICNN layer
+
+// Network constants computed on the device from the weights (Sec. 4.2):
+// psi: N(0) and the normalising coefficient n of -n (J - 1) that keeps
+// S(C = I) = 0; yield: N_k(0) and s = 1 / N_k'(0) so that G(0) = 0, G'(0) = 1.
+struct NetConst {
+    double psi_N0, psi_n, y_N0, y_s;
+};
+
+// One ICNN on the device: packed parameters (gd_icnn layout) plus a
+// transposed copy of the square layer W2 so that both the forward pass
+// (lane = output unit) and the reverse pass (lane = input unit) read
+// consecutive addresses.
+struct DevNet {
+    int n_in = 0, width = 0, n_params = 0;
+    double *p = nullptr;     // [n_params]
+    double *W2T = nullptr;   // [width * width], W2T[j * w + k] = W2[k * w + j]
+};
+
+struct MatConst {
+    double mu_e, lambda_e, eta_d, kappa_d, beta_d, c_d, gamma_d;
+    double qcoef;            // gamma_d * beta_d / eta_d (0 when gamma_d or beta_d is 0)
+    int energy;
+    int local_max;
+};
+
+struct AsmArgs {
+    int64_t n_elems;
+    const int32_t *conn;
+    const double *X;
+    const double *dofs;
+    const double *kappa_n;
+    double *R;               // may be null
+    double *vals;            // FP64 values (may be null)
+    float *vals32;           // FP32 values (mixed mode, may be null)
+    double *kappa_new;       // may be null
+    int8_t *loading;         // may be null
+    const int32_t *slot;     // [E * nen * nen] CSR position of (row node a dof 0, col node b dof 0)
+    const int32_t *rowptr;   // [n_dofs + 1]
+    DevNet psi, yld;
+    const NetConst *netc;
+    MatConst mat;
+    int tangent;
+    int *counters;           // [0] local-solve failures, [1] loading points
+};
+
+struct Handle {
+    // sizes
+    int dim = 0, nen = 0, nq = 0, ndof = 0;
+    int64_t n_nodes = 0, n_elems = 0, n_dofs = 0, nnz = 0;
+    // device mesh and pattern
+    double *X = nullptr;
+    int32_t *conn = nullptr;
+    int32_t *slot = nullptr;
+    int32_t *rowptr = nullptr;
+    int32_t *colidx = nullptr;
+    uint8_t *fixed = nullptr;        // [n_dofs] 1 = prescribed
+    int32_t *bc_dof = nullptr;
+    double *bc_scale = nullptr;
+    int64_t n_bc = 0;
+    int32_t *react_dof = nullptr;
+    int64_t n_react = 0;
+    // host copies of the pattern (for gd_csr_pattern)
+    std::vector<int32_t> h_rowptr, h_colidx;
+    // constitutive data
+    DevNet psi, yld;
+    NetConst *netc = nullptr;
+    MatConst mat{};
+    gd_options opt{};
+    cudaStream_t stream = nullptr;
+    std::vector<double> load;
+    // state
+    double *dofs = nullptr, *kappa = nullptr;            // committed
+    double *dofs_prev = nullptr;                         // state before the last committed step
+    double load_prev = 0.0, load_prevprev = 0.0;
+    bool have_prev = false;
+    int next_step = 0;
+    // work arrays
+    double *w_dofs = nullptr, *w_trial = nullptr;
+    double *R = nullptr, *R_trial = nullptr;
+    double *vals = nullptr, *vals_trial = nullptr;       // FP64 (or FP32 bit storage in mixed mode)
+    double *kappa_trial = nullptr, *kappa_trial2 = nullptr;
+    int8_t *loading = nullptr, *loading2 = nullptr;
+    int *counters = nullptr;                             // device [8]
+    // Krylov workspace (FP64 vectors of n_dofs)
+    double *kv[10] = {};
+    double *diag = nullptr;
+    double *red = nullptr;                               // device reduction buffers
+    double *scal = nullptr;                              // device scalars
+    int red_blocks = 0;
+    // timing
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double assembly_ms = 0.0, krylov_ms = 0.0;
+    int assemblies = 0;
+    std::string err;
+    int num_sms = 0;
+};
+
+// launchers (return the launch status)
+cudaError_t launch_prep_nets(const DevNet &psi, const DevNet &yld, int energy, NetConst *out, cudaStream_t s);
+cudaError_t launch_transpose(const DevNet &net, cudaStream_t s);
+cudaError_t launch_assemble_fp64(int dim, const AsmArgs &a, int num_sms, cudaStream_t s);
+
+// solver kernels (gd_solver.cu)
+struct SolverCtx {
+    int64_t n;                  // rows
+    int64_t n_nodes;
+    int ndof;
+    const int32_t *rowptr;
+    const int32_t *colidx;
+    const double *vals;
+    const uint8_t *fixed;
+    cudaStream_t stream;
+    double *red;                // [2 * blocks * 4]
+    double *scal;               // [64]
+    int blocks;
+};
+cudaError_t launch_jacobi_diag(const SolverCtx &c, double *diag);
+// Solves A x = b on the free dofs (A = vals with prescribed rows/cols removed);
+// x is overwritten; returns iterations (>= 0) or -1 on breakdown / cap.
+int bicgstab(const SolverCtx &c, const double *diag, const double *b, double *x, double *work[8],
+             double rtol, int max_it, double *final_rel);
+cudaError_t launch_norm2_free(const SolverCtx &c, const double *v, double *out_dev, double *out_fixed_dev);
+cudaError_t launch_axpy_free(const SolverCtx &c, double *y, const double *x, double alpha);
+cudaError_t launch_predictor(int64_t n, double *out, const double *cur, const double *prev, double factor,
+                             const int32_t *bc_dof, const double *bc_scale, int64_t n_bc, double load,
+                             cudaStream_t s);
+cudaError_t launch_reaction(const double *R, const int32_t *react_dof, int64_t n_react, double *out,
+                            cudaStream_t s);
+cudaError_t launch_damage_max(const double *kappa, int64_t n, double eta_d, double kappa_d, double *out,
+                              cudaStream_t s);
+
+}  // namespace gd

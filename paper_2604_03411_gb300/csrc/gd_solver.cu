@@ -1,0 +1,419 @@
+// gd_solver.cu -- device linear algebra for the global Newton iteration:
+// CSR SpMV over the node-block pattern, Jacobi preconditioning, FP64
+// reductions and a Jacobi-preconditioned BiCGStab (van der Vorst, 1992) whose
+// scalars live in device memory so that an iteration needs no host round trip.
+//
+// The paper solves every Newton system with a direct LU factorisation and
+// warm-starts each load step from the last converged state (Sec. 3.2); here
+// the linear systems are solved iteratively on the device.  Prescribed
+// displacement components are eliminated implicitly: Krylov vectors are zero
+// on prescribed dofs and the operator acts as the identity there.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "gd_internal.cuh"
+
+namespace gd {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block reduction of up to 4 values; thread 0 writes red[slot_k * nb + blockIdx.x]
+template <int K>
+__device__ __forceinline__ void block_partials(double (&v)[K], double *red, const int (&slot)[K], int nb)
+{
+    __shared__ double sh[K][kThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double s = warp_sum(v[k]);
+        if (lane == 0) sh[k][w] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double s = (lane < kThreads / 32) ? sh[k][lane] : 0.0;
+            s = warp_sum(s);
+            if (lane == 0) red[slot[k] * nb + blockIdx.x] = s;
+        }
+    }
+}
+
+// every block sums the nb partials of a slot (deterministic order)
+__device__ __forceinline__ double sum_partials(const double *red, int slot, int nb)
+{
+    __shared__ double sh[kThreads / 32];
+    __shared__ double res;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += red[slot * nb + i];
+    s = warp_sum(s);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = (lane < (int)(blockDim.x / 32)) ? sh[lane] : 0.0;
+        t = warp_sum(t);
+        if (lane == 0) res = t;
+    }
+    __syncthreads();
+    return res;
+}
+
+// y = A x on free rows, y = x on prescribed rows; warp per node: the ndof rows
+// of a node share one column list, read once; partial dots <a,y> and <b,y>
+// (a or b may be null) are written per block.
+template <int NDOF>
+__global__ void __launch_bounds__(kThreads) spmv_kernel(int64_t n_nodes, const int32_t *__restrict__ rowptr,
+                                                        const int32_t *__restrict__ colidx,
+                                                        const double *__restrict__ vals,
+                                                        const uint8_t *__restrict__ fixed,
+                                                        const double *__restrict__ x, double *__restrict__ y,
+                                                        const double *da, const double *db, double *red, int slot_a,
+                                                        int slot_b, int nb)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+    double pa = 0.0, pb = 0.0;
+    for (int64_t nd = warp0; nd < n_nodes; nd += nwarps) {
+        const int64_t r0 = nd * NDOF;
+        const int32_t base = rowptr[r0];
+        const int32_t len = rowptr[r0 + 1] - base;
+        double acc[NDOF];
+#pragma unroll
+        for (int i = 0; i < NDOF; ++i) acc[i] = 0.0;
+        for (int j = lane; j < len; j += 32) {
+            const double xv = x[colidx[base + j]];
+#pragma unroll
+            for (int i = 0; i < NDOF; ++i) acc[i] += vals[base + (int64_t)i * len + j] * xv;
+        }
+#pragma unroll
+        for (int i = 0; i < NDOF; ++i) acc[i] = warp_sum(acc[i]);
+        if (lane < NDOF) {
+            double v = 0.0;
+#pragma unroll
+            for (int i = 0; i < NDOF; ++i)
+                if (i == lane) v = acc[i];
+            const int64_t r = r0 + lane;
+            if (fixed[r]) v = x[r];
+            y[r] = v;
+            if (da) pa += da[r] * v;
+            if (db) pb += db[r] * v;
+        }
+    }
+    double v2[2] = {pa, pb};
+    const int sl[2] = {slot_a, slot_b};
+    block_partials<2>(v2, red, sl, nb);
+}
+
+// BiCGStab scalar slots in scal[]: 0 rho_old, 1 alpha, 2 omega, 3 rho, 4 flag
+// partial slots in red[]: 0 <rh,r>, 1 <rh,v>, 2 <t,s>, 3 <t,t>, 4 <r,r>, 5 <b,b>/misc
+enum { S_RHO = 0, S_RHV = 1, S_TS = 2, S_TT = 3, S_RR = 4, S_MISC = 5 };
+
+// p = r + beta (p - omega v), y = D^-1 p, beta = (rho/rho_old)(alpha/omega)
+__global__ void __launch_bounds__(kThreads) bicg_p_kernel(int64_t n, const double *__restrict__ r,
+                                                          double *__restrict__ p, const double *__restrict__ v,
+                                                          double *__restrict__ yv, const double *__restrict__ dinv,
+                                                          const double *red, double *scal, int nb, int first)
+{
+    const double rho = sum_partials(red, S_RHO, nb);
+    double beta = 0.0;
+    const double omega = scal[2];
+    if (!first) beta = (rho / scal[0]) * (scal[1] / omega);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double pv = first ? r[i] : r[i] + beta * (p[i] - omega * v[i]);
+        p[i] = pv;
+        yv[i] = dinv[i] * pv;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) scal[3] = rho;
+}
+
+// alpha = rho / <rh, v>; s = r - alpha v; z = D^-1 s
+__global__ void __launch_bounds__(kThreads) bicg_s_kernel(int64_t n, const double *__restrict__ r,
+                                                          const double *__restrict__ v, double *__restrict__ s,
+                                                          double *__restrict__ z, const double *__restrict__ dinv,
+                                                          const double *red, double *scal, int nb)
+{
+    const double rhv = sum_partials(red, S_RHV, nb);
+    const double alpha = scal[3] / rhv;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double sv = r[i] - alpha * v[i];
+        s[i] = sv;
+        z[i] = dinv[i] * sv;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) scal[1] = alpha;
+}
+
+// omega = <t,s>/<t,t>; x += alpha y + omega z; r = s - omega t; partials <rh,r>, <r,r>
+__global__ void __launch_bounds__(kThreads) bicg_x_kernel(int64_t n, double *__restrict__ x,
+                                                          const double *__restrict__ yv, const double *__restrict__ z,
+                                                          double *__restrict__ r, const double *__restrict__ s,
+                                                          const double *__restrict__ t, const double *__restrict__ rh,
+                                                          double *red, double *scal, int nb)
+{
+    const double ts = sum_partials(red, S_TS, nb);
+    const double tt = sum_partials(red, S_TT, nb);
+    const double omega = ts / tt;
+    const double alpha = scal[1];
+    double prr = 0.0, prhr = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] += alpha * yv[i] + omega * z[i];
+        double rv = s[i] - omega * t[i];
+        r[i] = rv;
+        prr += rv * rv;
+        prhr += rh[i] * rv;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        scal[2] = omega;
+        scal[0] = scal[3];
+    }
+    double v2[2] = {prhr, prr};
+    const int sl[2] = {S_RHO, S_RR};
+    block_partials<2>(v2, red, sl, nb);
+}
+
+// r = b (free) / 0 (fixed), rh = r, x = 0, p = v = 0; partials <rh,r>, <r,r>
+__global__ void __launch_bounds__(kThreads) bicg_init_kernel(int64_t n, const double *__restrict__ b,
+                                                             const uint8_t *__restrict__ fixed,
+                                                             double *__restrict__ x, double *__restrict__ r,
+                                                             double *__restrict__ rh, double *__restrict__ p,
+                                                             double *__restrict__ v, double *red, double *scal, int nb)
+{
+    double prr = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double bv = fixed[i] ? 0.0 : b[i];
+        x[i] = 0.0;
+        r[i] = bv;
+        rh[i] = bv;
+        p[i] = 0.0;
+        v[i] = 0.0;
+        prr += bv * bv;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        scal[0] = 1.0;
+        scal[1] = 1.0;
+        scal[2] = 1.0;
+    }
+    double v2[2] = {prr, prr};
+    const int sl[2] = {S_RHO, S_RR};
+    block_partials<2>(v2, red, sl, nb);
+}
+
+// reduce a slot to scal[idx] (one block)
+__global__ void reduce_slot_kernel(const double *red, int slot, int nb, double *out)
+{
+    double s = sum_partials(red, slot, nb);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// Jacobi: dinv_i = 1 / A_ii on free rows, 1 on prescribed rows
+template <int NDOF>
+__global__ void jacobi_kernel(int64_t n_nodes, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                              const double *__restrict__ vals, const uint8_t *__restrict__ fixed,
+                              double *__restrict__ dinv)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t nd = warp0; nd < n_nodes; nd += nwarps) {
+        const int64_t r0 = nd * NDOF;
+        const int32_t base = rowptr[r0];
+        const int32_t len = rowptr[r0 + 1] - base;
+        for (int j = lane; j < len; j += 32) {
+            const int32_t c = colidx[base + j];
+            if (c >= r0 && c < r0 + NDOF) {
+                const int i = (int)(c - r0);
+                const double d = vals[base + (int64_t)i * len + j];
+                dinv[r0 + i] = fixed[r0 + i] ? 1.0 : (d != 0.0 ? 1.0 / d : 1.0);
+            }
+        }
+    }
+}
+
+// ||v_free||^2 and ||v_fixed||^2 partials
+__global__ void __launch_bounds__(kThreads) norm_free_kernel(int64_t n, const double *__restrict__ v,
+                                                             const uint8_t *__restrict__ fixed, double *red, int nb)
+{
+    double a = 0.0, b = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double x = v[i];
+        if (fixed[i]) b += x * x; else a += x * x;
+    }
+    double v2[2] = {a, b};
+    const int sl[2] = {S_MISC, S_MISC + 1};
+    block_partials<2>(v2, red, sl, nb);
+}
+
+__global__ void norm_finish_kernel(const double *red, int nb, double *out_free, double *out_fixed)
+{
+    double a = sum_partials(red, S_MISC, nb);
+    double b = sum_partials(red, S_MISC + 1, nb);
+    if (threadIdx.x == 0) {
+        *out_free = sqrt(a);
+        if (out_fixed) *out_fixed = sqrt(b);
+    }
+}
+
+__global__ void axpy_free_kernel(int64_t n, double *y, const double *x, double alpha, const uint8_t *fixed)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!fixed[i]) y[i] += alpha * x[i];
+}
+
+// out = cur + factor (cur - prev) (prev null: out = cur), then prescribed dofs = scale * load
+__global__ void predictor_kernel(int64_t n, double *out, const double *cur, const double *prev, double factor)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = prev ? cur[i] + factor * (cur[i] - prev[i]) : cur[i];
+}
+__global__ void set_bc_kernel(double *out, const int32_t *bc_dof, const double *bc_scale, int64_t n_bc, double load)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_bc; i += (int64_t)gridDim.x * blockDim.x)
+        out[bc_dof[i]] = bc_scale[i] * load;
+}
+
+__global__ void reaction_kernel(const double *R, const int32_t *react_dof, int64_t n_react, double *out)
+{
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n_react; i += blockDim.x) s += R[react_dof[i]];
+    __shared__ double sh[32];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = (threadIdx.x < blockDim.x / 32) ? sh[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) *out = t;
+    }
+}
+
+__global__ void damage_max_kernel(const double *kappa, int64_t n, double eta_d, double kappa_d, double *out)
+{
+    double mx = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, kappa[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __shared__ double sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int i = 0; i < (int)(blockDim.x / 32); ++i) m = fmax(m, sh[i]);
+        *out = m > kappa_d ? -expm1(-eta_d * (m - kappa_d)) : 0.0;
+    }
+}
+
+int vec_grid(int64_t n, int nb) { return (int)((n + kThreads - 1) / kThreads < nb ? (n + kThreads - 1) / kThreads : nb); }
+
+cudaError_t spmv(const SolverCtx &c, const double *x, double *y, const double *da, const double *db, int slot_a,
+                 int slot_b)
+{
+    if (c.ndof == 3)
+        spmv_kernel<3><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals, c.fixed, x, y,
+                                                           da, db, c.red, slot_a, slot_b, c.blocks);
+    else
+        spmv_kernel<4><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals, c.fixed, x, y,
+                                                           da, db, c.red, slot_a, slot_b, c.blocks);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_jacobi_diag(const SolverCtx &c, double *diag)
+{
+    if (c.ndof == 3)
+        jacobi_kernel<3><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals, c.fixed, diag);
+    else
+        jacobi_kernel<4><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals, c.fixed, diag);
+    return cudaGetLastError();
+}
+
+// All blocks of the vector kernels use the same grid (c.blocks) so that every
+// partial slot has exactly c.blocks entries.
+int bicgstab(const SolverCtx &c, const double *dinv, const double *b, double *x, double *work[8], double rtol,
+             int max_it, double *final_rel)
+{
+    double *r = work[0], *rh = work[1], *p = work[2], *v = work[3], *s = work[4], *t = work[5], *yv = work[6],
+           *z = work[7];
+    const int nb = c.blocks;
+    bicg_init_kernel<<<nb, kThreads, 0, c.stream>>>(c.n, b, c.fixed, x, r, rh, p, v, c.red, c.scal, nb);
+    reduce_slot_kernel<<<1, kThreads, 0, c.stream>>>(c.red, S_RR, nb, c.scal + 8);
+    double h[2];
+    if (cudaMemcpyAsync(h, c.scal + 8, sizeof(double), cudaMemcpyDeviceToHost, c.stream) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess) return -1;
+    const double bnorm = std::sqrt(h[0]);
+    if (final_rel) *final_rel = 0.0;
+    if (bnorm == 0.0) return 0;
+    const int check = 4;
+    for (int it = 0; it < max_it; ++it) {
+        bicg_p_kernel<<<nb, kThreads, 0, c.stream>>>(c.n, r, p, v, yv, dinv, c.red, c.scal, nb, it == 0);
+        spmv(c, yv, v, rh, nullptr, S_RHV, S_MISC);
+        bicg_s_kernel<<<nb, kThreads, 0, c.stream>>>(c.n, r, v, s, z, dinv, c.red, c.scal, nb);
+        spmv(c, z, t, s, t, S_TS, S_TT);
+        bicg_x_kernel<<<nb, kThreads, 0, c.stream>>>(c.n, x, yv, z, r, s, t, rh, c.red, c.scal, nb);
+        if ((it + 1) % check == 0 || it + 1 == max_it) {
+            reduce_slot_kernel<<<1, kThreads, 0, c.stream>>>(c.red, S_RR, nb, c.scal + 8);
+            if (cudaMemcpyAsync(h, c.scal + 8, sizeof(double), cudaMemcpyDeviceToHost, c.stream) != cudaSuccess)
+                return -1;
+            if (cudaStreamSynchronize(c.stream) != cudaSuccess) return -1;
+            const double rel = std::sqrt(h[0]) / bnorm;
+            if (final_rel) *final_rel = rel;
+            if (!std::isfinite(rel)) return -1;
+            if (rel <= rtol) return it + 1;
+        }
+    }
+    return -1;
+}
+
+cudaError_t launch_norm2_free(const SolverCtx &c, const double *v, double *out_dev, double *out_fixed_dev)
+{
+    norm_free_kernel<<<c.blocks, kThreads, 0, c.stream>>>(c.n, v, c.fixed, c.red, c.blocks);
+    norm_finish_kernel<<<1, kThreads, 0, c.stream>>>(c.red, c.blocks, out_dev, out_fixed_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_free(const SolverCtx &c, double *y, const double *x, double alpha)
+{
+    axpy_free_kernel<<<vec_grid(c.n, c.blocks), kThreads, 0, c.stream>>>(c.n, y, x, alpha, c.fixed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_predictor(int64_t n, double *out, const double *cur, const double *prev, double factor,
+                             const int32_t *bc_dof, const double *bc_scale, int64_t n_bc, double load, cudaStream_t s)
+{
+    int g = (int)((n + kThreads - 1) / kThreads);
+    if (g > 1024) g = 1024;
+    predictor_kernel<<<g, kThreads, 0, s>>>(n, out, cur, prev, factor);
+    if (n_bc > 0) {
+        int gb = (int)((n_bc + kThreads - 1) / kThreads);
+        if (gb > 1024) gb = 1024;
+        set_bc_kernel<<<gb, kThreads, 0, s>>>(out, bc_dof, bc_scale, n_bc, load);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reaction(const double *R, const int32_t *react_dof, int64_t n_react, double *out, cudaStream_t s)
+{
+    reaction_kernel<<<1, 1024, 0, s>>>(R, react_dof, n_react, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_damage_max(const double *kappa, int64_t n, double eta_d, double kappa_d, double *out,
+                              cudaStream_t s)
+{
+    damage_max_kernel<<<1, 1024, 0, s>>>(kappa, n, eta_d, kappa_d, out);
+    return cudaGetLastError();
+}
+
+}  // namespace gd

@@ -1,0 +1,118 @@
+"""Parity of the device Newton iteration over a load path (gd_newton_step /
+gd_run_load_path) with the oracle's LU-based Newton, and of the homogeneous
+patch with the material-point driver (any mesh size)."""
+import numpy as np
+import pytest
+
+from gpu_common import rel_err
+from paper_2604_03411_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_03411_gb300 import build as build_mod
+    build_mod.build()
+    import oracle
+    import paper_2604_03411_gb300.binding as B
+    return torch, B, oracle
+
+
+def tight(B):
+    return B.gd_default_options(newton_rtol=1e-12, newton_atol=1e-14, krylov_rtol=1e-13, krylov_max=50000)
+
+
+def test_cfg1_load_unload_reload_path(env):
+    """The 8x8 Q4 square through the 40-step load-unload-reload path: reactions,
+    final fields and history against the oracle (both Newton to 1e-12)."""
+    torch, B, oracle = env
+    prob = I.config1()
+    h = B.gd_create(prob, tight(B))
+    reac, rep = B.gd_run_load_path(h)
+    assert rep.steps_done == 40
+    dofs, kappa = B.gd_get_fields(h)
+    model = oracle.Model.from_problem(prob)
+    ref = oracle.run_load_path(model, prob.mesh, prob.load, rtol=1e-12, atol=1e-14)
+    assert rel_err(reac, ref["reaction"]) < 1e-10
+    assert rel_err(dofs, ref["dofs"]) < 1e-10
+    assert rel_err(kappa, ref["kappa"]) < 1e-10
+
+
+def test_homogeneous_patch_32x32_matches_material_point(env):
+    torch, B, oracle = env
+    prob = I.config1(n=32)
+    prob.load = I.piecewise_path([0.0, 0.5, 0.1, 0.7], [5, 4, 6])
+    h = B.gd_create(prob, tight(B))
+    reac, rep = B.gd_run_load_path(h)
+    model = oracle.Model.from_problem(prob)
+    P11, lam2, kap = oracle.material_point_uniaxial(model, 1.0 + prob.load)
+    assert rel_err(reac, P11) < 1e-9
+    dofs, kappa = B.gd_get_fields(h)
+    assert rel_err(kappa, np.full_like(kappa, kap[-1])) < 1e-9
+    d = dofs.reshape(-1, 3)
+    assert rel_err(d[:, 2], np.full(d.shape[0], kap[-1])) < 1e-8
+
+
+def test_hex8_biaxial_path(env):
+    """3x3x3 HEX8 cube, biaxial stretch, both networks width 16/8, against the oracle."""
+    torch, B, oracle = env
+    psi, yld = I.icnn_pair(3, 16, 8)
+    mesh = I.biaxial_bc_3d(I.structured_hex8(3, 3, 3))
+    # break the symmetry a little so the field is not homogeneous
+    rng = np.random.default_rng(1)
+    inner = np.all((mesh.coords > 1e-9) & (mesh.coords < 1 - 1e-9), axis=1)
+    mesh.coords[inner] += 0.04 * rng.uniform(-1, 1, (inner.sum(), 3))
+    prob = I.Problem("hex", mesh, psi, yld, I.Material(c_d=0.1), np.linspace(0, 0.25, 6)[1:])
+    h = B.gd_create(prob, tight(B))
+    reac, rep = B.gd_run_load_path(h)
+    dofs, kappa = B.gd_get_fields(h)
+    model = oracle.Model.from_problem(prob)
+    ref = oracle.run_load_path(model, mesh, prob.load, rtol=1e-12, atol=1e-14)
+    assert rel_err(reac, ref["reaction"]) < 1e-10
+    assert rel_err(dofs, ref["dofs"]) < 1e-10
+    assert rel_err(kappa, ref["kappa"]) < 1e-10
+
+
+def test_newton_step_reports_and_state_roundtrip(env):
+    torch, B, oracle = env
+    prob = I.config1(n=4)
+    h = B.gd_create(prob, tight(B))
+    r1 = B.gd_newton_step(h)
+    assert r1.converged == 1 and r1.iterations >= 1 and r1.reaction > 0
+    d1, k1 = B.gd_get_fields(h)
+    r2 = B.gd_newton_step(h)
+    d2, k2 = B.gd_get_fields(h)
+    # restart from the state after step 1 and redo step 2: identical result
+    B.gd_set_state(h, d1, k1, next_step=1)
+    r2b = B.gd_newton_step(h)
+    d2b, k2b = B.gd_get_fields(h)
+    assert rel_err(d2b, d2) < 1e-11 and rel_err(k2b, k2) < 1e-11
+    assert abs(r2b.reaction - r2.reaction) <= 1e-11 * abs(r2.reaction)
+
+
+def test_errors_are_reported_not_faulted(env):
+    """Host-side failures: a finished path, an invalid mesh and a NaN state give
+    status codes; the handle stays usable."""
+    torch, B, oracle = env
+    prob = I.config1(n=2)
+    prob.load = prob.load[:2]
+    h = B.gd_create(prob, tight(B))
+    B.gd_run_load_path(h)
+    with pytest.raises(B.GDError) as ei:
+        B.gd_newton_step(h)
+    assert ei.value.status == 10
+    bad = I.config1(n=2)
+    bad.mesh.conn = bad.mesh.conn[:, ::-1].copy()
+    with pytest.raises(B.GDError) as ei:
+        B.gd_create(bad)
+    assert ei.value.status == 2
+    d, k = B.gd_get_fields(h)
+    d[5] = np.nan
+    B.gd_set_state(h, d, k, next_step=1)
+    with pytest.raises(B.GDError) as ei:
+        B.gd_newton_step(h)
+    assert ei.value.status in (6, 5, 7)
