@@ -1,0 +1,343 @@
+#!/usr/bin/env python3
+"""Benchmark of the gradient-enhanced damage hot path on one GB300 per rank.
+
+Metric: qp constitutive+assembly updates/s and Newton-step ms.  One bench step
+is one quasi-static load step of the monolithic scheme: Newton iterations, each
+an element-kernel pass (kinematics, ICNN energy with derivatives, yield network
+and local damage update, degraded stress, residual and consistent tangent,
+CSR scatter), the residual norms, a Jacobi-preconditioned BiCGStab solve and a
+backtracking line search.  value = (#qp x element-kernel passes in the timed
+steps) / (timed device time): whole-step throughput, inputs resident in HBM.
+
+Workloads (synthetic, seeded; see paper_2604_03411_gb300/inputs.py):
+  notched   2D notched plate 2:1, graded Q4 mesh of 39,936 elements (159,744 qp),
+            both ICNNs width 32, 50 steps to 60% nominal strain, FP64 (default)
+  cube      3D cube, 64^3 HEX8 (2,097,152 qp), biaxial, both ICNNs width 64
+  square    2D 8x8 Q4 square, load-unload-reload
+
+Multi-GPU: one process per GPU under torchrun; a single mesh does not shard, so
+every rank runs an independent replica of the workload (weak scaling) and
+value sums the ranks' qp updates over the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (the project's reference
+implementation of the method) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "qp constitutive+assembly updates/s & Newton-step ms, mixed vs FP64, 1 GB300"
+UNIT = "qp-updates/s"
+L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
+FP64_PEAK_TFLOPS_NOMINAL = 1.25     # GB300 dense FP64 (nominal, the recipe's table)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gd", choices=["gd", "reference"])
+    ap.add_argument("--workload", default="notched", choices=["notched", "cube", "square"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def make_workload(name):
+    from paper_2604_03411_gb300 import inputs as I
+    if name == "notched":
+        p = I.config2()
+        desc = {"workload": "notched_plate_q4", "elements": p.mesh.n_elems, "qp": p.mesh.n_elems * 4,
+                "dofs": p.mesh.n_nodes * 3, "icnn_width": [32, 32], "load_steps": int(p.load.size),
+                "length_scale": 0.02}
+    elif name == "cube":
+        p = I.config3(precision="fp64")
+        desc = {"workload": "cube_hex8_64", "elements": p.mesh.n_elems, "qp": p.mesh.n_elems * 8,
+                "dofs": p.mesh.n_nodes * 4, "icnn_width": [64, 64], "load_steps": int(p.load.size)}
+    else:
+        p = I.config1()
+        desc = {"workload": "square_q4_8x8", "elements": p.mesh.n_elems, "qp": p.mesh.n_elems * 4,
+                "dofs": p.mesh.n_nodes * 3, "icnn_width": [16, 8], "load_steps": int(p.load.size)}
+    return p, desc
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(prob, seconds, seed=7):
+    """The oracle as it stands (single thread): element assembly (residual, tangent,
+    local damage update) of a contiguous sample of elements at a seeded state."""
+    import numpy as np
+
+    import oracle
+    from paper_2604_03411_gb300 import inputs as I
+    model = oracle.Model.from_problem(prob)
+    rng = np.random.default_rng(seed)
+    dofs, kappa = I.random_state(prob.mesh, rng, u_amp=0.02, phi_amp=0.05, kappa_amp=0.02)
+    nq = prob.mesh.nq
+    t0 = time.perf_counter()
+    model.assemble(prob.mesh, dofs, kappa, e0=0, e1=min(64, prob.mesh.n_elems))
+    per_elem = (time.perf_counter() - t0) / min(64, prob.mesh.n_elems)
+    n = int(max(64, min(prob.mesh.n_elems, seconds / max(per_elem, 1e-9))))
+    t0 = time.perf_counter()
+    model.assemble(prob.mesh, dofs, kappa, e0=0, e1=n)
+    dt = time.perf_counter() - t0
+    return {"value": n * nq / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle assembly (residual, tangent, local damage update) of elements 0..{n - 1} "
+                      f"of {prob.mesh.n_elems} ({n * nq} qp) at a seeded state, {dt:.1f} s on 1 host thread"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    prob, desc = make_workload(args.workload)
+    vals = []
+    per_step = max(1.0, 120.0 / max(1, args.steps + args.warmup))
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline(prob, min(per_step, 20.0), seed=100 + k)
+        if k >= args.warmup:
+            vals.append(cb)
+    v = sum(c["value"] for c in vals) / len(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": desc,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": vals[-1]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gd(args):
+    import numpy as np
+    import torch
+
+    import paper_2604_03411_gb300.binding as B
+    from paper_2604_03411_gb300 import build as build_mod
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build_mod.build()
+    prob, desc = make_workload(args.workload)
+    stream = torch.cuda.current_stream()
+    prec = B.GD_FP64 if args.precision == "fp64" else B.GD_MIXED
+    opts = B.gd_default_options(precision=prec, cuda_stream=stream.cuda_stream)
+    h = B.gd_create(prob, opts)
+    n_qp = desc["qp"]
+    n_path = int(prob.load.size)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step(k):
+        if h_state["next"] >= n_path:          # restart the path when it runs out
+            B.gd_set_state(h, np.zeros(prob.mesh.n_nodes * prob.mesh.ndof),
+                           np.zeros((prob.mesh.n_elems, prob.mesh.nq)), 0)
+            h_state["next"] = 0
+        r = B.gd_newton_step(h)
+        h_state["next"] += 1
+        return r
+
+    h_state = {"next": 0}
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    reps = []
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()                               # L2 flush between timed steps (outside the events)
+        evs[k][0].record(stream)
+        reps.append(step(k))
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    asm = sum(r.assemblies for r in reps)
+    units = n_qp * asm
+    if dist:
+        t = torch.tensor([total_ms, float(units)], dtype=torch.float64, device="cuda")
+        tm = t.clone()
+        dist.all_reduce(tm[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+        total_ms_all, units_all = float(tm[0]), float(t[1])
+    else:
+        total_ms_all, units_all = total_ms, float(units)
+    value = units_all / (total_ms_all / 1e3)
+    newton = sum(r.iterations for r in reps)
+    krylov = sum(r.krylov_iterations for r in reps)
+    asm_ms = sum(r.assembly_ms for r in reps)
+    kry_ms = sum(r.krylov_ms for r in reps)
+    launches = sum(r.kernel_launches for r in reps)
+
+    # --- dominant-kernel roofline: SpMV of the Krylov loop vs the element kernel ---
+    n_dofs = prob.mesh.n_nodes * prob.mesh.ndof
+    rowptr, colidx = B.gd_csr_pattern(h)
+    nnz = colidx.size
+    x = torch.randn(n_dofs, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        B.gd_spmv(h, x, y, 1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps_spmv = 50
+    e0.record(stream)
+    for _ in range(reps_spmv):
+        B.gd_spmv(h, x, y, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    spmv_ms = e0.elapsed_time(e1) / reps_spmv
+    ndof = prob.mesh.ndof
+    # algorithmic bytes of one SpMV: every value once (FP64), the column list once per
+    # node (the ndof rows of a node share it), row pointers, x gathered once per
+    # column-list entry's node block (counted once per dof), y written, prescribed mask
+    spmv_bytes = nnz * 8 + (nnz // ndof) * 4 + (prob.mesh.n_nodes + 1) * 4 * 2 + n_dofs * (8 + 8 + 1)
+    spmv_total = 2 * krylov * spmv_ms
+    peak_bw, peak_kind = measured_peaks()
+    asm_avg = asm_ms / max(asm, 1)
+    if spmv_total >= asm_ms:
+        achieved = spmv_bytes / (spmv_ms / 1e3) / 1e9
+        roof = {"kernel": "spmv_kernel (CSR SpMV of the Krylov loop)", "bound": "hbm", "achieved": achieved,
+                "peak": peak_bw, "unit": "GB/s", "frac": achieved / peak_bw, "traffic": None,
+                "peak_source": f"{peak_kind} copy bandwidth", "avg_launch_us": spmv_ms * 1e3,
+                "algorithmic_bytes_per_launch": spmv_bytes,
+                "note": "the matrix (%.0f MB) is L2-resident across Krylov iterations" % (spmv_bytes / 1e6)}
+    else:
+        # FP64 ALU bound element kernel: algorithmic FP64 FLOPs (FMA = 2) of the dense parts
+        wp, wy = desc["icnn_width"]
+        nq = prob.mesh.nq
+        nd = prob.mesh.nen * ndof
+        evals = sum(r.yield_evals for r in reps)
+        flops = (n_qp * asm * (10 * wp * wp + 40 * wp) + evals * (4 * wy * wy + 20 * wy)
+                 + (asm * prob.mesh.n_elems) * nd * nd * nq * 25)
+        achieved = flops / (asm_ms / 1e3) / 1e12
+        roof = {"kernel": "asm_fp64_kernel (element kernel)", "bound": "alu", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS_NOMINAL,
+                "traffic": None, "peak_source": "nominal FP64 rate", "avg_launch_us": asm_avg * 1e3}
+
+    # --- end to end through the C ABI with host buffers ---
+    d_host, k_host = B.gd_get_fields(h)
+    nxt = h_state["next"] if h_state["next"] < n_path else 0
+    if nxt == 0:
+        d_host[:] = 0.0
+        k_host[:] = 0.0
+    e2e_ms = 0.0
+    e2e_units = 0
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.gd_set_state(h, d_host, k_host, nxt)           # host -> device
+        r = B.gd_newton_step(h)
+        d_out, k_out = B.gd_get_fields(h)                # device -> host
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+        e2e_units += n_qp * r.assemblies
+    h2d = d_host.nbytes + k_host.nbytes
+    e2e = {"value": e2e_units / (e2e_ms / 1e3) * (world if world > 1 else 1), "unit": UNIT,
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == B.GD_FP64 else "bf16+f32+f64",
+        "data": "synthetic (seeded mesh, seeded ICNN weights)",
+        "config": dict(desc, precision=args.precision, parallelism=f"replicas{world}",
+                       l2="flushed between timed steps (512 MB write)"),
+        "newton_step_ms": total_ms / max(newton, 1),
+        "newton_iterations": newton, "krylov_iterations": krylov,
+        "assembly": {"launches": asm, "avg_ms": asm_avg, "qp_per_s": n_qp / (asm_avg / 1e3),
+                     "share_of_step": asm_ms / total_ms},
+        "krylov_share_of_step": kry_ms / total_ms,
+        "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
+    elif rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gd(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -136,7 +136,12 @@ typedef struct gd_newton_report {
     int32_t local_failures;
     int32_t loading_points;    /* qps on the loading branch at convergence              */
     int32_t step_cuts;
+    int32_t assemblies;        /* element-kernel launches in the step                   */
     double residual0, residual, reaction, max_damage;
+    double assembly_ms;        /* device time of those launches (CUDA events)           */
+    double krylov_ms;          /* device time of the linear solves                      */
+    int64_t yield_evals;       /* yield-network evaluations of the local solves (all launches) */
+    int64_t kernel_launches;   /* device kernels this library launched for the step     */
 } gd_newton_report;
 
 typedef struct gd_path_report {
@@ -201,6 +206,13 @@ gd_status gd_build_pattern(const gd_mesh *mesh, int64_t *n_rows, int64_t *nnz, i
  * Returns GD_ERR_LOCAL_SOLVE when a local solve hit local_max (outputs still written). */
 gd_status gd_assemble(gd_handle *h, const double *dofs, const double *kappa_n, double *R,
                       void *csr_vals, double *kappa_trial, int8_t *loading, int32_t mode);
+
+/* y = K x with the tangent of the handle's last assembly (the one used by the
+ * most recent Newton direction, or by gd_assemble when csr_vals was NULL there):
+ * x, y device FP64 [n_nodes*ndof]; with free_only != 0 prescribed rows return
+ * x and prescribed columns are skipped (the eliminated operator of the Newton
+ * system).  Works on the handle's stream; does not synchronise. */
+gd_status gd_spmv(gd_handle *h, const double *x, double *y, int32_t free_only);
 
 /* Advances the next load step of the path to convergence (monolithic Newton,
  * Sec. 3.2, with a line search and nested step halving on failure); commits

@@ -63,9 +63,10 @@ class GdNewtonReport(ctypes.Structure):
     _fields_ = [("converged", ctypes.c_int32), ("iterations", ctypes.c_int32),
                 ("krylov_iterations", ctypes.c_int32), ("line_search_cuts", ctypes.c_int32),
                 ("local_failures", ctypes.c_int32), ("loading_points", ctypes.c_int32),
-                ("step_cuts", ctypes.c_int32),
+                ("step_cuts", ctypes.c_int32), ("assemblies", ctypes.c_int32),
                 ("residual0", ctypes.c_double), ("residual", ctypes.c_double), ("reaction", ctypes.c_double),
-                ("max_damage", ctypes.c_double)]
+                ("max_damage", ctypes.c_double), ("assembly_ms", ctypes.c_double), ("krylov_ms", ctypes.c_double),
+                ("yield_evals", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
 
 
 class GdPathReport(ctypes.Structure):
@@ -87,6 +88,7 @@ PROTOTYPES = {
     "gd_build_pattern": (ctypes.c_int, [ctypes.POINTER(GdMesh), _i64p, _i64p, _i32p, _i32p, _i32p]),
     "gd_assemble": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "gd_spmv": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "gd_newton_step": (ctypes.c_int, [_H, ctypes.POINTER(GdNewtonReport)]),
     "gd_run_load_path": (ctypes.c_int, [_H, _dp, ctypes.POINTER(GdPathReport)]),
     "gd_backward": (ctypes.c_int, [_H, _dp, _dp]),
@@ -250,6 +252,10 @@ def gd_assemble(h: Handle, dofs, kappa_n=None, R=None, csr_vals=None, kappa_tria
     st = lib().gd_assemble(h.ptr, _dptr(dofs), _dptr(kappa_n), _dptr(R), _dptr(csr_vals), _dptr(kappa_trial),
                            _dptr(loading), mode)
     _check(st, h.ptr)
+
+
+def gd_spmv(h: Handle, x, y, free_only: int = 0):
+    _check(lib().gd_spmv(h.ptr, _dptr(x), _dptr(y), int(free_only)), h.ptr)
 
 
 def gd_newton_step(h: Handle) -> GdNewtonReport:

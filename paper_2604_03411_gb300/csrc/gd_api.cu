@@ -109,6 +109,7 @@ gd::SolverCtx solver_ctx(gd::Handle &H, const double *vals)
     c.red = H.red;
     c.scal = H.scal;
     c.blocks = H.red_blocks;
+    c.launches = &H.launches;
     return c;
 }
 
@@ -150,6 +151,7 @@ gd_status assemble_pass(gd::Handle &H, const double *dofs, const double *kappa_n
     if (H.opt.precision != GD_FP64)
         return fail(&H, GD_ERR_ARG, "mixed precision assembly is not built into this library");
     GD_CUDA(&H, gd::launch_assemble_fp64(H.dim, a, H.num_sms, H.stream));
+    ++H.launches;
     GD_CUDA(&H, cudaEventRecord(H.ev1, H.stream));
     ++H.assemblies;
     return GD_OK;
@@ -187,8 +189,9 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
     NormPair nr;
     if ((st = norms(H, H.R, nr))) return st;
     H.assembly_ms += elapsed_ms(H);
-    int hc[2];
-    GD_CUDA(&H, cudaMemcpy(hc, H.counters, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+    int hc[3];
+    GD_CUDA(&H, cudaMemcpy(hc, H.counters, 3 * sizeof(int), cudaMemcpyDeviceToHost));
+    rep.yield_evals += hc[2];
     double nrm = nr.free_;
     const double r0 = std::max(nr.free_, nr.fixed_);
     rep.residual0 = nrm;
@@ -240,6 +243,8 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
                 return st;
             if ((st = norms(H, H.R_trial, nr))) return st;
             H.assembly_ms += elapsed_ms(H);
+            GD_CUDA(&H, cudaMemcpy(hc, H.counters, 3 * sizeof(int), cudaMemcpyDeviceToHost));
+            rep.yield_evals += hc[2];
             nt = nr.free_;
             if ((std::isfinite(nt) && nt <= (1.0 - 1e-4 * alpha) * nrm) || ls == H.opt.line_search_max) break;
             alpha *= 0.5;
@@ -250,7 +255,6 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
         std::swap(H.vals, H.vals_trial);
         std::swap(H.kappa_trial, H.kappa_trial2);
         std::swap(H.loading, H.loading2);
-        GD_CUDA(&H, cudaMemcpy(hc, H.counters, 2 * sizeof(int), cudaMemcpyDeviceToHost));
         rep.local_failures = hc[0];
         rep.loading_points = hc[1];
         nrm = nt;
@@ -265,6 +269,8 @@ gd_status commit(gd::Handle &H, double target, gd_newton_report &rep)
     GD_CUDA(&H, gd::launch_reaction(H.R, H.react_dof, H.n_react, H.scal + 20, H.stream));
     GD_CUDA(&H, gd::launch_damage_max(H.kappa_trial, H.n_elems * H.nq, H.mat.eta_d, H.mat.kappa_d, H.scal + 21,
                                       H.stream));
+    H.launches += 2;
+    rep.kernel_launches += 2;
     double h[2];
     GD_CUDA(&H, cudaMemcpyAsync(h, H.scal + 20, 2 * sizeof(double), cudaMemcpyDeviceToHost, H.stream));
     std::swap(H.dofs_prev, H.dofs);
@@ -287,8 +293,17 @@ gd_status advance(gd::Handle &H, double target, int depth, gd_newton_report &rep
     const double factor = extrap ? (target - H.load_prev) / dl : 0.0;
     GD_CUDA(&H, gd::launch_predictor(H.n_dofs, H.w_dofs, H.dofs, extrap ? H.dofs_prev : nullptr, factor, H.bc_dof,
                                      H.bc_scale, H.n_bc, target, H.stream));
+    H.launches += H.n_bc > 0 ? 2 : 1;
     gd_newton_report sub{};
+    const double a0 = H.assembly_ms, k0 = H.krylov_ms;
+    const int n0 = H.assemblies;
+    const long long l0 = H.launches;
     gd_status st = newton(H, sub);
+    rep.assembly_ms += H.assembly_ms - a0;
+    rep.krylov_ms += H.krylov_ms - k0;
+    rep.assemblies += H.assemblies - n0;
+    rep.yield_evals += sub.yield_evals;
+    rep.kernel_launches += H.launches - l0;
     rep.iterations += sub.iterations;
     rep.krylov_iterations += sub.krylov_iterations;
     rep.line_search_cuts += sub.line_search_cuts;
@@ -667,6 +682,17 @@ gd_status gd_assemble(gd_handle *h, const double *dofs, const double *kappa_n, d
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));
     H.assembly_ms += elapsed_ms(H);
     if (hc[0] > 0) return fail(&H, GD_ERR_LOCAL_SOLVE, std::to_string(hc[0]) + " local solves hit local_max");
+    return GD_OK;
+}
+
+gd_status gd_spmv(gd_handle *h, const double *x, double *y, int32_t free_only)
+{
+    if (!h) return fail(nullptr, GD_ERR_ARG, "null handle");
+    gd::Handle &H = h->h;
+    if (!x || !y) return fail(&H, GD_ERR_ARG, "null vector");
+    if (H.opt.precision != GD_FP64) return fail(&H, GD_ERR_ARG, "gd_spmv needs FP64 values");
+    gd::SolverCtx c = solver_ctx(H, H.vals);
+    GD_CUDA(&H, gd::launch_spmv(c, x, y, free_only));
     return GD_OK;
 }
 

@@ -520,6 +520,7 @@ __global__ void __launch_bounds__(32 * kWarps) asm_fp64_kernel(AsmArgs A)
             if (e0 + p / NQ >= A.n_elems) break;
             const double ppe = sIn[p * 4], pphi = sIn[p * 4 + 1], kn = sIn[p * 4 + 2];
             double r, dr, Gp;
+            int n_eval = 1;
             r_slope(A, nc, ppe, pphi, kn, r, dr, Gp, sBuf, lane);
             double kappa = kn, fail = 0.0, loading = 0.0;
             if (r > 0.0) {
@@ -528,16 +529,19 @@ __global__ void __launch_bounds__(32 * kWarps) asm_fp64_kernel(AsmArgs A)
                 int grow = 0;
                 double rh, drh, gph;
                 r_slope(A, nc, ppe, pphi, hi, rh, drh, gph, sBuf, lane);
+                ++n_eval;
                 while (rh > 0.0 && grow < 200) {
                     lo = hi;
                     step *= 2.0;
                     hi = kn + step;
                     ++grow;
                     r_slope(A, nc, ppe, pphi, hi, rh, drh, gph, sBuf, lane);
+                    ++n_eval;
                 }
                 if (grow >= 200) fail = 1.0;
                 kappa = lo;
                 r_slope(A, nc, ppe, pphi, kappa, r, dr, Gp, sBuf, lane);
+                ++n_eval;
                 double dx_prev = hi - lo, dx = dx_prev;
                 int it;
                 for (it = 0; it < m.local_max; ++it) {
@@ -554,12 +558,14 @@ __global__ void __launch_bounds__(32 * kWarps) asm_fp64_kernel(AsmArgs A)
                         kappa = lo + dx;
                     }
                     r_slope(A, nc, ppe, pphi, kappa, r, dr, Gp, sBuf, lane);
+                    ++n_eval;
                     if (r > 0.0) lo = kappa; else hi = kappa;
                 }
                 if (it >= m.local_max) fail = 1.0;
             }
             if (lane == 0) {
                 double *o = sOut + p * 10;
+                if (e0 + p / NQ < A.n_elems) atomicAdd(A.counters + 2, n_eval);
                 o[0] = kappa;
                 o[1] = loading;
                 o[2] = Gp;

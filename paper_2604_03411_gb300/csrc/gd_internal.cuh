@@ -55,7 +55,7 @@ struct AsmArgs {
     const NetConst *netc;
     MatConst mat;
     int tangent;
-    int *counters;           // [0] local-solve failures, [1] loading points
+    int *counters;           // [0] local-solve failures, [1] loading points, [2] yield-network evaluations
 };
 
 struct Handle {
@@ -106,6 +106,7 @@ struct Handle {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double assembly_ms = 0.0, krylov_ms = 0.0;
     int assemblies = 0;
+    long long launches = 0;                              // kernels launched by this handle
     std::string err;
     int num_sms = 0;
 };
@@ -128,8 +129,11 @@ struct SolverCtx {
     double *red;                // [2 * blocks * 4]
     double *scal;               // [64]
     int blocks;
+    long long *launches;        // host counter of kernel launches (may be null)
 };
 cudaError_t launch_jacobi_diag(const SolverCtx &c, double *diag);
+// y = A x; free_only: prescribed rows copy x, prescribed columns skipped
+cudaError_t launch_spmv(const SolverCtx &c, const double *x, double *y, int free_only);
 // Solves A x = b on the free dofs (A = vals with prescribed rows/cols removed);
 // x is overwritten; returns iterations (>= 0) or -1 on breakdown / cap.
 int bicgstab(const SolverCtx &c, const double *diag, const double *b, double *x, double *work[8],

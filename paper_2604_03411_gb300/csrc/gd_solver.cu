@@ -116,6 +116,45 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(int64_t n_nodes, const i
     block_partials<2>(v2, red, sl, nb);
 }
 
+// plain y = A x (free_only: prescribed rows y = x, prescribed columns skipped)
+template <int NDOF>
+__global__ void __launch_bounds__(kThreads) spmv_plain_kernel(int64_t n_nodes, const int32_t *__restrict__ rowptr,
+                                                              const int32_t *__restrict__ colidx,
+                                                              const double *__restrict__ vals,
+                                                              const uint8_t *__restrict__ fixed,
+                                                              const double *__restrict__ x, double *__restrict__ y,
+                                                              int free_only)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+    for (int64_t nd = warp0; nd < n_nodes; nd += nwarps) {
+        const int64_t r0 = nd * NDOF;
+        const int32_t base = rowptr[r0];
+        const int32_t len = rowptr[r0 + 1] - base;
+        double acc[NDOF];
+#pragma unroll
+        for (int i = 0; i < NDOF; ++i) acc[i] = 0.0;
+        for (int j = lane; j < len; j += 32) {
+            const int32_t c = colidx[base + j];
+            const double xv = (free_only && fixed[c]) ? 0.0 : x[c];
+#pragma unroll
+            for (int i = 0; i < NDOF; ++i) acc[i] += vals[base + (int64_t)i * len + j] * xv;
+        }
+#pragma unroll
+        for (int i = 0; i < NDOF; ++i) acc[i] = warp_sum(acc[i]);
+        if (lane < NDOF) {
+            double v = 0.0;
+#pragma unroll
+            for (int i = 0; i < NDOF; ++i)
+                if (i == lane) v = acc[i];
+            const int64_t r = r0 + lane;
+            if (free_only && fixed[r]) v = x[r];
+            y[r] = v;
+        }
+    }
+}
+
 // BiCGStab scalar slots in scal[]: 0 rho_old, 1 alpha, 2 omega, 3 rho, 4 flag
 // partial slots in red[]: 0 <rh,r>, 1 <rh,v>, 2 <t,s>, 3 <t,t>, 4 <r,r>, 5 <b,b>/misc
 enum { S_RHO = 0, S_RHV = 1, S_TS = 2, S_TT = 3, S_RR = 4, S_MISC = 5 };
@@ -129,7 +168,10 @@ __global__ void __launch_bounds__(kThreads) bicg_p_kernel(int64_t n, const doubl
     const double rho = sum_partials(red, S_RHO, nb);
     double beta = 0.0;
     const double omega = scal[2];
-    if (!first) beta = (rho / scal[0]) * (scal[1] / omega);
+    // exact convergence or breakdown makes a denominator vanish: take a zero step
+    // and flag it (scal[4]) instead of producing 0/0
+    if (!first && scal[0] != 0.0 && omega != 0.0) beta = (rho / scal[0]) * (scal[1] / omega);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && rho == 0.0) scal[4] = 1.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double pv = first ? r[i] : r[i] + beta * (p[i] - omega * v[i]);
         p[i] = pv;
@@ -145,7 +187,7 @@ __global__ void __launch_bounds__(kThreads) bicg_s_kernel(int64_t n, const doubl
                                                           const double *red, double *scal, int nb)
 {
     const double rhv = sum_partials(red, S_RHV, nb);
-    const double alpha = scal[3] / rhv;
+    const double alpha = rhv != 0.0 ? scal[3] / rhv : 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double sv = r[i] - alpha * v[i];
         s[i] = sv;
@@ -163,7 +205,7 @@ __global__ void __launch_bounds__(kThreads) bicg_x_kernel(int64_t n, double *__r
 {
     const double ts = sum_partials(red, S_TS, nb);
     const double tt = sum_partials(red, S_TT, nb);
-    const double omega = ts / tt;
+    const double omega = tt != 0.0 ? ts / tt : 0.0;
     const double alpha = scal[1];
     double prr = 0.0, prhr = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -204,6 +246,7 @@ __global__ void __launch_bounds__(kThreads) bicg_init_kernel(int64_t n, const do
         scal[0] = 1.0;
         scal[1] = 1.0;
         scal[2] = 1.0;
+        scal[4] = 0.0;
     }
     double v2[2] = {prr, prr};
     const int sl[2] = {S_RHO, S_RR};
@@ -314,11 +357,17 @@ __global__ void damage_max_kernel(const double *kappa, int64_t n, double eta_d, 
     }
 }
 
+inline void count(const SolverCtx &c, int n = 1)
+{
+    if (c.launches) *c.launches += n;
+}
+
 int vec_grid(int64_t n, int nb) { return (int)((n + kThreads - 1) / kThreads < nb ? (n + kThreads - 1) / kThreads : nb); }
 
 cudaError_t spmv(const SolverCtx &c, const double *x, double *y, const double *da, const double *db, int slot_a,
                  int slot_b)
 {
+    count(c);
     if (c.ndof == 3)
         spmv_kernel<3><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals, c.fixed, x, y,
                                                            da, db, c.red, slot_a, slot_b, c.blocks);
@@ -330,8 +379,21 @@ cudaError_t spmv(const SolverCtx &c, const double *x, double *y, const double *d
 
 }  // namespace
 
+cudaError_t launch_spmv(const SolverCtx &c, const double *x, double *y, int free_only)
+{
+    count(c);
+    if (c.ndof == 3)
+        spmv_plain_kernel<3><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals, c.fixed, x,
+                                                                 y, free_only);
+    else
+        spmv_plain_kernel<4><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals, c.fixed, x,
+                                                                 y, free_only);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_jacobi_diag(const SolverCtx &c, double *diag)
 {
+    count(c);
     if (c.ndof == 3)
         jacobi_kernel<3><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals, c.fixed, diag);
     else
@@ -349,6 +411,7 @@ int bicgstab(const SolverCtx &c, const double *dinv, const double *b, double *x,
     const int nb = c.blocks;
     bicg_init_kernel<<<nb, kThreads, 0, c.stream>>>(c.n, b, c.fixed, x, r, rh, p, v, c.red, c.scal, nb);
     reduce_slot_kernel<<<1, kThreads, 0, c.stream>>>(c.red, S_RR, nb, c.scal + 8);
+    count(c, 2);
     double h[2];
     if (cudaMemcpyAsync(h, c.scal + 8, sizeof(double), cudaMemcpyDeviceToHost, c.stream) != cudaSuccess) return -1;
     if (cudaStreamSynchronize(c.stream) != cudaSuccess) return -1;
@@ -362,15 +425,21 @@ int bicgstab(const SolverCtx &c, const double *dinv, const double *b, double *x,
         bicg_s_kernel<<<nb, kThreads, 0, c.stream>>>(c.n, r, v, s, z, dinv, c.red, c.scal, nb);
         spmv(c, z, t, s, t, S_TS, S_TT);
         bicg_x_kernel<<<nb, kThreads, 0, c.stream>>>(c.n, x, yv, z, r, s, t, rh, c.red, c.scal, nb);
+        count(c, 3);
         if ((it + 1) % check == 0 || it + 1 == max_it) {
             reduce_slot_kernel<<<1, kThreads, 0, c.stream>>>(c.red, S_RR, nb, c.scal + 8);
+            count(c);
             if (cudaMemcpyAsync(h, c.scal + 8, sizeof(double), cudaMemcpyDeviceToHost, c.stream) != cudaSuccess)
+                return -1;
+            double flag = 0.0;
+            if (cudaMemcpyAsync(&flag, c.scal + 4, sizeof(double), cudaMemcpyDeviceToHost, c.stream) != cudaSuccess)
                 return -1;
             if (cudaStreamSynchronize(c.stream) != cudaSuccess) return -1;
             const double rel = std::sqrt(h[0]) / bnorm;
             if (final_rel) *final_rel = rel;
             if (!std::isfinite(rel)) return -1;
             if (rel <= rtol) return it + 1;
+            if (flag != 0.0) return -1;   // rho = 0 with a non-zero residual: breakdown
         }
     }
     return -1;
@@ -378,6 +447,7 @@ int bicgstab(const SolverCtx &c, const double *dinv, const double *b, double *x,
 
 cudaError_t launch_norm2_free(const SolverCtx &c, const double *v, double *out_dev, double *out_fixed_dev)
 {
+    count(c, 2);
     norm_free_kernel<<<c.blocks, kThreads, 0, c.stream>>>(c.n, v, c.fixed, c.red, c.blocks);
     norm_finish_kernel<<<1, kThreads, 0, c.stream>>>(c.red, c.blocks, out_dev, out_fixed_dev);
     return cudaGetLastError();
@@ -385,6 +455,7 @@ cudaError_t launch_norm2_free(const SolverCtx &c, const double *v, double *out_d
 
 cudaError_t launch_axpy_free(const SolverCtx &c, double *y, const double *x, double alpha)
 {
+    count(c);
     axpy_free_kernel<<<vec_grid(c.n, c.blocks), kThreads, 0, c.stream>>>(c.n, y, x, alpha, c.fixed);
     return cudaGetLastError();
 }
