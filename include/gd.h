@@ -114,12 +114,15 @@ typedef struct gd_load_path {
 
 typedef struct gd_options {
     int32_t precision;         /* GD_FP64 or GD_MIXED                                  */
-    double newton_rtol;        /* ||R_free|| <= max(rtol max(||R0_free||, ||R_fixed||), atol) */
+    double newton_rtol;        /* ||R_free|| <= max(rtol max(||R0_free||, ||R_fixed||), atol);
+                                  raised to 1e-6 in GD_MIXED (FP32 element math)          */
     double newton_atol;
     int32_t newton_max;        /* Newton iterations per step                           */
     int32_t line_search_max;   /* backtracking halvings per Newton direction           */
     int32_t krylov;            /* GD_BICGSTAB (GD_GMRES reserved)                      */
-    double krylov_rtol;        /* relative residual of each linear solve               */
+    double krylov_rtol;        /* floor of the relative residual of each Newton solve (the
+                                  solve stops at max(krylov_rtol, min(1e-2, 0.1 tol/||R||)),
+                                  tol the Newton tolerance); gd_solve uses it directly       */
     int32_t krylov_max;
     int32_t gmres_m;
     int32_t local_max;         /* local kappa iterations (the paper caps at 100, Sec. 5.3) */
@@ -213,6 +216,16 @@ gd_status gd_assemble(gd_handle *h, const double *dofs, const double *kappa_n, d
  * x and prescribed columns are skipped (the eliminated operator of the Newton
  * system).  Works on the handle's stream; does not synchronise. */
 gd_status gd_spmv(gd_handle *h, const double *x, double *y, int32_t free_only);
+
+/* Solves K x = b on the free dofs (the eliminated Newton system) with
+ * node-block-Jacobi BiCGStab (opt.krylov_rtol / krylov_max).  csr_vals: device
+ * tangent values in the handle's precision from gd_assemble, or NULL for the
+ * tangent of the handle's last Newton iteration.  b, x device FP64
+ * [n_nodes*ndof]; prescribed dofs of x are returned as 0.  iterations and
+ * rel_residual (host, may be NULL) report the solve.  Synchronises the stream.
+ * Errors: GD_ERR_KRYLOV when the tolerance is not reached. */
+gd_status gd_solve(gd_handle *h, const void *csr_vals, const double *b, double *x, int32_t *iterations,
+                   double *rel_residual);
 
 /* Advances the next load step of the path to convergence (monolithic Newton,
  * Sec. 3.2, with a line search and nested step halving on failure); commits

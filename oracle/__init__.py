@@ -64,7 +64,10 @@ class _OrMat(ctypes.Structure):
 def lib():
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
+        # GD_ORACLE_SO points the pins at another build of this file (the mutation
+        # test plants mistakes in a copy and checks that the pins catch them)
+        so = os.environ.get("GD_ORACLE_SO") or build()
+        L = ctypes.CDLL(so)
         P = ctypes.POINTER(_OrMat)
         L.or_prepare.argtypes = [P]
         L.or_prepare.restype = ctypes.c_int

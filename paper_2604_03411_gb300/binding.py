@@ -89,6 +89,8 @@ PROTOTYPES = {
     "gd_assemble": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "gd_spmv": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "gd_solve": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                _dp]),
     "gd_newton_step": (ctypes.c_int, [_H, ctypes.POINTER(GdNewtonReport)]),
     "gd_run_load_path": (ctypes.c_int, [_H, _dp, ctypes.POINTER(GdPathReport)]),
     "gd_backward": (ctypes.c_int, [_H, _dp, _dp]),
@@ -256,6 +258,14 @@ def gd_assemble(h: Handle, dofs, kappa_n=None, R=None, csr_vals=None, kappa_tria
 
 def gd_spmv(h: Handle, x, y, free_only: int = 0):
     _check(lib().gd_spmv(h.ptr, _dptr(x), _dptr(y), int(free_only)), h.ptr)
+
+
+def gd_solve(h: Handle, b, x, csr_vals=None):
+    """Solve K x = b (device FP64 tensors); returns (iterations, relative residual)."""
+    it = ctypes.c_int32()
+    rel = ctypes.c_double()
+    _check(lib().gd_solve(h.ptr, _dptr(csr_vals), _dptr(b), _dptr(x), ctypes.byref(it), ctypes.byref(rel)), h.ptr)
+    return it.value, rel.value
 
 
 def gd_newton_step(h: Handle) -> GdNewtonReport:

@@ -86,13 +86,15 @@ bool element_ok(int dim, const double *Xe)
 void free_handle(gd::Handle &H)
 {
     void *ptrs[] = {H.X, H.conn, H.slot, H.rowptr, H.colidx, H.fixed, H.bc_dof, H.bc_scale, H.react_dof,
-                    H.psi.p, H.psi.W2T, H.yld.p, H.yld.W2T, H.netc, H.dofs, H.kappa, H.dofs_prev, H.w_dofs,
+                    H.psi.p, H.psi.W2T, H.yld.p, H.yld.W2T, H.psi.pf, H.psi.W2Tf, H.yld.pf, H.yld.W2Tf, H.netc, H.dofs, H.kappa, H.dofs_prev, H.w_dofs,
                     H.w_trial, H.R, H.R_trial, H.vals, H.vals_trial, H.kappa_trial, H.kappa_trial2, H.loading,
-                    H.loading2, H.counters, H.diag, H.red, H.scal};
+                    H.loading2, H.counters, H.diag, H.binv, H.red, H.scal};
     for (void *p : ptrs) dfree(p);
     for (double *p : H.kv) dfree(p);
     if (H.ev0) cudaEventDestroy(H.ev0);
     if (H.ev1) cudaEventDestroy(H.ev1);
+    if (H.kv0) cudaEventDestroy(H.kv0);
+    if (H.kv1) cudaEventDestroy(H.kv1);
 }
 
 gd::SolverCtx solver_ctx(gd::Handle &H, const double *vals)
@@ -148,9 +150,8 @@ gd_status assemble_pass(gd::Handle &H, const double *dofs, const double *kappa_n
     GD_CUDA(&H, cudaMemsetAsync(H.counters, 0, sizeof(int) * 8, H.stream));
     GD_CUDA(&H, cudaEventRecord(H.ev0, H.stream));
     gd::AsmArgs a = asm_args(H, dofs, kappa_n, R, vals, kappa_out, loading, tangent);
-    if (H.opt.precision != GD_FP64)
-        return fail(&H, GD_ERR_ARG, "mixed precision assembly is not built into this library");
-    GD_CUDA(&H, gd::launch_assemble_fp64(H.dim, a, H.num_sms, H.stream));
+    if (H.opt.precision == GD_FP64) GD_CUDA(&H, gd::launch_assemble_fp64(H.dim, a, H.num_sms, H.stream));
+    else GD_CUDA(&H, gd::launch_assemble_fp32(H.dim, a, H.num_sms, H.stream));
     ++H.launches;
     GD_CUDA(&H, cudaEventRecord(H.ev1, H.stream));
     ++H.assemblies;
@@ -180,6 +181,41 @@ gd_status norms(gd::Handle &H, const double *R, NormPair &out)
     return GD_OK;
 }
 
+// K x = b with the persistent Krylov kernel on `vals`; timing accumulated in H.krylov_ms
+gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, int &iters, double &rel,
+                 double rtol)
+{
+    gd::KrylovCtx kc;
+    kc.n_nodes = H.n_nodes;
+    kc.ndof = H.ndof;
+    kc.rowptr = H.rowptr;
+    kc.colidx = H.colidx;
+    kc.fixed = H.fixed;
+    kc.binv = H.binv;
+    for (int k = 0; k < 8; ++k) kc.work[k] = H.kv[k];
+    kc.red = H.red;
+    kc.out = H.scal + 24;
+    kc.stream = H.stream;
+    kc.blocks = H.krylov_grid;
+    kc.num_sms = H.num_sms;
+    GD_CUDA(&H, cudaEventRecord(H.kv0, H.stream));
+    GD_CUDA(&H, gd::krylov_solve(kc, vals, H.opt.precision == GD_MIXED, b, x, rtol, H.opt.krylov_max));
+    H.launches += 2;
+    GD_CUDA(&H, cudaEventRecord(H.kv1, H.stream));
+    double kout[3];
+    GD_CUDA(&H, cudaMemcpyAsync(kout, H.scal + 24, 3 * sizeof(double), cudaMemcpyDeviceToHost, H.stream));
+    GD_CUDA(&H, cudaStreamSynchronize(H.stream));
+    float kms = 0.0f;
+    cudaEventElapsedTime(&kms, H.kv0, H.kv1);
+    H.krylov_ms += kms;
+    iters = (int)kout[0];
+    rel = kout[1];
+    if (kout[2] != 0.0)
+        return fail(&H, GD_ERR_KRYLOV, "BiCGStab stopped (status " + std::to_string((int)kout[2]) +
+                                           ", relative residual " + std::to_string(rel) + ")");
+    return GD_OK;
+}
+
 // Newton iteration for one load value starting from H.w_dofs (already predicted,
 // prescribed dofs set).  On return H.w_dofs/H.R/H.kappa_trial hold the last iterate.
 gd_status newton(gd::Handle &H, gd_newton_report &rep)
@@ -197,8 +233,6 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
     rep.residual0 = nrm;
     rep.local_failures = hc[0];
     rep.loading_points = hc[1];
-    double *work[8];
-    for (int k = 0; k < 8; ++k) work[k] = H.kv[k];
     double *delta = H.kv[8], *rhs = H.kv[9];
     for (int it = 0; it <= H.opt.newton_max; ++it) {
         rep.iterations = it;
@@ -209,30 +243,19 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
             return GD_OK;
         }
         if (it == H.opt.newton_max) break;
-        // K delta = -R on the free dofs
+        // K delta = -R on the free dofs (one persistent cooperative launch)
         gd::SolverCtx c = solver_ctx(H, H.vals);
-        GD_CUDA(&H, gd::launch_jacobi_diag(c, H.diag));
         GD_CUDA(&H, cudaMemsetAsync(rhs, 0, sizeof(double) * H.n_dofs, H.stream));
         GD_CUDA(&H, gd::launch_axpy_free(c, rhs, H.R, -1.0));
-        cudaEvent_t k0, k1;
-        cudaEventCreate(&k0);
-        cudaEventCreate(&k1);
-        cudaEventRecord(k0, H.stream);
+        // inexact Newton: the linear solve only needs to reach a tenth of the Newton
+        // tolerance relative to the current residual (floor krylov_rtol, cap 1e-2)
+        const double ntol = std::max(H.opt.newton_rtol * r0, H.opt.newton_atol);
+        const double eta = std::min(1e-2, std::max(H.opt.krylov_rtol, 0.1 * ntol / nrm));
+        int kit = 0;
         double rel = 0.0;
-        int kit = gd::bicgstab(c, H.diag, rhs, delta, work, H.opt.krylov_rtol, H.opt.krylov_max, &rel);
-        cudaEventRecord(k1, H.stream);
-        cudaEventSynchronize(k1);
-        float kms = 0.0f;
-        cudaEventElapsedTime(&kms, k0, k1);
-        cudaEventDestroy(k0);
-        cudaEventDestroy(k1);
-        H.krylov_ms += kms;
-        if (kit < 0) {
-            rep.krylov_iterations += H.opt.krylov_max;
-            return fail(&H, GD_ERR_KRYLOV, "BiCGStab did not reach the tolerance (relative residual " +
-                                               std::to_string(rel) + ")");
-        }
+        st = krylov(H, H.vals, rhs, delta, kit, rel, eta);
         rep.krylov_iterations += kit;
+        if (st) return st;
         // backtracking line search on ||R_free||
         double alpha = 1.0, nt = 0.0;
         for (int ls = 0; ls <= H.opt.line_search_max; ++ls) {
@@ -492,8 +515,11 @@ static gd_status stage_net(gd::Handle &H, gd::DevNet &d, int n_in, int w, const 
     if (w == 0) return GD_OK;
     GD_CUDA(&H, dalloc(&d.p, d.n_params));
     GD_CUDA(&H, dalloc(&d.W2T, (size_t)w * w));
+    GD_CUDA(&H, dalloc(&d.pf, d.n_params));
+    GD_CUDA(&H, dalloc(&d.W2Tf, (size_t)w * w));
     GD_CUDA(&H, cudaMemcpyAsync(d.p, params, sizeof(double) * d.n_params, cudaMemcpyDefault, H.stream));
     GD_CUDA(&H, gd::launch_transpose(d, H.stream));
+    GD_CUDA(&H, gd::launch_net_to_float(d, H.stream));
     return GD_OK;
 }
 
@@ -513,6 +539,8 @@ gd_status gd_create(const gd_mesh *mesh, const gd_icnn *psi, const gd_icnn *yiel
     if (opt) o = *opt;
     else gd_default_options(&o);
     if (o.precision != GD_FP64 && o.precision != GD_MIXED) return fail(nullptr, GD_ERR_ARG, "precision");
+    // FP32 element math resolves the residual to ~1e-6 of its scale
+    if (o.precision == GD_MIXED && o.newton_rtol < 1e-6) o.newton_rtol = 1e-6;
     if (o.newton_max < 0 || o.krylov_max < 1 || o.local_max < 1 || o.line_search_max < 0)
         return fail(nullptr, GD_ERR_ARG, "iteration caps");
 
@@ -570,6 +598,8 @@ gd_status gd_create(const gd_mesh *mesh, const gd_icnn *psi, const gd_icnn *yiel
     GD_CREATE_CUDA(cudaDeviceGetAttribute(&H.num_sms, cudaDevAttrMultiProcessorCount, dev));
     GD_CREATE_CUDA(cudaEventCreate(&H.ev0));
     GD_CREATE_CUDA(cudaEventCreate(&H.ev1));
+    GD_CREATE_CUDA(cudaEventCreate(&H.kv0));
+    GD_CREATE_CUDA(cudaEventCreate(&H.kv1));
     GD_CREATE_CUDA(dalloc(&H.X, (size_t)(NN * dim)));
     GD_CREATE_CUDA(dalloc(&H.conn, (size_t)(NE * nen)));
     GD_CREATE_CUDA(dalloc(&H.slot, slot.size()));
@@ -614,6 +644,12 @@ gd_status gd_create(const gd_mesh *mesh, const gd_icnn *psi, const gd_icnn *yiel
     GD_CREATE_CUDA(dalloc(&H.vals, (size_t)nnz));
     GD_CREATE_CUDA(dalloc(&H.vals_trial, (size_t)nnz));
     GD_CREATE_CUDA(dalloc(&H.counters, 8));
+    GD_CREATE_CUDA(dalloc(&H.binv, (size_t)(NN * ndof * ndof)));
+    H.krylov_grid = gd::krylov_blocks(ndof, o.precision == GD_MIXED, H.num_sms);
+    if (H.krylov_grid < 1) {
+        H.err = "no cooperative grid fits on this device";
+        return bail(GD_ERR_CUDA);
+    }
     H.red_blocks = 2 * H.num_sms;
     GD_CREATE_CUDA(dalloc(&H.red, (size_t)8 * H.red_blocks));
     GD_CREATE_CUDA(dalloc(&H.scal, 64));
@@ -647,10 +683,12 @@ gd_status gd_set_params(gd_handle *h, const double *theta_psi, const double *the
     if (theta_psi && H.psi.width > 0) {
         GD_CUDA(&H, cudaMemcpyAsync(H.psi.p, theta_psi, sizeof(double) * H.psi.n_params, cudaMemcpyDefault, H.stream));
         GD_CUDA(&H, gd::launch_transpose(H.psi, H.stream));
+        GD_CUDA(&H, gd::launch_net_to_float(H.psi, H.stream));
     }
     if (theta_yield && H.yld.width > 0) {
         GD_CUDA(&H, cudaMemcpyAsync(H.yld.p, theta_yield, sizeof(double) * H.yld.n_params, cudaMemcpyDefault, H.stream));
         GD_CUDA(&H, gd::launch_transpose(H.yld, H.stream));
+        GD_CUDA(&H, gd::launch_net_to_float(H.yld, H.stream));
     }
     GD_CUDA(&H, gd::launch_prep_nets(H.psi, H.yld, H.mat.energy, H.netc, H.stream));
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));
@@ -694,6 +732,20 @@ gd_status gd_spmv(gd_handle *h, const double *x, double *y, int32_t free_only)
     gd::SolverCtx c = solver_ctx(H, H.vals);
     GD_CUDA(&H, gd::launch_spmv(c, x, y, free_only));
     return GD_OK;
+}
+
+gd_status gd_solve(gd_handle *h, const void *csr_vals, const double *b, double *x, int32_t *iterations,
+                   double *rel_residual)
+{
+    if (!h) return fail(nullptr, GD_ERR_ARG, "null handle");
+    gd::Handle &H = h->h;
+    if (!b || !x) return fail(&H, GD_ERR_ARG, "null vector");
+    int it = 0;
+    double rel = 0.0;
+    gd_status st = krylov(H, csr_vals ? csr_vals : H.vals, b, x, it, rel, H.opt.krylov_rtol);
+    if (iterations) *iterations = it;
+    if (rel_residual) *rel_residual = rel;
+    return st;
 }
 
 gd_status gd_newton_step(gd_handle *h, gd_newton_report *rep)

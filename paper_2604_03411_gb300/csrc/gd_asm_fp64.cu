@@ -883,6 +883,23 @@ cudaError_t launch_prep_nets(const DevNet &psi, const DevNet &yld, int energy, N
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void to_float_kernel(const double *in, float *out, int n)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = (float)in[t];
+}
+}  // namespace
+
+cudaError_t launch_net_to_float(const DevNet &net, cudaStream_t s)
+{
+    if (net.width <= 0) return cudaSuccess;
+    to_float_kernel<<<(net.n_params + 255) / 256, 256, 0, s>>>(net.p, net.pf, net.n_params);
+    const int ww = net.width * net.width;
+    to_float_kernel<<<(ww + 255) / 256, 256, 0, s>>>(net.W2T, net.W2Tf, ww);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_transpose(const DevNet &net, cudaStream_t s)
 {
     if (net.width <= 0) return cudaSuccess;

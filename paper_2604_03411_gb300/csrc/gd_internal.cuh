@@ -29,6 +29,8 @@ struct DevNet {
     int n_in = 0, width = 0, n_params = 0;
     double *p = nullptr;     // [n_params]
     double *W2T = nullptr;   // [width * width], W2T[j * w + k] = W2[k * w + j]
+    float *pf = nullptr;     // FP32 copies for the mixed-precision kernel
+    float *W2Tf = nullptr;
 };
 
 struct MatConst {
@@ -99,11 +101,13 @@ struct Handle {
     // Krylov workspace (FP64 vectors of n_dofs)
     double *kv[10] = {};
     double *diag = nullptr;
+    double *binv = nullptr;                              // node-block Jacobi inverses
+    int krylov_grid = 0;
     double *red = nullptr;                               // device reduction buffers
     double *scal = nullptr;                              // device scalars
     int red_blocks = 0;
     // timing
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, kv0 = nullptr, kv1 = nullptr;
     double assembly_ms = 0.0, krylov_ms = 0.0;
     int assemblies = 0;
     long long launches = 0;                              // kernels launched by this handle
@@ -115,6 +119,9 @@ struct Handle {
 cudaError_t launch_prep_nets(const DevNet &psi, const DevNet &yld, int energy, NetConst *out, cudaStream_t s);
 cudaError_t launch_transpose(const DevNet &net, cudaStream_t s);
 cudaError_t launch_assemble_fp64(int dim, const AsmArgs &a, int num_sms, cudaStream_t s);
+cudaError_t launch_assemble_fp32(int dim, const AsmArgs &a, int num_sms, cudaStream_t s);
+// FP32 copies of a network's parameters and transposed W2
+cudaError_t launch_net_to_float(const DevNet &net, cudaStream_t s);
 
 // solver kernels (gd_solver.cu)
 struct SolverCtx {
@@ -147,5 +154,24 @@ cudaError_t launch_reaction(const double *R, const int32_t *react_dof, int64_t n
                             cudaStream_t s);
 cudaError_t launch_damage_max(const double *kappa, int64_t n, double eta_d, double kappa_d, double *out,
                               cudaStream_t s);
+
+// persistent cooperative Krylov solve (gd_krylov.cu)
+struct KrylovCtx {
+    int64_t n_nodes;
+    int ndof;
+    const int32_t *rowptr, *colidx;
+    const uint8_t *fixed;
+    double *binv;               // [n_nodes * ndof * ndof]
+    double *work[8];            // [n_nodes * ndof] each
+    double *red;                // [8 * blocks]
+    double *out;                // [3] device: iterations, relative residual, status
+    cudaStream_t stream;
+    int blocks;                 // cooperative grid size (all blocks co-resident)
+    int num_sms;
+};
+int krylov_blocks(int ndof, bool fp32_vals, int num_sms);
+// Solves K x = b on the free dofs; the result and statistics land in x and c.out.
+cudaError_t krylov_solve(const KrylovCtx &c, const void *vals, bool fp32_vals, const double *b, double *x,
+                         double rtol, int max_it);
 
 }  // namespace gd

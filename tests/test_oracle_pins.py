@@ -455,3 +455,66 @@ def test_single_hex8_element_sec51():
             fd = np.exp(-case["eta_d"] * max(kmax - case["kappa_d"], 0.0))
             assert abs(res["reaction"][s] - fd * P11) <= 1e-8 * abs(P11)
             np.testing.assert_allclose(res["states"][s][1], kmax, rtol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# FE patch test on distorted elements, analytic non-local field
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dim", [2, 3])
+def test_patch_test_distorted_mesh(dim):
+    """Isoparametric patch test: on a mesh with perturbed interior nodes, a linear
+    displacement field u = G X with uniform phi = kappa gives a uniform stress, so
+    every displacement row of an interior node has zero residual (the Gauss rules
+    integrate grad N_a det J exactly for Q4 and HEX8)."""
+    rng = np.random.default_rng(21)
+    mesh = I.structured_q4(3, 3) if dim == 2 else I.structured_hex8(2, 2, 2)
+    X = mesh.coords.copy()
+    inner = np.all((X > 1e-9) & (X < 1 - 1e-9), axis=1)
+    X[inner] += 0.12 * rng.uniform(-1, 1, (inner.sum(), dim))
+    mesh.coords = X
+    m, _, _ = model_for(I.ENERGY_ICNN_RAW, seed=3, w=16, dim=dim, kappa_d=1000.0, gamma_d=0.0)
+    G = 0.08 * rng.standard_normal((dim, dim))
+    d = np.zeros((mesh.n_nodes, dim + 1))
+    d[:, :dim] = X @ G.T
+    d[:, dim] = 50.0
+    kappa = np.full((mesh.n_elems, mesh.nq), 50.0)
+    R, _, k1, qi, _ = m.assemble(mesh, d, kappa, tangent=False)
+    assert np.all(qi[..., 5] == 0)
+    Rn = R.reshape(-1, dim + 1)
+    scale = np.abs(Rn[~inner, :dim]).max()
+    assert scale > 1e-3
+    assert np.abs(Rn[inner, :dim]).max() <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("stretch", [1.0, 1.5])
+def test_nonlocal_field_matches_analytic_solution(stretch):
+    """With the displacement prescribed as a uniform stretch lam along x and an
+    elastic history kappa_n(x) = k0 + A cos(pi x / L), the non-local equation of
+    Sec. 2.1 (grad-energy c_d/2 gradphi.C^-1.gradphi, penalty beta_d/2 (phi-kappa)^2,
+    zero flux on the boundary) reduces to -(c_d/lam^2) phi'' + beta_d (phi - kappa) = 0,
+    whose solution is phi = k0 + A cos(pi x/L) / (1 + c_d pi^2 / (beta_d lam^2 L^2))."""
+    n = 64
+    mesh = I.structured_q4(n, 2, 1.0, 0.05)
+    x = mesh.coords[:, 0]
+    nodes = np.repeat(np.arange(mesh.n_nodes, dtype=np.int32), 2)
+    comps = np.tile(np.array([0, 1], np.int8), mesh.n_nodes)
+    scale = np.where(comps == 0, (stretch - 1.0) * x[nodes], 0.0)
+    mesh.bc_node, mesh.bc_comp, mesh.bc_scale = nodes, comps, scale
+    mesh.react_node = np.zeros(0, np.int32)
+    psi, _ = I.icnn_pair(2, 16, 8)
+    c_d, beta = 0.05, 10.0
+    mat = I.Material(c_d=c_d, beta_d=beta, gamma_d=0.0, kappa_d=1000.0)
+    m = oracle.Model(2, mat, psi.params, 16, np.zeros(1), 0)
+    k0, A = 100.0, 0.5
+    h = 1.0 / n
+    gp = 1.0 / np.sqrt(3.0)
+    ei = np.arange(mesh.n_elems) % n
+    xq = np.stack([ei * h + h * (1 + s) / 2 for s in (-gp, gp, -gp, gp)], axis=1)
+    kappa = k0 + A * np.cos(np.pi * xq)
+    d0 = np.zeros(mesh.n_nodes * 3)
+    d0[2::3] = k0
+    dofs, k1, res, R = oracle.newton_step(m, mesh, d0, kappa, 1.0, rtol=1e-13, atol=1e-13)
+    assert res.converged and np.array_equal(k1, kappa)
+    phi = dofs.reshape(-1, 3)[:, 2]
+    exact = k0 + A * np.cos(np.pi * x) / (1.0 + c_d * np.pi ** 2 / (beta * stretch ** 2))
+    assert np.abs(phi - exact).max() < 3e-4
