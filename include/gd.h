@@ -115,7 +115,7 @@ typedef struct gd_load_path {
 typedef struct gd_options {
     int32_t precision;         /* GD_FP64 or GD_MIXED                                  */
     double newton_rtol;        /* ||R_free|| <= max(rtol max(||R0_free||, ||R_fixed||), atol);
-                                  raised to 1e-6 in GD_MIXED (FP32 element math)          */
+                                  raised to 1e-5 in GD_MIXED (FP32 element math)          */
     double newton_atol;
     int32_t newton_max;        /* Newton iterations per step                           */
     int32_t line_search_max;   /* backtracking halvings per Newton direction           */

@@ -539,8 +539,8 @@ gd_status gd_create(const gd_mesh *mesh, const gd_icnn *psi, const gd_icnn *yiel
     if (opt) o = *opt;
     else gd_default_options(&o);
     if (o.precision != GD_FP64 && o.precision != GD_MIXED) return fail(nullptr, GD_ERR_ARG, "precision");
-    // FP32 element math resolves the residual to ~1e-6 of its scale
-    if (o.precision == GD_MIXED && o.newton_rtol < 1e-6) o.newton_rtol = 1e-6;
+    // FP32 element math resolves the residual to ~1e-5 of its scale
+    if (o.precision == GD_MIXED && o.newton_rtol < 1e-5) o.newton_rtol = 1e-5;
     if (o.newton_max < 0 || o.krylov_max < 1 || o.local_max < 1 || o.line_search_max < 0)
         return fail(nullptr, GD_ERR_ARG, "iteration caps");
 
