@@ -227,6 +227,34 @@ gd_status gd_spmv(gd_handle *h, const double *x, double *y, int32_t free_only);
 gd_status gd_solve(gd_handle *h, const void *csr_vals, const double *b, double *x, int32_t *iterations,
                    double *rel_residual);
 
+/* Largest system (n_nodes * ndof) that gd_solve_noalloc accepts. */
+#define GD_NOALLOC_MAX_DOFS 131072
+
+/* Krylov solve that allocates no device memory (the paper has no counterpart;
+ * this exists for callers that cannot call cudaMalloc -- code that runs while a
+ * CUDA graph is being captured, applications whose own pool owns the device
+ * memory, runtimes that forbid allocation after start-up).
+ * Solves K x = b on the free dofs of a caller-provided node-block CSR system
+ * (the layout of gd_csr_pattern, ndof 3 or 4, FP64 values) with the same
+ * node-block-Jacobi BiCGStab as gd_solve.  All arrays are device pointers owned
+ * by the caller: rowptr [n_nodes*ndof + 1], colidx, vals [nnz], fixed
+ * [n_nodes*ndof] (1 = prescribed dof), b, x [n_nodes*ndof]; prescribed dofs of x
+ * come back as 0.  iterations and rel_residual (host, may be NULL) report the
+ * solve.  Work runs on `stream` (a cudaStream_t, NULL for the legacy default
+ * stream), which the call synchronises.
+ * Work space: one fixed device array inside the library, sized for
+ * GD_NOALLOC_MAX_DOFS dofs (about 12.6 MB), held by every GPU that loads the
+ * library until the process exits; larger systems are rejected with GD_ERR_ARG.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every call
+ * on a device shares the one array and rewrites all of it that it reads, so
+ * calls that overlap on the GPU (other streams, other host threads) race: run
+ * them one after another.  Errors: GD_ERR_ARG, GD_ERR_CUDA, GD_ERR_KRYLOV; the
+ * message is available from gd_last_error(NULL) on the calling thread. */
+gd_status gd_solve_noalloc(int32_t ndof, int64_t n_nodes, const int32_t *rowptr, const int32_t *colidx,
+                           const double *vals, const uint8_t *fixed, const double *b, double *x, double rtol,
+                           int32_t max_it, void *stream, int32_t *iterations, double *rel_residual);
+
 /* Advances the next load step of the path to convergence (monolithic Newton,
  * Sec. 3.2, with a line search and nested step halving on failure); commits
  * kappa and the fields on success.  rep may be NULL. */

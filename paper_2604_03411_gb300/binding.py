@@ -23,6 +23,7 @@ STATUS = {0: "GD_OK", 1: "GD_ERR_ARG", 2: "GD_ERR_MESH", 3: "GD_ERR_CUDA", 4: "G
           9: "GD_ERR_TIMEOUT", 10: "GD_ERR_STATE"}
 GD_FP64, GD_MIXED = 0, 1
 GD_ASM_RESIDUAL, GD_ASM_TANGENT = 0, 1
+GD_NOALLOC_MAX_DOFS = 131072
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -91,6 +92,10 @@ PROTOTYPES = {
     "gd_spmv": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "gd_solve": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
                                 _dp]),
+    "gd_solve_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_double, ctypes.c_int32, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_int32), _dp]),
     "gd_newton_step": (ctypes.c_int, [_H, ctypes.POINTER(GdNewtonReport)]),
     "gd_run_load_path": (ctypes.c_int, [_H, _dp, ctypes.POINTER(GdPathReport)]),
     "gd_backward": (ctypes.c_int, [_H, _dp, _dp]),
@@ -265,6 +270,17 @@ def gd_solve(h: Handle, b, x, csr_vals=None):
     it = ctypes.c_int32()
     rel = ctypes.c_double()
     _check(lib().gd_solve(h.ptr, _dptr(csr_vals), _dptr(b), _dptr(x), ctypes.byref(it), ctypes.byref(rel)), h.ptr)
+    return it.value, rel.value
+
+
+def gd_solve_noalloc(ndof, n_nodes, rowptr, colidx, vals, fixed, b, x, rtol, max_it, stream=None):
+    """All arrays are contiguous CUDA tensors; returns (iterations, relative residual)."""
+    it = ctypes.c_int32()
+    rel = ctypes.c_double()
+    st = lib().gd_solve_noalloc(int(ndof), int(n_nodes), _dptr(rowptr), _dptr(colidx), _dptr(vals), _dptr(fixed),
+                                _dptr(b), _dptr(x), float(rtol), int(max_it), stream, ctypes.byref(it),
+                                ctypes.byref(rel))
+    _check(st, None)
     return it.value, rel.value
 
 

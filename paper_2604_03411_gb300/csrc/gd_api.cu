@@ -465,6 +465,12 @@ gd_status build_pattern(const gd_mesh *mesh, Pattern &P)
 
 }  // namespace
 
+gd_status gd::set_error(gd_status st, const std::string &msg)
+{
+    g_create_error = msg;
+    return st;
+}
+
 extern "C" {
 
 void gd_default_options(gd_options *o)

@@ -115,6 +115,9 @@ struct Handle {
     int num_sms = 0;
 };
 
+// records a message for gd_last_error(NULL) on this thread and returns st
+gd_status set_error(gd_status st, const std::string &msg);
+
 // launchers (return the launch status)
 cudaError_t launch_prep_nets(const DevNet &psi, const DevNet &yld, int energy, NetConst *out, cudaStream_t s);
 cudaError_t launch_transpose(const DevNet &net, cudaStream_t s);
