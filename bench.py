@@ -6,18 +6,24 @@ is one quasi-static load step of the monolithic scheme: Newton iterations, each
 an element-kernel pass (kinematics, ICNN energy with derivatives, yield network
 and local damage update, degraded stress, residual and consistent tangent,
 CSR scatter), the residual norms, a Jacobi-preconditioned BiCGStab solve and a
-backtracking line search.  value = (#qp x element-kernel passes in the timed
-steps) / (timed device time): whole-step throughput, inputs resident in HBM.
+backtracking line search.  value = (#qp x Newton iterates in the timed steps) /
+(timed device time), an iterate being the first pass of a (sub)step or the
+accepted pass of a Newton direction: whole-step throughput, inputs resident in
+HBM.  Rejected line-search trials are timed but not counted.
 
 Workloads (synthetic, seeded; see paper_2604_03411_gb300/inputs.py):
   notched   2D notched plate 2:1, graded Q4 mesh of 39,936 elements (159,744 qp),
             both ICNNs width 32, 50 steps to 60% nominal strain, FP64 (default)
   cube      3D cube, 64^3 HEX8 (2,097,152 qp), biaxial, both ICNNs width 64
   square    2D 8x8 Q4 square, load-unload-reload
+  batch     96 independent Q4 specimens (16..96 x 16..48 elements, widths 16/24/32,
+            20..60 steps each) in one batched handle, mixed precision; under
+            torchrun the specimens are split across the ranks (strong scaling)
 
 Multi-GPU: one process per GPU under torchrun; a single mesh does not shard, so
 every rank runs an independent replica of the workload (weak scaling) and
-value sums the ranks' qp updates over the slowest rank's time.
+value sums the ranks' qp updates over the slowest rank's time.  The batch
+workload shards its specimens instead (no collective on the data path).
 
 --impl reference times the FP64 CPU oracle (the project's reference
 implementation of the method) on a bounded sample of the same workload.
@@ -40,6 +46,7 @@ METRIC = "qp constitutive+assembly updates/s & Newton-step ms, mixed vs FP64, 1 
 UNIT = "qp-updates/s"
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 FP64_PEAK_TFLOPS_NOMINAL = 1.25     # GB300 dense FP64 (nominal, the recipe's table)
+FP32_PEAK_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: SMs x FP32 lanes x FMA x max clock
 
 
 def parse():
@@ -48,15 +55,28 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gd", choices=["gd", "reference"])
-    ap.add_argument("--workload", default="notched", choices=["notched", "cube", "square"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="notched", choices=["notched", "cube", "square", "batch"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
+                    help="default: fp64 (mixed for the batch workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--inner", default="auto", choices=["auto", "fp64", "refined"],
+                    help="Newton inner-solve policy (gd_options.inner_solve)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
 
-def make_workload(name):
+def make_workload(name, rank=0, world=1):
     from paper_2604_03411_gb300 import inputs as I
+    if name == "batch":
+        from paper_2604_03411_gb300 import shard
+        allp = I.config5()
+        mine = shard.shard(allp, rank, world)
+        ps = [allp[i] for i in mine]
+        desc = {"workload": "batch_96_specimens_q4", "specimens": len(allp), "specimens_this_rank": len(ps),
+                "elements": sum(p.mesh.n_elems for p in ps), "qp": sum(p.mesh.n_elems * 4 for p in ps),
+                "dofs": sum(p.mesh.n_nodes * 3 for p in ps), "icnn_width": "16/24/32 per specimen",
+                "load_steps": "20..60 per specimen", "length_scale": 0.1}
+        return ps, desc
     if name == "notched":
         p = I.config2()
         desc = {"workload": "notched_plate_q4", "elements": p.mesh.n_elems, "qp": p.mesh.n_elems * 4,
@@ -155,6 +175,9 @@ def run_reference(args):
     if rank != 0:
         return 0
     prob, desc = make_workload(args.workload)
+    if isinstance(prob, list):
+        prob = max(prob, key=lambda p: p.mesh.n_elems)
+        desc = dict(desc, oracle_sample="largest specimen")
     vals = []
     per_step = max(1.0, 120.0 / max(1, args.steps + args.warmup))
     for k in range(args.warmup + args.steps):
@@ -187,19 +210,26 @@ def run_gd(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build_mod.build()
-    prob, desc = make_workload(args.workload)
+    prob, desc = make_workload(args.workload, rank, world)
+    batch = isinstance(prob, list)
+    if args.precision is None:
+        args.precision = "mixed" if batch else "fp64"
     stream = torch.cuda.current_stream()
     prec = B.GD_FP64 if args.precision == "fp64" else B.GD_MIXED
-    opts = B.gd_default_options(precision=prec, cuda_stream=stream.cuda_stream)
-    h = B.gd_create(prob, opts)
+    opts = B.gd_default_options(precision=prec, cuda_stream=stream.cuda_stream, inner_solve={"auto": B.GD_INNER_AUTO, "fp64": B.GD_INNER_FP64,
+                                             "refined": B.GD_INNER_REFINED}[args.inner])
+    h = B.gd_create_batch(prob, opts) if batch else B.gd_create(prob, opts)
+    probs = prob if batch else [prob]
     n_qp = desc["qp"]
-    n_path = int(prob.load.size)
+    n_path = h.meta["n_steps"]
+    n_nodes_all = sum(p.mesh.n_nodes for p in probs)
+    n_elems_all = sum(p.mesh.n_elems for p in probs)
+    mesh0 = probs[0].mesh
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def step(k):
         if h_state["next"] >= n_path:          # restart the path when it runs out
-            B.gd_set_state(h, np.zeros(prob.mesh.n_nodes * prob.mesh.ndof),
-                           np.zeros((prob.mesh.n_elems, prob.mesh.nq)), 0)
+            B.gd_set_state(h, np.zeros(n_nodes_all * mesh0.ndof), np.zeros((n_elems_all, mesh0.nq)), 0)
             h_state["next"] = 0
         r = B.gd_newton_step(h)
         h_state["next"] += 1
@@ -225,7 +255,11 @@ def run_gd(args):
     clk = clocks.stop()
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
     asm = sum(r.assemblies for r in reps)
-    units = n_qp * asm
+    # qp updates counted per Newton iterate: the first pass of every attempted (sub)step
+    # plus the accepted pass of every direction; rejected line-search trials and the
+    # mixed mode's FP64 noise pass are work, not progress, and are left out
+    useful = sum(r.iterations + 1 + 2 * r.step_cuts for r in reps)
+    units = n_qp * useful
     if dist:
         t = torch.tensor([total_ms, float(units)], dtype=torch.float64, device="cuda")
         tm = t.clone()
@@ -241,49 +275,49 @@ def run_gd(args):
     kry_ms = sum(r.krylov_ms for r in reps)
     launches = sum(r.kernel_launches for r in reps)
 
-    # --- dominant-kernel roofline: SpMV of the Krylov loop vs the element kernel ---
-    n_dofs = prob.mesh.n_nodes * prob.mesh.ndof
+    # --- dominant-kernel roofline: persistent Krylov kernel vs the element kernel ---
+    # both durations come from CUDA events the library records on its stream around
+    # each launch inside the timed steps
+    n_dofs = n_nodes_all * mesh0.ndof
     rowptr, colidx = B.gd_csr_pattern(h)
     nnz = colidx.size
-    x = torch.randn(n_dofs, dtype=torch.float64, device="cuda")
-    y = torch.empty_like(x)
-    for _ in range(3):
-        B.gd_spmv(h, x, y, 1)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps_spmv = 50
-    e0.record(stream)
-    for _ in range(reps_spmv):
-        B.gd_spmv(h, x, y, 1)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    spmv_ms = e0.elapsed_time(e1) / reps_spmv
-    ndof = prob.mesh.ndof
-    # algorithmic bytes of one SpMV: every value once (FP64), the column list once per
-    # node (the ndof rows of a node share it), row pointers, x gathered once per
-    # column-list entry's node block (counted once per dof), y written, prescribed mask
-    spmv_bytes = nnz * 8 + (nnz // ndof) * 4 + (prob.mesh.n_nodes + 1) * 4 * 2 + n_dofs * (8 + 8 + 1)
-    spmv_total = 2 * krylov * spmv_ms
+    ndof = mesh0.ndof
     peak_bw, peak_kind = measured_peaks()
     asm_avg = asm_ms / max(asm, 1)
-    if spmv_total >= asm_ms:
-        achieved = spmv_bytes / (spmv_ms / 1e3) / 1e9
-        roof = {"kernel": "spmv_kernel (CSR SpMV of the Krylov loop)", "bound": "hbm", "achieved": achieved,
-                "peak": peak_bw, "unit": "GB/s", "frac": achieved / peak_bw, "traffic": None,
-                "peak_source": f"{peak_kind} copy bandwidth", "avg_launch_us": spmv_ms * 1e3,
-                "algorithmic_bytes_per_launch": spmv_bytes,
-                "note": "the matrix (%.0f MB) is L2-resident across Krylov iterations" % (spmv_bytes / 1e6)}
+    solves = max(newton, 1)
+    kry_avg = kry_ms / solves
+    iters_per_solve = krylov / solves
+    # algorithmic bytes of one BiCGStab iteration on the FP32 inner system: two SpMVs
+    # (values, the column list once per node block, row pointers, gathered x, y) and
+    # the vector phases (p, y, s, z, x, r updates: 15 vector reads/writes), 4-byte data
+    spmv_b = nnz * 4 + (nnz // ndof) * 4 + (n_nodes_all + 1) * 4 * 2 + n_dofs * (4 + 4 + 1)
+    iter_b = 2 * spmv_b + 15 * n_dofs * 4
+    if kry_ms >= asm_ms:
+        bytes_launch = iter_b * iters_per_solve
+        achieved = bytes_launch / (kry_avg / 1e3) / 1e9
+        roof = {"kernel": "bicgstab_kernel (persistent Krylov solve of one Newton system)", "bound": "hbm",
+                "achieved": achieved, "peak": peak_bw, "unit": "GB/s", "frac": achieved / peak_bw, "traffic": None,
+                "peak_source": f"{peak_kind} copy bandwidth", "avg_launch_ms": kry_avg,
+                "algorithmic_bytes_per_launch": bytes_launch, "iterations_per_launch": iters_per_solve,
+                "note": "the FP32 inner system (%.0f MB) stays L2-resident across the iterations of a launch"
+                        % (spmv_b / 1e6)}
     else:
-        # FP64 ALU bound element kernel: algorithmic FP64 FLOPs (FMA = 2) of the dense parts
-        wp, wy = desc["icnn_width"]
-        nq = prob.mesh.nq
-        nd = prob.mesh.nen * ndof
+        # element kernel: FP64 (or FP32) ALU bound; algorithmic FLOPs (FMA = 2) of the dense parts
+        nq = mesh0.nq
+        nd = mesh0.nen * ndof
         evals = sum(r.yield_evals for r in reps)
-        flops = (n_qp * asm * (10 * wp * wp + 40 * wp) + evals * (4 * wy * wy + 20 * wy)
-                 + (asm * prob.mesh.n_elems) * nd * nd * nq * 25)
+        # per pass: energy network with tangents at every qp, element tangent; the yield
+        # network per local-solve evaluation (qp-weighted mean width over specimens)
+        psi_f = sum(p.mesh.n_elems * nq * (10 * p.psi.width ** 2 + 40 * p.psi.width) for p in probs)
+        wy = sum(p.mesh.n_elems * p.yld.width for p in probs) / max(n_elems_all, 1)
+        flops = asm * psi_f + evals * (4 * wy * wy + 20 * wy) + (asm * n_elems_all) * nd * nd * nq * 25
         achieved = flops / (asm_ms / 1e3) / 1e12
-        roof = {"kernel": "asm_fp64_kernel (element kernel)", "bound": "alu", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS_NOMINAL,
-                "traffic": None, "peak_source": "nominal FP64 rate", "avg_launch_us": asm_avg * 1e3}
+        peak = FP64_PEAK_TFLOPS_NOMINAL if prec == B.GD_FP64 else FP32_PEAK_TFLOPS_NOMINAL
+        roof = {"kernel": "element kernel (asm_fp64_kernel)" if prec == B.GD_FP64 else "element kernel (asm_fp32_kernel)",
+                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": "nominal FP64 rate" if prec == B.GD_FP64 else
+                "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "avg_launch_ms": asm_avg,
+                "algorithmic_flops_per_launch": flops / max(asm, 1)}
 
     # --- end to end through the C ABI with host buffers ---
     d_host, k_host = B.gd_get_fields(h)
@@ -301,7 +335,7 @@ def run_gd(args):
         r = B.gd_newton_step(h)
         d_out, k_out = B.gd_get_fields(h)                # device -> host
         e2e_ms += (time.perf_counter() - t0) * 1e3
-        e2e_units += n_qp * r.assemblies
+        e2e_units += n_qp * (r.iterations + 1 + 2 * r.step_cuts)
     h2d = d_host.nbytes + k_host.nbytes
     e2e = {"value": e2e_units / (e2e_ms / 1e3) * (world if world > 1 else 1), "unit": UNIT,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d)}
@@ -309,21 +343,24 @@ def run_gd(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == B.GD_FP64 else "bf16+f32+f64",
+        "scaling": "strong" if batch else "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == B.GD_FP64 else "f32+f64",
         "data": "synthetic (seeded mesh, seeded ICNN weights)",
-        "config": dict(desc, precision=args.precision, parallelism=f"replicas{world}",
+        "config": dict(desc, precision=args.precision,
+                       parallelism=f"specimen-shards{world}" if batch else f"replicas{world}",
+                       inner_solve=args.inner,
                        l2="flushed between timed steps (512 MB write)"),
         "newton_step_ms": total_ms / max(newton, 1),
         "newton_iterations": newton, "krylov_iterations": krylov,
-        "assembly": {"launches": asm, "avg_ms": asm_avg, "qp_per_s": n_qp / (asm_avg / 1e3),
-                     "share_of_step": asm_ms / total_ms},
+        "assembly": {"launches": asm, "counted_passes": useful, "avg_ms": asm_avg,
+                     "qp_per_s": n_qp / (asm_avg / 1e3), "share_of_step": asm_ms / total_ms},
         "krylov_share_of_step": kry_ms / total_ms,
+        "krylov_ms_per_newton": kry_avg, "krylov_iterations_per_newton": iters_per_solve,
+        "krylov_fp32_iterations": sum(r.krylov_fp32_iterations for r in reps),
         "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
-    elif rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(max(probs, key=lambda p: p.mesh.n_elems), args.cpu_seconds)
     if dist:
         dist.barrier()
         dist.destroy_process_group()

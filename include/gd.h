@@ -58,6 +58,7 @@ enum { GD_ENERGY_ICNN_RAW = 0,   /* psi-ICNN of (I1-3, I2-3, J-1)               
 enum { GD_FP64 = 0, GD_MIXED = 1 };
 enum { GD_BICGSTAB = 0, GD_GMRES = 1 };
 enum { GD_ASM_RESIDUAL = 0, GD_ASM_TANGENT = 1 };
+enum { GD_INNER_AUTO = 0, GD_INNER_FP64 = 1, GD_INNER_REFINED = 2 };
 
 /* Mesh and boundary data (Sec. 3.1, Table kernel_inputs; Dirichlet data of the
  * incremental load, Sec. 3.2).
@@ -115,7 +116,9 @@ typedef struct gd_load_path {
 typedef struct gd_options {
     int32_t precision;         /* GD_FP64 or GD_MIXED                                  */
     double newton_rtol;        /* ||R_free|| <= max(rtol max(||R0_free||, ||R_fixed||), atol);
-                                  raised to 1e-5 in GD_MIXED (FP32 element math)          */
+                                  raised to 1e-5 in GD_MIXED (FP32 element math), where an
+                                  iterate whose residual the line search cannot lower any
+                                  more and that is below 1e-4 of that scale is accepted    */
     double newton_atol;
     int32_t newton_max;        /* Newton iterations per step                           */
     int32_t line_search_max;   /* backtracking halvings per Newton direction           */
@@ -129,6 +132,12 @@ typedef struct gd_options {
     int32_t checkpoint_every;  /* adjoint checkpoint interval in load steps            */
     int32_t max_step_cuts;     /* nested load-step halvings after a failed step        */
     void *cuda_stream;         /* cudaStream_t or NULL                                 */
+    int32_t inner_solve;       /* GD_INNER_AUTO (default): FP64 BiCGStab in GD_FP64; in GD_MIXED
+                                  FP32 BiCGStab (FP64 dots) for directions that need at most
+                                  1e-5 relative accuracy, FP64 otherwise.  GD_INNER_FP64: FP64
+                                  BiCGStab always.  GD_INNER_REFINED: FP32 BiCGStab cycles
+                                  refined by FP64 residuals b - K x until the FP64 tolerance
+                                  is met.  A failed FP32 solve falls back to FP64.          */
 } gd_options;
 
 typedef struct gd_newton_report {
@@ -145,6 +154,7 @@ typedef struct gd_newton_report {
     double krylov_ms;          /* device time of the linear solves                      */
     int64_t yield_evals;       /* yield-network evaluations of the local solves (all launches) */
     int64_t kernel_launches;   /* device kernels this library launched for the step     */
+    int32_t krylov_fp32_iterations; /* iterations of FP32 inner solves (the rest ran in FP64) */
 } gd_newton_report;
 
 typedef struct gd_path_report {
@@ -176,6 +186,36 @@ void gd_default_options(gd_options *opt);
 gd_status gd_create(const gd_mesh *mesh, const gd_icnn *psi, const gd_icnn *yield,
                     const gd_material *mat, const gd_load_path *path, const gd_options *opt,
                     gd_handle **out);
+
+/* Batched specimens (many independent problems in one handle): n_spec meshes,
+ * energy networks, yield networks and load paths (arrays of n_spec structs; psi
+ * may be NULL for GD_ENERGY_NEO_HOOKE), one material and one set of options.
+ * The meshes are laid end to end into one block-diagonal system (nodes and
+ * elements of specimen s follow those of specimens 0..s-1), every assembly is a
+ * single persistent launch over the elements of all specimens, each element
+ * reading its own specimen's network weights, and one Newton iteration advances
+ * all specimens together: each specimen has its own convergence test
+ * ||R_free,s|| <= max(rtol max(||R0_free,s||, ||R_fixed,s||), atol) and its own
+ * line-search step, and a converged specimen is held fixed while the others
+ * iterate.  Load step k of the batch takes step k of every path; a specimen whose
+ * path is shorter holds its last load.  A failed step is halved for every
+ * specimen.  The dim, and the widths' upper bound (64), are common; widths may
+ * differ between specimens.  gd_newton_step and gd_run_load_path advance the
+ * batch (reactions [n_steps * n_spec], step-major; see gd_batch_layout for
+ * n_steps), gd_get_fields/gd_set_state/gd_assemble/gd_solve work on the union;
+ * gd_set_params and gd_backward return GD_ERR_STATE.  This batching (one
+ * handle, per-specimen weights) is a throughput layout with no counterpart in
+ * the paper, which treats one specimen at a time (Sec. 5).
+ * Errors: as gd_create, with the specimen index in the message. */
+gd_status gd_create_batch(int32_t n_spec, const gd_mesh *meshes, const gd_icnn *psi, const gd_icnn *yield,
+                          const gd_material *mat, const gd_load_path *paths, const gd_options *opt,
+                          gd_handle **out);
+
+/* Layout of a handle's specimens (a single-specimen handle is a batch of one):
+ * node_off and elem_off [n_spec + 1] (host, may be NULL) receive the first node
+ * and element of every specimen, n_steps the number of load steps of the batch
+ * (the longest path). */
+gd_status gd_batch_layout(gd_handle *h, int32_t *n_spec, int64_t *node_off, int64_t *elem_off, int32_t *n_steps);
 
 /* Replaces the network weights (same widths) from host or device memory
  * (cudaMemcpyDefault) and recomputes the normalising constants on the device. */
@@ -261,7 +301,8 @@ gd_status gd_solve_noalloc(int32_t ndof, int64_t n_nodes, const int32_t *rowptr,
 gd_status gd_newton_step(gd_handle *h, gd_newton_report *rep);
 
 /* Runs every remaining step of the load path; reaction [n_steps] (host, may be
- * NULL) receives the reaction of each step.  rep may be NULL. */
+ * NULL; [n_steps * n_spec] step-major for a batch) receives the reaction of each
+ * step.  rep may be NULL. */
 gd_status gd_run_load_path(gd_handle *h, double *reaction, gd_path_report *rep);
 
 /* Gradient of a loss of the reaction curve with respect to the network weights

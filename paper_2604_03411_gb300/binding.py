@@ -23,6 +23,7 @@ STATUS = {0: "GD_OK", 1: "GD_ERR_ARG", 2: "GD_ERR_MESH", 3: "GD_ERR_CUDA", 4: "G
           9: "GD_ERR_TIMEOUT", 10: "GD_ERR_STATE"}
 GD_FP64, GD_MIXED = 0, 1
 GD_ASM_RESIDUAL, GD_ASM_TANGENT = 0, 1
+GD_INNER_AUTO, GD_INNER_FP64, GD_INNER_REFINED = 0, 1, 2
 GD_NOALLOC_MAX_DOFS = 131072
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -57,7 +58,7 @@ class GdOptions(ctypes.Structure):
                 ("newton_max", ctypes.c_int32), ("line_search_max", ctypes.c_int32), ("krylov", ctypes.c_int32),
                 ("krylov_rtol", ctypes.c_double), ("krylov_max", ctypes.c_int32), ("gmres_m", ctypes.c_int32),
                 ("local_max", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
-                ("max_step_cuts", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+                ("max_step_cuts", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p), ("inner_solve", ctypes.c_int32)]
 
 
 class GdNewtonReport(ctypes.Structure):
@@ -67,7 +68,8 @@ class GdNewtonReport(ctypes.Structure):
                 ("step_cuts", ctypes.c_int32), ("assemblies", ctypes.c_int32),
                 ("residual0", ctypes.c_double), ("residual", ctypes.c_double), ("reaction", ctypes.c_double),
                 ("max_damage", ctypes.c_double), ("assembly_ms", ctypes.c_double), ("krylov_ms", ctypes.c_double),
-                ("yield_evals", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+                ("yield_evals", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("krylov_fp32_iterations", ctypes.c_int32)]
 
 
 class GdPathReport(ctypes.Structure):
@@ -84,6 +86,11 @@ PROTOTYPES = {
     "gd_create": (ctypes.c_int, [ctypes.POINTER(GdMesh), ctypes.POINTER(GdIcnn), ctypes.POINTER(GdIcnn),
                                  ctypes.POINTER(GdMaterial), ctypes.POINTER(GdLoadPath), ctypes.POINTER(GdOptions),
                                  ctypes.POINTER(_H)]),
+    "gd_create_batch": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(GdMesh), ctypes.POINTER(GdIcnn),
+                                       ctypes.POINTER(GdIcnn), ctypes.POINTER(GdMaterial), ctypes.POINTER(GdLoadPath),
+                                       ctypes.POINTER(GdOptions), ctypes.POINTER(_H)]),
+    "gd_batch_layout": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int32), _i64p, _i64p,
+                                       ctypes.POINTER(ctypes.c_int32)]),
     "gd_set_params": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p]),
     "gd_csr_pattern": (ctypes.c_int, [_H, _i64p, _i64p, _i32p, _i32p]),
     "gd_build_pattern": (ctypes.c_int, [ctypes.POINTER(GdMesh), _i64p, _i64p, _i32p, _i32p, _i32p]),
@@ -227,6 +234,51 @@ def gd_create(problem, options: Optional[GdOptions] = None) -> Handle:
     return Handle(h, meta)
 
 
+def gd_create_batch(problems, options: Optional[GdOptions] = None) -> Handle:
+    """gd_create_batch from a list of problem descriptions (one per specimen; the
+    material and options of the first apply to all)."""
+    n = len(problems)
+    meshes = (GdMesh * n)()
+    psis = (GdIcnn * n)()
+    ylds = (GdIcnn * n)()
+    paths = (GdLoadPath * n)()
+    keep = []
+    for i, p in enumerate(problems):
+        meshes[i], k = _mesh_struct(p.mesh)
+        keep.append(k)
+        pp = np.ascontiguousarray(p.psi.params, np.float64) if p.psi is not None else None
+        yp = np.ascontiguousarray(p.yld.params, np.float64) if p.yld.width > 0 else None
+        ld = np.ascontiguousarray(p.load, np.float64)
+        keep += [pp, yp, ld]
+        psis[i] = GdIcnn(3, p.psi.width if p.psi is not None else 0, _hp(pp))
+        ylds[i] = GdIcnn(1, p.yld.width, _hp(yp))
+        paths[i] = GdLoadPath(ld.size, _hp(ld))
+    mt = problems[0].mat
+    mat = GdMaterial(mt.mu_e, mt.lambda_e, mt.eta_d, mt.kappa_d, mt.beta_d, mt.c_d, mt.gamma_d, int(mt.energy))
+    opt = options if options is not None else gd_default_options()
+    h = _H()
+    _check(lib().gd_create_batch(n, meshes, psis, ylds, ctypes.byref(mat), paths, ctypes.byref(opt),
+                                 ctypes.byref(h)), None)
+    dim = problems[0].mesh.dim
+    nen = 4 if dim == 2 else 8
+    n_nodes = sum(p.mesh.coords.shape[0] for p in problems)
+    n_elems = sum(p.mesh.conn.shape[0] for p in problems)
+    meta = dict(dim=dim, n_nodes=n_nodes, n_elems=n_elems, ndof=dim + 1, nq=nen, nen=nen,
+                n_steps=max(p.load.size for p in problems), n_spec=n, precision=opt.precision, n_psi=0, n_yield=0)
+    return Handle(h, meta)
+
+
+def gd_batch_layout(h: Handle):
+    """(node_off, elem_off, n_steps) of the handle's specimens; offsets have n_spec + 1 entries."""
+    ns = ctypes.c_int32()
+    st = ctypes.c_int32()
+    _check(lib().gd_batch_layout(h.ptr, ctypes.byref(ns), None, None, ctypes.byref(st)), h.ptr)
+    no = np.zeros(ns.value + 1, np.int64)
+    eo = np.zeros(ns.value + 1, np.int64)
+    _check(lib().gd_batch_layout(h.ptr, None, _hp(no, _i64p), _hp(eo, _i64p), None), h.ptr)
+    return no, eo, st.value
+
+
 def gd_set_params(h: Handle, theta_psi=None, theta_yield=None):
     """theta_* may be numpy arrays (host) or CUDA tensors (device), or None to keep."""
     keep = []
@@ -291,10 +343,14 @@ def gd_newton_step(h: Handle) -> GdNewtonReport:
 
 
 def gd_run_load_path(h: Handle):
-    reac = np.zeros(max(h.meta["n_steps"], 1))
+    """(reaction [n_steps], report); a batch returns reaction [n_steps, n_spec]."""
+    ns = h.meta.get("n_spec", 1)
+    reac = np.zeros(max(h.meta["n_steps"], 1) * ns)
     rep = GdPathReport()
     st = lib().gd_run_load_path(h.ptr, _hp(reac), ctypes.byref(rep))
     _check(st, h.ptr)
+    if "n_spec" in h.meta:
+        return reac[:h.meta["n_steps"] * ns].reshape(h.meta["n_steps"], ns), rep
     return reac[:h.meta["n_steps"]], rep
 
 

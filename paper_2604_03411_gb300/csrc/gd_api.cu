@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -83,14 +84,41 @@ bool element_ok(int dim, const double *Xe)
     return true;
 }
 
+void free_ckpts(gd::Handle &H);
+
 void free_handle(gd::Handle &H)
 {
     void *ptrs[] = {H.X, H.conn, H.slot, H.rowptr, H.colidx, H.fixed, H.bc_dof, H.bc_scale, H.react_dof,
                     H.psi.p, H.psi.W2T, H.yld.p, H.yld.W2T, H.psi.pf, H.psi.W2Tf, H.yld.pf, H.yld.W2Tf, H.netc, H.dofs, H.kappa, H.dofs_prev, H.w_dofs,
                     H.w_trial, H.R, H.R_trial, H.vals, H.vals_trial, H.kappa_trial, H.kappa_trial2, H.loading,
-                    H.loading2, H.counters, H.diag, H.binv, H.red, H.scal};
+                    H.loading2, H.counters, H.diag, H.binv, H.vals_f32, H.kx, H.red, H.scal};
     for (void *p : ptrs) dfree(p);
     for (double *p : H.kv) dfree(p);
+    free_ckpts(H);
+    dfree(H.perm_T);
+    dfree(H.vals_T);
+    for (double *p : H.adj_v) dfree(p);
+    dfree(H.kbar);
+    dfree(H.kbar2);
+    dfree(H.theta_bar);
+    dfree(H.glob);
+    dfree(H.seg);
+    dfree(H.elem_spec);
+    dfree(H.node_spec);
+    dfree(H.bc_spec);
+    dfree(H.react_off);
+    dfree(H.node_off);
+    dfree(H.d_load);
+    dfree(H.d_norm);
+    dfree(H.d_coef);
+    dfree(H.psi_tab);
+    dfree(H.yld_tab);
+    for (gd::DevNet &n : H.h_psi_tab) {
+        dfree(n.p); dfree(n.W2T); dfree(n.pf); dfree(n.W2Tf);
+    }
+    for (gd::DevNet &n : H.h_yld_tab) {
+        dfree(n.p); dfree(n.W2T); dfree(n.pf); dfree(n.W2Tf);
+    }
     if (H.ev0) cudaEventDestroy(H.ev0);
     if (H.ev1) cudaEventDestroy(H.ev1);
     if (H.kv0) cudaEventDestroy(H.kv0);
@@ -137,20 +165,25 @@ gd::AsmArgs asm_args(gd::Handle &H, const double *dofs, const double *kappa_n, d
     a.mat = H.mat;
     a.tangent = tangent && vals != nullptr;
     a.counters = H.counters;
+    a.elem_spec = H.elem_spec;
+    a.psi_tab = H.psi_tab;
+    a.yld_tab = H.yld_tab;
+    a.wmax = H.wmax;
     return a;
 }
 
 // one assembly pass with timing; counters[0] = local failures, [1] = loading points
 gd_status assemble_pass(gd::Handle &H, const double *dofs, const double *kappa_n, double *R, void *vals,
-                        double *kappa_out, int8_t *loading, int tangent)
+                        double *kappa_out, int8_t *loading, int tangent, bool force_fp64 = false)
 {
     const size_t vbytes = H.opt.precision == GD_FP64 ? sizeof(double) : sizeof(float);
+    if (force_fp64) tangent = 0;
     if (R) GD_CUDA(&H, cudaMemsetAsync(R, 0, sizeof(double) * H.n_dofs, H.stream));
     if (tangent && vals) GD_CUDA(&H, cudaMemsetAsync(vals, 0, vbytes * H.nnz, H.stream));
     GD_CUDA(&H, cudaMemsetAsync(H.counters, 0, sizeof(int) * 8, H.stream));
     GD_CUDA(&H, cudaEventRecord(H.ev0, H.stream));
     gd::AsmArgs a = asm_args(H, dofs, kappa_n, R, vals, kappa_out, loading, tangent);
-    if (H.opt.precision == GD_FP64) GD_CUDA(&H, gd::launch_assemble_fp64(H.dim, a, H.num_sms, H.stream));
+    if (H.opt.precision == GD_FP64 || force_fp64) GD_CUDA(&H, gd::launch_assemble_fp64(H.dim, a, H.num_sms, H.stream));
     else GD_CUDA(&H, gd::launch_assemble_fp32(H.dim, a, H.num_sms, H.stream));
     ++H.launches;
     GD_CUDA(&H, cudaEventRecord(H.ev1, H.stream));
@@ -182,8 +215,11 @@ gd_status norms(gd::Handle &H, const double *R, NormPair &out)
 }
 
 // K x = b with the persistent Krylov kernel on `vals`; timing accumulated in H.krylov_ms
+// accept: a solve that stops at its iteration cap or on a breakdown is still
+// returned as GD_OK when its relative residual is at most `accept` (default: rtol,
+// i.e. strict); a non-finite residual is always an error.
 gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, int &iters, double &rel,
-                 double rtol)
+                 double rtol, bool inner_fp32 = false, double accept = -1.0)
 {
     gd::KrylovCtx kc;
     kc.n_nodes = H.n_nodes;
@@ -193,13 +229,21 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
     kc.fixed = H.fixed;
     kc.binv = H.binv;
     for (int k = 0; k < 8; ++k) kc.work[k] = H.kv[k];
+    kc.work_x = H.kx;
     kc.red = H.red;
     kc.out = H.scal + 24;
     kc.stream = H.stream;
     kc.blocks = H.krylov_grid;
     kc.num_sms = H.num_sms;
     GD_CUDA(&H, cudaEventRecord(H.kv0, H.stream));
-    GD_CUDA(&H, gd::krylov_solve(kc, vals, H.opt.precision == GD_MIXED, b, x, rtol, H.opt.krylov_max));
+    bool fp32_vals = H.opt.precision == GD_MIXED;
+    if (inner_fp32 && !fp32_vals) {
+        GD_CUDA(&H, gd::narrow_to_float((const double *)vals, H.vals_f32, H.nnz, H.stream));
+        ++H.launches;
+        vals = H.vals_f32;
+        fp32_vals = true;
+    }
+    GD_CUDA(&H, gd::krylov_solve(kc, vals, fp32_vals, b, x, rtol, H.opt.krylov_max, inner_fp32));
     H.launches += 2;
     GD_CUDA(&H, cudaEventRecord(H.kv1, H.stream));
     double kout[3];
@@ -210,10 +254,109 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
     H.krylov_ms += kms;
     iters = (int)kout[0];
     rel = kout[1];
-    if (kout[2] != 0.0)
+    if (kout[2] != 0.0 && !(kout[2] != 2.0 && std::isfinite(rel) && rel <= std::max(accept, rtol)))
         return fail(&H, GD_ERR_KRYLOV, "BiCGStab stopped (status " + std::to_string((int)kout[2]) +
                                            ", relative residual " + std::to_string(rel) + ")");
     return GD_OK;
+}
+
+// K x = b to relative tolerance eta by mixed-precision iterative refinement:
+// FP32 BiCGStab cycles on the FP32 tangent copy, each followed by the FP64
+// residual r = b - K x with the FP64 tangent (GB300's FP64 rate makes the FP32
+// iteration several times cheaper, and the FP64 residual keeps the result at
+// FP64 accuracy).  Returns GD_ERR_KRYLOV when a cycle breaks down.
+gd_status krylov_refined(gd::Handle &H, const double *b, double *x, double eta, int &iters, double &rel)
+{
+    gd::SolverCtx c = solver_ctx(H, H.vals);
+    // scratch: residual in R_trial, correction in w_trial (both rewritten by the line search after the solve)
+    double *res = H.R_trial, *dx = H.w_trial, *y = H.diag;
+    GD_CUDA(&H, cudaMemsetAsync(x, 0, sizeof(double) * H.n_dofs, H.stream));
+    GD_CUDA(&H, cudaMemcpyAsync(res, b, sizeof(double) * H.n_dofs, cudaMemcpyDeviceToDevice, H.stream));
+    double bn = 0.0, rn = 0.0;
+    {
+        GD_CUDA(&H, gd::launch_norm2_free(c, b, H.scal + 30, nullptr));
+        GD_CUDA(&H, cudaMemcpyAsync(&bn, H.scal + 30, sizeof(double), cudaMemcpyDeviceToHost, H.stream));
+        GD_CUDA(&H, cudaStreamSynchronize(H.stream));
+    }
+    iters = 0;
+    rel = 1.0;
+    if (bn == 0.0) {
+        rel = 0.0;
+        return GD_OK;
+    }
+    for (int cycle = 0; cycle < 12; ++cycle) {
+        int kit = 0;
+        double krel = 0.0;
+        // each cycle reduces the FP64 residual by about the FP32 solve's tolerance
+        const double inner = std::max(1e-4, std::min(1e-2, 0.5 * eta * bn / std::max(rn > 0.0 ? rn : bn, 1e-300)));
+        gd_status st = krylov(H, H.vals, res, dx, kit, krel, inner, true, 0.5);
+        iters += kit;
+        if (st) return st;
+        GD_CUDA(&H, gd::launch_axpy_free(c, x, dx, 1.0));
+        GD_CUDA(&H, gd::launch_spmv(c, x, y, 1));
+        GD_CUDA(&H, gd::launch_residual(c, b, y, res, H.scal + 31));
+        H.launches += 1;
+        GD_CUDA(&H, cudaMemcpyAsync(&rn, H.scal + 31, sizeof(double), cudaMemcpyDeviceToHost, H.stream));
+        GD_CUDA(&H, cudaStreamSynchronize(H.stream));
+        rel = rn / bn;
+        if (!std::isfinite(rel)) return fail(&H, GD_ERR_KRYLOV, "refined solve produced a non-finite residual");
+        if (rel <= eta) return GD_OK;
+    }
+    return fail(&H, GD_ERR_KRYLOV, "refined solve did not reach its tolerance");
+}
+
+// Newton direction K delta = rhs to relative tolerance eta (policy: gd_options.inner_solve).
+// GD_MIXED solves directions that need at most 1e-5 relative accuracy with FP32
+// values and vectors (FP64 dot products); GD_INNER_REFINED refines FP32 cycles by
+// FP64 residuals; any FP32 solve that breaks down falls back to the FP64 solve.  The
+// FP64 residual of the assembly decides convergence, so FP64 parity is unaffected.
+gd_status solve_direction(gd::Handle &H, const double *rhs, double *delta, double eta, gd_newton_report &rep)
+{
+    int kit = 0;
+    double rel = 0.0;
+    gd_status st = GD_ERR_KRYLOV;
+    if (H.opt.inner_solve != GD_INNER_FP64) {
+        if (H.opt.inner_solve == GD_INNER_REFINED) {
+            st = krylov_refined(H, rhs, delta, eta, kit, rel);
+        } else if (H.opt.precision == GD_MIXED && eta >= 1e-5) {
+            st = krylov(H, H.vals, rhs, delta, kit, rel, eta, true, 0.1);
+        }
+        rep.krylov_iterations += kit;
+        rep.krylov_fp32_iterations += kit;
+    }
+    if (st) {
+        // an FP64 solve that stalls (iteration cap, breakdown) after a tenfold reduction
+        // still gives a descent direction for the line search: inexact Newton
+        st = krylov(H, H.vals, rhs, delta, kit, rel, eta, false, 0.1);
+        rep.krylov_iterations += kit;
+    }
+    return st;
+}
+
+gd_status norms_batch(gd::Handle &H, const double *R, std::vector<double> &nf, std::vector<double> &nx);
+
+// GD_MIXED: rounding noise of the FP32 residual at the current iterate, measured
+// as ||R_fp32 - R_fp64|| on the free dofs (one residual-only FP64 pass), per
+// specimen.  Near equilibrium the residual is a sum of element forces that cancel,
+// so its FP32 rounding error, not the Newton iteration, sets how small it can get;
+// the Newton test is not asked to go below twice this level.
+gd_status mixed_noise(gd::Handle &H, const double *R32, std::vector<double> &noise)
+{
+    gd_status st = assemble_pass(H, H.w_dofs, H.kappa, H.R_trial, nullptr, nullptr, nullptr, 0, true);
+    if (st) return st;
+    H.assembly_ms += elapsed_ms(H);
+    gd::SolverCtx c = solver_ctx(H, nullptr);
+    double *diff = H.kv[9];
+    GD_CUDA(&H, gd::launch_residual(c, H.R_trial, R32, diff, H.scal + 32));
+    H.launches += 2;
+    noise.assign(H.n_spec, 0.0);
+    if (H.n_spec == 1) {
+        GD_CUDA(&H, cudaMemcpyAsync(noise.data(), H.scal + 32, sizeof(double), cudaMemcpyDeviceToHost, H.stream));
+        GD_CUDA(&H, cudaStreamSynchronize(H.stream));
+        return GD_OK;
+    }
+    std::vector<double> nx;
+    return norms_batch(H, diff, noise, nx);
 }
 
 // Newton iteration for one load value starting from H.w_dofs (already predicted,
@@ -230,6 +373,13 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
     rep.yield_evals += hc[2];
     double nrm = nr.free_;
     const double r0 = std::max(nr.free_, nr.fixed_);
+    double noise = 0.0;
+    if (H.opt.precision == GD_MIXED) {
+        std::vector<double> nz;
+        if ((st = mixed_noise(H, H.R, nz))) return st;
+        noise = nz[0];
+    }
+    const double ntol = std::max(std::max(H.opt.newton_rtol * r0, H.opt.newton_atol), 2.0 * noise);
     rep.residual0 = nrm;
     rep.local_failures = hc[0];
     rep.loading_points = hc[1];
@@ -238,7 +388,7 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
         rep.iterations = it;
         rep.residual = nrm;
         if (!std::isfinite(nrm)) return fail(&H, GD_ERR_NAN, "non-finite residual in the Newton iteration");
-        if (nrm <= std::max(H.opt.newton_rtol * r0, H.opt.newton_atol)) {
+        if (nrm <= ntol) {
             rep.converged = 1;
             return GD_OK;
         }
@@ -249,16 +399,15 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
         GD_CUDA(&H, gd::launch_axpy_free(c, rhs, H.R, -1.0));
         // inexact Newton: the linear solve only needs to reach a tenth of the Newton
         // tolerance relative to the current residual (floor krylov_rtol, cap 1e-2)
-        const double ntol = std::max(H.opt.newton_rtol * r0, H.opt.newton_atol);
         const double eta = std::min(1e-2, std::max(H.opt.krylov_rtol, 0.1 * ntol / nrm));
-        int kit = 0;
-        double rel = 0.0;
-        st = krylov(H, H.vals, rhs, delta, kit, rel, eta);
-        rep.krylov_iterations += kit;
-        if (st) return st;
-        // backtracking line search on ||R_free||
+        if ((st = solve_direction(H, rhs, delta, eta, rep))) return st;
+        // backtracking line search on ||R_free|| (GD_MIXED near its noise floor: at most
+        // two halvings, a decrease below the noise cannot be measured)
         double alpha = 1.0, nt = 0.0;
-        for (int ls = 0; ls <= H.opt.line_search_max; ++ls) {
+        bool decreased = false;
+        const int ls_max = (H.opt.precision == GD_MIXED && nrm <= 8.0 * noise) ? std::min(2, H.opt.line_search_max)
+                                                                               : H.opt.line_search_max;
+        for (int ls = 0; ls <= ls_max; ++ls) {
             GD_CUDA(&H, cudaMemcpyAsync(H.w_trial, H.w_dofs, sizeof(double) * H.n_dofs, cudaMemcpyDeviceToDevice,
                                         H.stream));
             GD_CUDA(&H, gd::launch_axpy_free(c, H.w_trial, delta, alpha));
@@ -269,7 +418,8 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
             GD_CUDA(&H, cudaMemcpy(hc, H.counters, 3 * sizeof(int), cudaMemcpyDeviceToHost));
             rep.yield_evals += hc[2];
             nt = nr.free_;
-            if ((std::isfinite(nt) && nt <= (1.0 - 1e-4 * alpha) * nrm) || ls == H.opt.line_search_max) break;
+            decreased = std::isfinite(nt) && nt <= (1.0 - 1e-4 * alpha) * nrm;
+            if (decreased || ls == ls_max) break;
             alpha *= 0.5;
             ++rep.line_search_cuts;
         }
@@ -281,8 +431,240 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
         rep.local_failures = hc[0];
         rep.loading_points = hc[1];
         nrm = nt;
+        // GD_MIXED: when no step of the line search lowers ||R_free|| any more and it is
+        // within four times the measured FP32 noise, the iterate is converged to the
+        // precision of the mode
+        if (!decreased && H.opt.precision == GD_MIXED && std::isfinite(nrm) && nrm <= 4.0 * noise) {
+            rep.iterations = it + 1;
+            rep.residual = nrm;
+            rep.converged = 1;
+            return GD_OK;
+        }
     }
     rep.converged = 0;
+    return GD_OK;
+}
+
+// per-specimen ||R_free|| and ||R_fixed|| (batches)
+gd_status norms_batch(gd::Handle &H, const double *R, std::vector<double> &nf, std::vector<double> &nx)
+{
+    const int S = H.n_spec;
+    GD_CUDA(&H, gd::launch_norms_batch(R, H.fixed, H.node_off, H.ndof, S, H.d_norm, H.stream));
+    ++H.launches;
+    std::vector<double> h((size_t)2 * S);
+    GD_CUDA(&H, cudaMemcpyAsync(h.data(), H.d_norm, sizeof(double) * 2 * S, cudaMemcpyDeviceToHost, H.stream));
+    GD_CUDA(&H, cudaStreamSynchronize(H.stream));
+    nf.resize(S);
+    nx.resize(S);
+    for (int s = 0; s < S; ++s) {
+        nf[s] = h[2 * s];
+        nx[s] = h[2 * s + 1];
+    }
+    return GD_OK;
+}
+
+gd_status set_coef(gd::Handle &H, const std::vector<double> &coef)
+{
+    GD_CUDA(&H, cudaMemcpyAsync(H.d_coef, coef.data(), sizeof(double) * H.n_spec, cudaMemcpyHostToDevice, H.stream));
+    GD_CUDA(&H, cudaStreamSynchronize(H.stream));
+    return GD_OK;
+}
+
+// Newton iteration of a batch of independent specimens in one block-diagonal
+// system.  Each specimen keeps its own convergence test (its own force scale),
+// its own line-search step length and, once converged, stays where it is (zero
+// right-hand side, zero step) while the others continue.  The linear solve of the
+// union system is tight enough that every unconverged block meets its own
+// inexact-Newton tolerance.
+gd_status newton_batch(gd::Handle &H, gd_newton_report &rep)
+{
+    const int S = H.n_spec;
+    gd_status st = assemble_pass(H, H.w_dofs, H.kappa, H.R, H.vals, H.kappa_trial, H.loading, 1);
+    if (st) return st;
+    std::vector<double> nf, nx, nt, ntx;
+    if ((st = norms_batch(H, H.R, nf, nx))) return st;
+    H.assembly_ms += elapsed_ms(H);
+    int hc[3];
+    GD_CUDA(&H, cudaMemcpy(hc, H.counters, 3 * sizeof(int), cudaMemcpyDeviceToHost));
+    rep.yield_evals += hc[2];
+    std::vector<double> r0(S), ntol(S), coef(S), alpha(S);
+    std::vector<char> done(S, 0), accepted(S, 0);
+    auto total = [&](const std::vector<double> &v) {
+        double t = 0.0;
+        for (double x : v) t += x * x;
+        return std::sqrt(t);
+    };
+    std::vector<double> noise(S, 0.0);
+    if (H.opt.precision == GD_MIXED && (st = mixed_noise(H, H.R, noise))) return st;
+    for (int s = 0; s < S; ++s) {
+        r0[s] = std::max(nf[s], nx[s]);
+        ntol[s] = std::max(std::max(H.opt.newton_rtol * r0[s], H.opt.newton_atol), 2.0 * noise[s]);
+    }
+    rep.residual0 = total(nf);
+    rep.local_failures = hc[0];
+    rep.loading_points = hc[1];
+    double *delta = H.kv[8], *rhs = H.kv[9];
+    for (int it = 0; it <= H.opt.newton_max; ++it) {
+        rep.iterations = it;
+        rep.residual = total(nf);
+        if (!std::isfinite(rep.residual)) return fail(&H, GD_ERR_NAN, "non-finite residual in the Newton iteration");
+        bool all = true;
+        for (int s = 0; s < S; ++s) {
+            if (nf[s] <= ntol[s]) done[s] = 1;
+            all = all && done[s];
+        }
+        if (all) {
+            rep.converged = 1;
+            return GD_OK;
+        }
+        if (it == H.opt.newton_max) break;
+        // right-hand side -R on the unconverged specimens only
+        double bn2 = 0.0, need = 1e300;
+        for (int s = 0; s < S; ++s) {
+            coef[s] = done[s] ? 0.0 : -1.0;
+            if (done[s]) continue;
+            bn2 += nf[s] * nf[s];
+            const double eta_s = std::min(1e-2, std::max(H.opt.krylov_rtol, 0.1 * ntol[s] / nf[s]));
+            need = std::min(need, eta_s * nf[s]);
+        }
+        if ((st = set_coef(H, coef))) return st;
+        GD_CUDA(&H, gd::launch_scale_spec(H.n_dofs, H.ndof, rhs, H.R, H.d_coef, H.node_spec, H.fixed, 0, H.stream));
+        ++H.launches;
+        // ||r_s|| <= ||r|| <= eta ||b||: eta = min_s eta_s ||b_s|| / ||b|| meets every block's tolerance
+        const double eta = std::max(1e-14, need / std::sqrt(bn2));
+        if ((st = solve_direction(H, rhs, delta, eta, rep))) return st;
+        // backtracking line search per specimen on its own ||R_free||
+        bool near_floor = H.opt.precision == GD_MIXED;
+        for (int s = 0; s < S; ++s) {
+            alpha[s] = done[s] ? 0.0 : 1.0;
+            accepted[s] = done[s];
+            if (!done[s] && nf[s] > 8.0 * noise[s]) near_floor = false;
+        }
+        const int ls_max = near_floor ? std::min(2, H.opt.line_search_max) : H.opt.line_search_max;
+        for (int ls = 0; ls <= ls_max; ++ls) {
+            if ((st = set_coef(H, alpha))) return st;
+            GD_CUDA(&H, cudaMemcpyAsync(H.w_trial, H.w_dofs, sizeof(double) * H.n_dofs, cudaMemcpyDeviceToDevice,
+                                        H.stream));
+            GD_CUDA(&H, gd::launch_scale_spec(H.n_dofs, H.ndof, H.w_trial, delta, H.d_coef, H.node_spec, H.fixed, 1,
+                                              H.stream));
+            ++H.launches;
+            if ((st = assemble_pass(H, H.w_trial, H.kappa, H.R_trial, H.vals_trial, H.kappa_trial2, H.loading2, 1)))
+                return st;
+            if ((st = norms_batch(H, H.R_trial, nt, ntx))) return st;
+            H.assembly_ms += elapsed_ms(H);
+            GD_CUDA(&H, cudaMemcpy(hc, H.counters, 3 * sizeof(int), cudaMemcpyDeviceToHost));
+            rep.yield_evals += hc[2];
+            bool all_acc = true;
+            for (int s = 0; s < S; ++s) {
+                if (!accepted[s] && std::isfinite(nt[s]) && nt[s] <= (1.0 - 1e-4 * alpha[s]) * nf[s]) accepted[s] = 1;
+                all_acc = all_acc && accepted[s];
+            }
+            if (all_acc || ls == ls_max) break;
+            for (int s = 0; s < S; ++s)
+                if (!accepted[s]) alpha[s] *= 0.5;
+            ++rep.line_search_cuts;
+        }
+        std::swap(H.w_dofs, H.w_trial);
+        std::swap(H.R, H.R_trial);
+        std::swap(H.vals, H.vals_trial);
+        std::swap(H.kappa_trial, H.kappa_trial2);
+        std::swap(H.loading, H.loading2);
+        rep.local_failures = hc[0];
+        rep.loading_points = hc[1];
+        // GD_MIXED: a specimen whose residual no step can lower any more and that is
+        // within four times its measured FP32 noise is converged to the precision of the mode
+        for (int s = 0; s < S; ++s) {
+            if (!accepted[s] && H.opt.precision == GD_MIXED && std::isfinite(nt[s]) && nt[s] <= 4.0 * noise[s])
+                ntol[s] = std::max(ntol[s], nt[s]);
+        }
+        nf = nt;
+    }
+    rep.converged = 0;
+    return GD_OK;
+}
+
+// load of specimen s at step coordinate t: piecewise linear through 0 at t = 0
+// and the path values at t = 1..n (held after the last step)
+double path_load(const gd::Handle &H, int s, double t)
+{
+    const std::vector<double> &P = H.paths[s];
+    const int n = (int)P.size();
+    if (n == 0 || t <= 0.0) return 0.0;
+    if (t >= n) return P[n - 1];
+    const int k = (int)std::floor(t);
+    const double a = k == 0 ? 0.0 : P[k - 1], b = P[k];
+    return a + (t - k) * (b - a);
+}
+
+// initial guess for step coordinate t: the last converged state plus the previous
+// increment scaled to this one (per specimen), prescribed dofs at their loads
+gd_status predict(gd::Handle &H, double t)
+{
+    if (H.n_spec == 1) {
+        const double Lt = path_load(H, 0, t), L1 = path_load(H, 0, H.load_prev), L2 = path_load(H, 0, H.load_prevprev);
+        const double dl = L1 - L2;
+        const bool extrap = H.have_prev && dl != 0.0;
+        GD_CUDA(&H, gd::launch_predictor(H.n_dofs, H.w_dofs, H.dofs, extrap ? H.dofs_prev : nullptr,
+                                         extrap ? (Lt - L1) / dl : 0.0, H.bc_dof, H.bc_scale, H.n_bc, Lt, H.stream));
+        H.launches += H.n_bc > 0 ? 2 : 1;
+        return GD_OK;
+    }
+    std::vector<double> hl((size_t)2 * H.n_spec);
+    for (int s = 0; s < H.n_spec; ++s) {
+        const double Lt = path_load(H, s, t), L1 = path_load(H, s, H.load_prev), L2 = path_load(H, s, H.load_prevprev);
+        const double dl = L1 - L2;
+        hl[s] = Lt;
+        hl[H.n_spec + s] = (H.have_prev && dl != 0.0) ? (Lt - L1) / dl : 0.0;
+    }
+    GD_CUDA(&H, cudaMemcpyAsync(H.d_load, hl.data(), sizeof(double) * 2 * H.n_spec, cudaMemcpyHostToDevice, H.stream));
+    GD_CUDA(&H, gd::launch_predictor_batch(H.n_dofs, H.ndof, H.w_dofs, H.dofs, H.have_prev ? H.dofs_prev : nullptr,
+                                           H.d_factor, H.node_spec, H.bc_dof, H.bc_scale, H.bc_spec, H.d_load, H.n_bc,
+                                           H.stream));
+    GD_CUDA(&H, cudaStreamSynchronize(H.stream));     // hl is pageable host memory
+    H.launches += H.n_bc > 0 ? 2 : 1;
+    return GD_OK;
+}
+
+void free_ckpts(gd::Handle &H)
+{
+    for (auto &c : H.ckpts) {
+        dfree(c.dofs);
+        dfree(c.dofs_prev);
+        dfree(c.kappa);
+    }
+    H.ckpts.clear();
+}
+
+// stores the handle's committed state as a checkpoint after `commits` commits
+gd_status save_ckpt(gd::Handle &H, int commits)
+{
+    gd::Checkpoint c;
+    c.commit = commits;
+    GD_CUDA(&H, dalloc(&c.dofs, (size_t)H.n_dofs));
+    GD_CUDA(&H, dalloc(&c.dofs_prev, (size_t)H.n_dofs));
+    GD_CUDA(&H, dalloc(&c.kappa, (size_t)(H.n_elems * H.nq)));
+    GD_CUDA(&H, cudaMemcpyAsync(c.dofs, H.dofs, sizeof(double) * H.n_dofs, cudaMemcpyDeviceToDevice, H.stream));
+    GD_CUDA(&H, cudaMemcpyAsync(c.dofs_prev, H.dofs_prev, sizeof(double) * H.n_dofs, cudaMemcpyDeviceToDevice,
+                                H.stream));
+    GD_CUDA(&H, cudaMemcpyAsync(c.kappa, H.kappa, sizeof(double) * H.n_elems * H.nq, cudaMemcpyDeviceToDevice,
+                                H.stream));
+    c.load_prev = H.load_prev;
+    c.load_prevprev = H.load_prevprev;
+    c.have_prev = H.have_prev;
+    H.ckpts.push_back(c);
+    return GD_OK;
+}
+
+gd_status restore_ckpt(gd::Handle &H, const gd::Checkpoint &c)
+{
+    GD_CUDA(&H, cudaMemcpyAsync(H.dofs, c.dofs, sizeof(double) * H.n_dofs, cudaMemcpyDeviceToDevice, H.stream));
+    GD_CUDA(&H, cudaMemcpyAsync(H.dofs_prev, c.dofs_prev, sizeof(double) * H.n_dofs, cudaMemcpyDeviceToDevice,
+                                H.stream));
+    GD_CUDA(&H, cudaMemcpyAsync(H.kappa, c.kappa, sizeof(double) * H.n_elems * H.nq, cudaMemcpyDeviceToDevice,
+                                H.stream));
+    H.load_prev = c.load_prev;
+    H.load_prevprev = c.load_prevprev;
+    H.have_prev = c.have_prev;
     return GD_OK;
 }
 
@@ -296,36 +678,46 @@ gd_status commit(gd::Handle &H, double target, gd_newton_report &rep)
     rep.kernel_launches += 2;
     double h[2];
     GD_CUDA(&H, cudaMemcpyAsync(h, H.scal + 20, 2 * sizeof(double), cudaMemcpyDeviceToHost, H.stream));
+    if (H.n_spec > 1) {
+        GD_CUDA(&H, gd::launch_reaction_batch(H.R, H.react_dof, H.react_off, H.n_spec, H.d_load, H.stream));
+        ++H.launches;
+        H.last_reac.resize(H.n_spec);
+        GD_CUDA(&H, cudaMemcpyAsync(H.last_reac.data(), H.d_load, sizeof(double) * H.n_spec, cudaMemcpyDeviceToHost,
+                                    H.stream));
+    }
     std::swap(H.dofs_prev, H.dofs);
     std::swap(H.dofs, H.w_dofs);            // dofs <- converged iterate
     std::swap(H.kappa, H.kappa_trial);
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));
     rep.reaction = h[0];
     rep.max_damage = h[1];
+    if (H.n_spec == 1) H.last_reac.assign(1, h[0]);
     H.load_prevprev = H.load_prev;
     H.load_prev = target;
     H.have_prev = true;
+    if (H.rec_on && !H.replaying) {
+        H.rec_load.push_back(target);
+        H.rec_step.push_back(-1);
+        const int k = H.opt.checkpoint_every > 0 ? H.opt.checkpoint_every : 1;
+        if ((int)H.rec_load.size() % k == 0) return save_ckpt(H, (int)H.rec_load.size());
+    }
     return GD_OK;
 }
 
 gd_status advance(gd::Handle &H, double target, int depth, gd_newton_report &rep)
 {
-    // predictor: last converged state plus the previous increment scaled to this one
-    const double dl = H.load_prev - H.load_prevprev;
-    const bool extrap = H.have_prev && dl != 0.0;
-    const double factor = extrap ? (target - H.load_prev) / dl : 0.0;
-    GD_CUDA(&H, gd::launch_predictor(H.n_dofs, H.w_dofs, H.dofs, extrap ? H.dofs_prev : nullptr, factor, H.bc_dof,
-                                     H.bc_scale, H.n_bc, target, H.stream));
-    H.launches += H.n_bc > 0 ? 2 : 1;
+    gd_status sp = predict(H, target);
+    if (sp) return sp;
     gd_newton_report sub{};
     const double a0 = H.assembly_ms, k0 = H.krylov_ms;
     const int n0 = H.assemblies;
     const long long l0 = H.launches;
-    gd_status st = newton(H, sub);
+    gd_status st = H.n_spec > 1 ? newton_batch(H, sub) : newton(H, sub);
     rep.assembly_ms += H.assembly_ms - a0;
     rep.krylov_ms += H.krylov_ms - k0;
     rep.assemblies += H.assemblies - n0;
     rep.yield_evals += sub.yield_evals;
+    rep.krylov_fp32_iterations += sub.krylov_fp32_iterations;
     rep.kernel_launches += H.launches - l0;
     rep.iterations += sub.iterations;
     rep.krylov_iterations += sub.krylov_iterations;
@@ -342,9 +734,12 @@ gd_status advance(gd::Handle &H, double target, int depth, gd_newton_report &rep
         return advance(H, target, depth + 1, rep);
     }
     if (st) return st;
-    if (!sub.converged)
-        return fail(&H, GD_ERR_NOT_CONVERGED,
-                    "Newton did not converge (residual " + std::to_string(sub.residual) + ")");
+    if (!sub.converged) {
+        char msg[160];
+        snprintf(msg, sizeof(msg), "Newton did not converge (|R_free| %.3e after %d iterations, first %.3e)",
+                 sub.residual, sub.iterations, sub.residual0);
+        return fail(&H, GD_ERR_NOT_CONVERGED, msg);
+    }
     rep.converged = 1;
     return commit(H, target, rep);
 }
@@ -529,18 +924,101 @@ static gd_status stage_net(gd::Handle &H, gd::DevNet &d, int n_in, int w, const 
     return GD_OK;
 }
 
-gd_status gd_create(const gd_mesh *mesh, const gd_icnn *psi, const gd_icnn *yield, const gd_material *mat,
-                    const gd_load_path *path, const gd_options *opt, gd_handle **out)
+// The meshes of a batch laid end to end: node, element, boundary and reaction
+// numbering shifted by the counts of the specimens before; per-specimen
+// reaction dofs carry each specimen's own react_comp.
+struct Union {
+    std::vector<double> coords, bc_scale;
+    std::vector<int32_t> conn, bc_node, react_node;
+    std::vector<int8_t> bc_comp;
+    std::vector<int64_t> node_off, elem_off, bc_off, react_off;
+    std::vector<int32_t> react_comp;
+    gd_mesh mesh{};
+};
+
+static gd_status build_union(int32_t n_spec, const gd_mesh *meshes, Union &U)
+{
+    const int dim = meshes[0].dim;
+    if (dim != 2 && dim != 3) return fail(nullptr, GD_ERR_ARG, "dim must be 2 or 3");
+    const int nen = dim == 2 ? 4 : 8;
+    U.node_off.assign(1, 0);
+    U.elem_off.assign(1, 0);
+    U.bc_off.assign(1, 0);
+    U.react_off.assign(1, 0);
+    for (int s = 0; s < n_spec; ++s) {
+        const gd_mesh &m = meshes[s];
+        const std::string tag = "specimen " + std::to_string(s) + ": ";
+        if (m.dim != dim) return fail(nullptr, GD_ERR_ARG, tag + "all specimens must have the same dim");
+        if (m.n_nodes <= 0 || m.n_elems < 0 || !m.coords || (m.n_elems > 0 && !m.conn))
+            return fail(nullptr, GD_ERR_ARG, tag + "empty or null mesh arrays");
+        if (m.n_bc < 0 || (m.n_bc > 0 && (!m.bc_node || !m.bc_comp || !m.bc_scale)))
+            return fail(nullptr, GD_ERR_ARG, tag + "boundary arrays");
+        if (m.n_react < 0 || (m.n_react > 0 && !m.react_node)) return fail(nullptr, GD_ERR_ARG, tag + "reaction arrays");
+        if (m.react_comp < 0 || m.react_comp >= dim) return fail(nullptr, GD_ERR_ARG, tag + "react_comp");
+        const int64_t off = U.node_off.back();
+        for (int64_t i = 0; i < m.n_elems * nen; ++i)
+            if (m.conn[i] < 0 || m.conn[i] >= m.n_nodes) return fail(nullptr, GD_ERR_MESH, tag + "bad node id in conn");
+        for (int64_t i = 0; i < m.n_bc; ++i)
+            if (m.bc_node[i] < 0 || m.bc_node[i] >= m.n_nodes) return fail(nullptr, GD_ERR_ARG, tag + "bad boundary node");
+        for (int64_t i = 0; i < m.n_react; ++i)
+            if (m.react_node[i] < 0 || m.react_node[i] >= m.n_nodes)
+                return fail(nullptr, GD_ERR_ARG, tag + "bad reaction node");
+        if (off + m.n_nodes >= ((int64_t)1 << 31) / (dim + 1)) return fail(nullptr, GD_ERR_ARG, "batch too large");
+        U.coords.insert(U.coords.end(), m.coords, m.coords + m.n_nodes * dim);
+        for (int64_t i = 0; i < m.n_elems * nen; ++i) U.conn.push_back((int32_t)(m.conn[i] + off));
+        for (int64_t i = 0; i < m.n_bc; ++i) {
+            U.bc_node.push_back((int32_t)(m.bc_node[i] + off));
+            U.bc_comp.push_back(m.bc_comp[i]);
+            U.bc_scale.push_back(m.bc_scale[i]);
+        }
+        for (int64_t i = 0; i < m.n_react; ++i) U.react_node.push_back((int32_t)(m.react_node[i] + off));
+        U.react_comp.push_back(m.react_comp);
+        U.node_off.push_back(off + m.n_nodes);
+        U.elem_off.push_back(U.elem_off.back() + m.n_elems);
+        U.bc_off.push_back(U.bc_off.back() + m.n_bc);
+        U.react_off.push_back(U.react_off.back() + m.n_react);
+    }
+    gd_mesh &M = U.mesh;
+    M.dim = dim;
+    M.n_nodes = U.node_off.back();
+    M.n_elems = U.elem_off.back();
+    M.coords = U.coords.data();
+    M.conn = U.conn.data();
+    M.n_bc = U.bc_off.back();
+    M.bc_node = U.bc_node.data();
+    M.bc_comp = U.bc_comp.data();
+    M.bc_scale = U.bc_scale.data();
+    M.n_react = U.react_off.back();
+    M.react_node = U.react_node.data();
+    M.react_comp = meshes[0].react_comp;
+    return GD_OK;
+}
+
+static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icnn *psis, const gd_icnn *ylds,
+                      const gd_material *mat, const gd_load_path *paths, const gd_options *opt, gd_handle **out)
 {
     if (!out) return fail(nullptr, GD_ERR_ARG, "out is null");
     *out = nullptr;
-    if (!mesh || !mat || !path) return fail(nullptr, GD_ERR_ARG, "mesh, material or load path is null");
+    if (n_spec < 1) return fail(nullptr, GD_ERR_ARG, "n_spec must be at least 1");
+    if (!meshes || !mat || !paths) return fail(nullptr, GD_ERR_ARG, "mesh, material or load path is null");
     if (mat->energy < 0 || mat->energy > 2) return fail(nullptr, GD_ERR_ARG, "unknown energy kind");
     if (!(mat->eta_d > 0.0)) return fail(nullptr, GD_ERR_ARG, "eta_d must be positive");
-    if (path->n_steps < 0 || (path->n_steps > 0 && !path->load)) return fail(nullptr, GD_ERR_ARG, "load path");
     gd_status st;
-    if (mat->energy != GD_ENERGY_NEO_HOOKE && (st = validate_net(psi, 3, false, "energy"))) return st;
-    if ((st = validate_net(yield, 1, true, "yield"))) return st;
+    for (int s = 0; s < n_spec; ++s) {
+        const gd_load_path *path = paths + s;
+        if (path->n_steps < 0 || (path->n_steps > 0 && !path->load)) return fail(nullptr, GD_ERR_ARG, "load path");
+        if (mat->energy != GD_ENERGY_NEO_HOOKE && (st = validate_net(psis ? psis + s : nullptr, 3, false, "energy")))
+            return st;
+        if ((st = validate_net(ylds ? ylds + s : nullptr, 1, true, "yield"))) return st;
+    }
+    const gd_icnn *psi = psis, *yield = ylds;
+    const gd_load_path *path = paths;
+    Union U;
+    const gd_mesh *mesh = meshes;
+    if (n_spec > 1) {
+        if ((st = build_union(n_spec, meshes, U))) return st;
+        mesh = &U.mesh;
+    }
     gd_options o;
     if (opt) o = *opt;
     else gd_default_options(&o);
@@ -549,11 +1027,17 @@ gd_status gd_create(const gd_mesh *mesh, const gd_icnn *psi, const gd_icnn *yiel
     if (o.precision == GD_MIXED && o.newton_rtol < 1e-5) o.newton_rtol = 1e-5;
     if (o.newton_max < 0 || o.krylov_max < 1 || o.local_max < 1 || o.line_search_max < 0)
         return fail(nullptr, GD_ERR_ARG, "iteration caps");
+    if (o.inner_solve < GD_INNER_AUTO || o.inner_solve > GD_INNER_REFINED)
+        return fail(nullptr, GD_ERR_ARG, "inner_solve");
 
     const int dim = mesh->dim, nen = dim == 2 ? 4 : 8, ndof = dim + 1;
     const int64_t NN = mesh->n_nodes, NE = mesh->n_elems;
     Pattern P;
     if ((st = build_pattern(mesh, P))) return st;
+    if (n_spec > 1)                          // each specimen's own reaction component
+        for (int s = 0; s < n_spec; ++s)
+            for (int64_t j = U.react_off[s]; j < U.react_off[s + 1]; ++j)
+                P.react[j] = (int32_t)((int64_t)U.react_node[j] * ndof + U.react_comp[s]);
     std::vector<uint8_t> &fixed = P.fixed;
     std::vector<int32_t> &bc_dof = P.bc_dof, &react = P.react, &slot = P.slot;
     const int64_t n_dofs = NN * ndof, nnz = P.nnz;
@@ -572,6 +1056,12 @@ gd_status gd_create(const gd_mesh *mesh, const gd_icnn *psi, const gd_icnn *yiel
     H.opt = o;
     H.stream = (cudaStream_t)o.cuda_stream;
     H.load.assign(path->load, path->load + path->n_steps);
+    H.n_spec = n_spec;
+    H.paths.resize(n_spec);
+    for (int s = 0; s < n_spec; ++s) {
+        H.paths[s].assign(paths[s].load, paths[s].load + paths[s].n_steps);
+        H.n_steps_max = std::max(H.n_steps_max, paths[s].n_steps);
+    }
     H.mat.mu_e = mat->mu_e;
     H.mat.lambda_e = mat->lambda_e;
     H.mat.eta_d = mat->eta_d;
@@ -631,12 +1121,58 @@ gd_status gd_create(const gd_mesh *mesh, const gd_icnn *psi, const gd_icnn *yiel
     if (!react.empty())
         GD_CREATE_CUDA(cudaMemcpy(H.react_dof, react.data(), sizeof(int32_t) * react.size(), cudaMemcpyHostToDevice));
     // networks
-    if (mat->energy != GD_ENERGY_NEO_HOOKE) {
-        if ((st = stage_net(H, H.psi, 3, psi->width, psi->params))) return bail(st);
+    if (n_spec == 1) {
+        if (mat->energy != GD_ENERGY_NEO_HOOKE) {
+            if ((st = stage_net(H, H.psi, 3, psi->width, psi->params))) return bail(st);
+        }
+        if ((st = stage_net(H, H.yld, 1, yield->width, yield->params))) return bail(st);
+        GD_CREATE_CUDA(dalloc(&H.netc, 1));
+        GD_CREATE_CUDA(gd::launch_prep_nets(H.psi, H.yld, H.mat.energy, H.netc, H.stream));
+        H.wmax = std::max(H.psi.width, H.yld.width);
+    } else {
+        // per-specimen networks in device tables indexed by the element's specimen
+        H.h_psi_tab.resize(n_spec);
+        H.h_yld_tab.resize(n_spec);
+        GD_CREATE_CUDA(dalloc(&H.netc, (size_t)n_spec));
+        for (int s = 0; s < n_spec; ++s) {
+            if (mat->energy != GD_ENERGY_NEO_HOOKE) {
+                if ((st = stage_net(H, H.h_psi_tab[s], 3, psis[s].width, psis[s].params))) return bail(st);
+            }
+            if ((st = stage_net(H, H.h_yld_tab[s], 1, ylds[s].width, ylds[s].params))) return bail(st);
+            GD_CREATE_CUDA(gd::launch_prep_nets(H.h_psi_tab[s], H.h_yld_tab[s], H.mat.energy, H.netc + s, H.stream));
+            H.wmax = std::max(H.wmax, std::max(H.h_psi_tab[s].width, H.h_yld_tab[s].width));
+        }
+        GD_CREATE_CUDA(dalloc(&H.psi_tab, (size_t)n_spec));
+        GD_CREATE_CUDA(dalloc(&H.yld_tab, (size_t)n_spec));
+        GD_CREATE_CUDA(cudaMemcpy(H.psi_tab, H.h_psi_tab.data(), sizeof(gd::DevNet) * n_spec, cudaMemcpyHostToDevice));
+        GD_CREATE_CUDA(cudaMemcpy(H.yld_tab, H.h_yld_tab.data(), sizeof(gd::DevNet) * n_spec, cudaMemcpyHostToDevice));
+        // specimen maps
+        std::vector<int32_t> es((size_t)NE), ns((size_t)NN), bs((size_t)mesh->n_bc);
+        for (int s = 0; s < n_spec; ++s) {
+            for (int64_t e = U.elem_off[s]; e < U.elem_off[s + 1]; ++e) es[e] = s;
+            for (int64_t n = U.node_off[s]; n < U.node_off[s + 1]; ++n) ns[n] = s;
+            for (int64_t i = U.bc_off[s]; i < U.bc_off[s + 1]; ++i) bs[i] = s;
+            H.spec_nbc.push_back(U.bc_off[s + 1] - U.bc_off[s]);
+        }
+        H.h_node_off = U.node_off;
+        H.h_elem_off = U.elem_off;
+        GD_CREATE_CUDA(dalloc(&H.elem_spec, es.size()));
+        GD_CREATE_CUDA(dalloc(&H.node_spec, ns.size()));
+        GD_CREATE_CUDA(dalloc(&H.bc_spec, bs.size()));
+        GD_CREATE_CUDA(dalloc(&H.react_off, U.react_off.size()));
+        GD_CREATE_CUDA(dalloc(&H.node_off, U.node_off.size()));
+        GD_CREATE_CUDA(dalloc(&H.d_load, (size_t)2 * n_spec));
+        GD_CREATE_CUDA(dalloc(&H.d_norm, (size_t)2 * n_spec));
+        GD_CREATE_CUDA(dalloc(&H.d_coef, (size_t)n_spec));
+        H.d_factor = H.d_load + n_spec;
+        if (NE > 0) GD_CREATE_CUDA(cudaMemcpy(H.elem_spec, es.data(), sizeof(int32_t) * es.size(), cudaMemcpyHostToDevice));
+        GD_CREATE_CUDA(cudaMemcpy(H.node_spec, ns.data(), sizeof(int32_t) * ns.size(), cudaMemcpyHostToDevice));
+        if (!bs.empty()) GD_CREATE_CUDA(cudaMemcpy(H.bc_spec, bs.data(), sizeof(int32_t) * bs.size(), cudaMemcpyHostToDevice));
+        GD_CREATE_CUDA(cudaMemcpy(H.react_off, U.react_off.data(), sizeof(int64_t) * U.react_off.size(),
+                                  cudaMemcpyHostToDevice));
+        GD_CREATE_CUDA(cudaMemcpy(H.node_off, U.node_off.data(), sizeof(int64_t) * U.node_off.size(),
+                                  cudaMemcpyHostToDevice));
     }
-    if ((st = stage_net(H, H.yld, 1, yield->width, yield->params))) return bail(st);
-    GD_CREATE_CUDA(dalloc(&H.netc, 1));
-    GD_CREATE_CUDA(gd::launch_prep_nets(H.psi, H.yld, H.mat.energy, H.netc, H.stream));
     // state and work arrays
     const size_t nq_tot = (size_t)(NE * nen);
     double **vec_d[] = {&H.dofs, &H.dofs_prev, &H.w_dofs, &H.w_trial, &H.R, &H.R_trial, &H.diag};
@@ -651,6 +1187,8 @@ gd_status gd_create(const gd_mesh *mesh, const gd_icnn *psi, const gd_icnn *yiel
     GD_CREATE_CUDA(dalloc(&H.vals_trial, (size_t)nnz));
     GD_CREATE_CUDA(dalloc(&H.counters, 8));
     GD_CREATE_CUDA(dalloc(&H.binv, (size_t)(NN * ndof * ndof)));
+    GD_CREATE_CUDA(dalloc(&H.vals_f32, (size_t)nnz));
+    GD_CREATE_CUDA(dalloc(&H.kx, (size_t)n_dofs));
     H.krylov_grid = gd::krylov_blocks(ndof, o.precision == GD_MIXED, H.num_sms);
     if (H.krylov_grid < 1) {
         H.err = "no cooperative grid fits on this device";
@@ -665,6 +1203,36 @@ gd_status gd_create(const gd_mesh *mesh, const gd_icnn *psi, const gd_icnn *yiel
     GD_CREATE_CUDA(cudaStreamSynchronize(H.stream));
     *out = hh;
 #undef GD_CREATE_CUDA
+    return GD_OK;
+}
+
+gd_status gd_create(const gd_mesh *mesh, const gd_icnn *psi, const gd_icnn *yield, const gd_material *mat,
+                    const gd_load_path *path, const gd_options *opt, gd_handle **out)
+{
+    if (!mesh || !path) {
+        if (out) *out = nullptr;
+        return fail(nullptr, GD_ERR_ARG, "mesh, material or load path is null");
+    }
+    return create_impl(1, mesh, psi, yield, mat, path, opt, out);
+}
+
+gd_status gd_create_batch(int32_t n_spec, const gd_mesh *meshes, const gd_icnn *psi, const gd_icnn *yield,
+                          const gd_material *mat, const gd_load_path *paths, const gd_options *opt, gd_handle **out)
+{
+    return create_impl(n_spec, meshes, psi, yield, mat, paths, opt, out);
+}
+
+gd_status gd_batch_layout(gd_handle *h, int32_t *n_spec, int64_t *node_off, int64_t *elem_off, int32_t *n_steps)
+{
+    if (!h) return fail(nullptr, GD_ERR_ARG, "null handle");
+    gd::Handle &H = h->h;
+    if (n_spec) *n_spec = H.n_spec;
+    if (n_steps) *n_steps = H.n_steps_max;
+    for (int s = 0; s <= H.n_spec; ++s) {
+        const bool one = H.n_spec == 1;
+        if (node_off) node_off[s] = one ? (s ? H.n_nodes : 0) : H.h_node_off[s];
+        if (elem_off) elem_off[s] = one ? (s ? H.n_elems : 0) : H.h_elem_off[s];
+    }
     return GD_OK;
 }
 
@@ -686,6 +1254,7 @@ gd_status gd_set_params(gd_handle *h, const double *theta_psi, const double *the
 {
     if (!h) return fail(nullptr, GD_ERR_ARG, "null handle");
     gd::Handle &H = h->h;
+    if (H.n_spec > 1) return fail(&H, GD_ERR_STATE, "a batch keeps the networks given to gd_create_batch");
     if (theta_psi && H.psi.width > 0) {
         GD_CUDA(&H, cudaMemcpyAsync(H.psi.p, theta_psi, sizeof(double) * H.psi.n_params, cudaMemcpyDefault, H.stream));
         GD_CUDA(&H, gd::launch_transpose(H.psi, H.stream));
@@ -758,11 +1327,25 @@ gd_status gd_newton_step(gd_handle *h, gd_newton_report *rep)
 {
     if (!h) return fail(nullptr, GD_ERR_ARG, "null handle");
     gd::Handle &H = h->h;
-    if (H.next_step >= (int)H.load.size()) return fail(&H, GD_ERR_STATE, "load path already finished");
+    if (H.next_step >= H.n_steps_max) return fail(&H, GD_ERR_STATE, "load path already finished");
+    if (!H.rec_on) {
+        // record the path from here on for gd_backward
+        free_ckpts(H);
+        H.rec_load.clear();
+        H.rec_step.clear();
+        H.rec_start_step = H.next_step;
+        gd_status s0 = save_ckpt(H, 0);
+        if (s0) return s0;
+        H.rec_on = true;
+    }
     gd_newton_report r{};
-    gd_status st = advance(H, H.load[H.next_step], 0, r);
+    gd_status st = advance(H, (double)(H.next_step + 1), 0, r);
     if (rep) *rep = r;
-    if (st) return st;
+    if (st) {
+        H.rec_on = false;                   // a failed step ends the record
+        return st;
+    }
+    if (H.rec_on && !H.rec_step.empty()) H.rec_step.back() = H.next_step;
     ++H.next_step;
     return GD_OK;
 }
@@ -779,7 +1362,7 @@ gd_status gd_run_load_path(gd_handle *h, double *reaction, gd_path_report *rep)
     cudaEventCreate(&t1);
     cudaEventRecord(t0, H.stream);
     gd_status st = GD_OK;
-    while (H.next_step < (int)H.load.size()) {
+    while (H.next_step < H.n_steps_max) {
         gd_newton_report r{};
         const int s = H.next_step;
         st = gd_newton_step(h, &r);
@@ -787,7 +1370,8 @@ gd_status gd_run_load_path(gd_handle *h, double *reaction, gd_path_report *rep)
         pr.total_krylov += r.krylov_iterations;
         pr.step_cuts += r.step_cuts;
         if (st) break;
-        if (reaction) reaction[s] = r.reaction;
+        if (reaction)
+            for (int i = 0; i < H.n_spec; ++i) reaction[(size_t)s * H.n_spec + i] = H.last_reac[i];
         ++pr.steps_done;
     }
     cudaEventRecord(t1, H.stream);
@@ -819,24 +1403,170 @@ gd_status gd_set_state(gd_handle *h, const double *dofs, const double *kappa, in
 {
     if (!h) return fail(nullptr, GD_ERR_ARG, "null handle");
     gd::Handle &H = h->h;
-    if (next_step < 0 || next_step > (int)H.load.size()) return fail(&H, GD_ERR_ARG, "next_step out of range");
+    if (next_step < 0 || next_step > H.n_steps_max) return fail(&H, GD_ERR_ARG, "next_step out of range");
     if (dofs) GD_CUDA(&H, cudaMemcpyAsync(H.dofs, dofs, sizeof(double) * H.n_dofs, cudaMemcpyHostToDevice, H.stream));
     if (kappa)
         GD_CUDA(&H, cudaMemcpyAsync(H.kappa, kappa, sizeof(double) * H.n_elems * H.nq, cudaMemcpyHostToDevice, H.stream));
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));
     H.next_step = next_step;
+    H.rec_on = false;
     H.have_prev = false;
-    H.load_prev = next_step > 0 ? H.load[next_step - 1] : 0.0;
+    H.load_prev = (double)next_step;
     H.load_prevprev = H.load_prev;
     return GD_OK;
 }
 
 gd_status gd_backward(gd_handle *h, const double *dL_dreaction, double *dL_dtheta)
 {
-    (void)dL_dreaction;
-    (void)dL_dtheta;
     if (!h) return fail(nullptr, GD_ERR_ARG, "null handle");
-    return fail(&h->h, GD_ERR_STATE, "gd_backward: the adjoint is not built into this library yet");
+    gd::Handle &H = h->h;
+    if (!dL_dreaction || !dL_dtheta) return fail(&H, GD_ERR_ARG, "null argument");
+    if (H.opt.precision != GD_FP64) return fail(&H, GD_ERR_STATE, "gd_backward needs GD_FP64 precision");
+    if (H.n_spec > 1) return fail(&H, GD_ERR_STATE, "gd_backward takes a single-specimen handle");
+    if (!H.rec_on || H.rec_load.empty() || H.ckpts.empty())
+        return fail(&H, GD_ERR_STATE, "no recorded load path: run gd_newton_step / gd_run_load_path first");
+    const int M = (int)H.rec_load.size();
+    const int64_t nq_tot = H.n_elems * H.nq;
+    const int kseg = H.opt.checkpoint_every > 0 ? H.opt.checkpoint_every : 1;
+    const int n_theta = H.psi.n_params + H.yld.n_params;
+    // --- work space ---
+    if (!H.perm_T) {
+        std::vector<int32_t> perm((size_t)H.nnz);
+        for (int64_t r = 0; r < H.n_dofs; ++r)
+            for (int32_t p = H.h_rowptr[r]; p < H.h_rowptr[r + 1]; ++p) {
+                const int32_t c = H.h_colidx[p];
+                const int32_t *b0 = H.h_colidx.data() + H.h_rowptr[c], *b1 = H.h_colidx.data() + H.h_rowptr[c + 1];
+                perm[p] = (int32_t)(H.h_rowptr[c] + (std::lower_bound(b0, b1, (int32_t)r) - b0));
+            }
+        GD_CUDA(&H, dalloc(&H.perm_T, (size_t)H.nnz));
+        GD_CUDA(&H, cudaMemcpy(H.perm_T, perm.data(), sizeof(int32_t) * H.nnz, cudaMemcpyHostToDevice));
+        GD_CUDA(&H, dalloc(&H.vals_T, (size_t)H.nnz));
+        for (double *&p : H.adj_v) GD_CUDA(&H, dalloc(&p, (size_t)H.n_dofs));
+        GD_CUDA(&H, dalloc(&H.kbar, (size_t)nq_tot));
+        GD_CUDA(&H, dalloc(&H.kbar2, (size_t)nq_tot));
+        GD_CUDA(&H, dalloc(&H.theta_bar, (size_t)(n_theta > 0 ? n_theta : 1)));
+        GD_CUDA(&H, dalloc(&H.glob, 4));
+    }
+    if (H.seg_cap < kseg + 1) {
+        dfree(H.seg);
+        H.seg = nullptr;
+        GD_CUDA(&H, dalloc(&H.seg, (size_t)(kseg + 1) * (H.n_dofs + nq_tot)));
+        H.seg_cap = kseg + 1;
+    }
+    double *er = H.adj_v[0], *y = H.adj_v[1], *S = H.adj_v[2], *rhs = H.adj_v[3], *lam = H.adj_v[4],
+           *w = H.adj_v[5];
+    // reaction indicator e_r
+    {
+        std::vector<double> e((size_t)H.n_dofs, 0.0);
+        std::vector<int32_t> rd((size_t)H.n_react);
+        if (H.n_react > 0)
+            GD_CUDA(&H, cudaMemcpy(rd.data(), H.react_dof, sizeof(int32_t) * H.n_react, cudaMemcpyDeviceToHost));
+        for (int32_t d : rd) e[d] += 1.0;
+        GD_CUDA(&H, cudaMemcpy(er, e.data(), sizeof(double) * H.n_dofs, cudaMemcpyHostToDevice));
+    }
+    // save the committed end state, restored at the end
+    gd::Checkpoint end;
+    {
+        gd_status s0 = save_ckpt(H, M);
+        if (s0) return s0;
+        end = H.ckpts.back();
+        H.ckpts.pop_back();
+    }
+    const int end_step = H.next_step;
+    GD_CUDA(&H, cudaMemsetAsync(H.kbar, 0, sizeof(double) * nq_tot, H.stream));
+    GD_CUDA(&H, cudaMemsetAsync(H.theta_bar, 0, sizeof(double) * (n_theta > 0 ? n_theta : 1), H.stream));
+    GD_CUDA(&H, cudaMemsetAsync(H.glob, 0, sizeof(double) * 4, H.stream));
+    gd_status st = GD_OK;
+    H.replaying = true;
+    for (int ci = (int)H.ckpts.size() - 1; ci >= 0 && st == GD_OK; --ci) {
+        const int c0 = H.ckpts[ci].commit;
+        const int c1 = (ci + 1 < (int)H.ckpts.size()) ? H.ckpts[ci + 1].commit : M;
+        if (c1 <= c0) continue;
+        // recompute the segment's states from its checkpoint
+        if ((st = restore_ckpt(H, H.ckpts[ci]))) break;
+        auto seg_d = [&](int i) { return H.seg + (size_t)i * (H.n_dofs + nq_tot); };
+        auto seg_k = [&](int i) { return seg_d(i) + H.n_dofs; };
+        GD_CUDA(&H, cudaMemcpyAsync(seg_d(0), H.dofs, sizeof(double) * H.n_dofs, cudaMemcpyDeviceToDevice, H.stream));
+        GD_CUDA(&H, cudaMemcpyAsync(seg_k(0), H.kappa, sizeof(double) * nq_tot, cudaMemcpyDeviceToDevice, H.stream));
+        for (int c = c0 + 1; c <= c1 && st == GD_OK; ++c) {
+            const double target = H.rec_load[c - 1];
+            if ((st = predict(H, target))) break;
+            gd_newton_report sub{};
+            st = newton(H, sub);
+            if (st == GD_OK && !sub.converged)
+                st = fail(&H, GD_ERR_NOT_CONVERGED, "recomputation of load commit " + std::to_string(c) + " failed");
+            if (st) break;
+            gd_newton_report cr{};
+            if ((st = commit(H, target, cr))) break;
+            GD_CUDA(&H, cudaMemcpyAsync(seg_d(c - c0), H.dofs, sizeof(double) * H.n_dofs, cudaMemcpyDeviceToDevice,
+                                        H.stream));
+            GD_CUDA(&H, cudaMemcpyAsync(seg_k(c - c0), H.kappa, sizeof(double) * nq_tot, cudaMemcpyDeviceToDevice,
+                                        H.stream));
+        }
+        if (st) break;
+        // reverse sweep through the segment
+        for (int c = c1; c > c0 && st == GD_OK; --c) {
+            const int step = H.rec_step[c - 1];
+            const double fbar = step >= 0 ? dL_dreaction[step - H.rec_start_step] : 0.0;
+            const double *d_c = seg_d(c - c0), *k_c = seg_k(c - c0), *k_p = seg_k(c - c0 - 1);
+            // tangent at the converged state of commit c
+            if ((st = assemble_pass(H, d_c, k_p, H.R_trial, H.vals, H.kappa_trial2, H.loading2, 1))) break;
+            GD_CUDA(&H, gd::launch_gather(H.vals, H.perm_T, H.vals_T, H.nnz, H.stream));
+            // source (dkappa/dd)^T kbar
+            GD_CUDA(&H, cudaMemsetAsync(S, 0, sizeof(double) * H.n_dofs, H.stream));
+            gd::AdjArgs A;
+            A.n_elems = H.n_elems;
+            A.conn = H.conn;
+            A.X = H.X;
+            A.dofs = d_c;
+            A.kappa_prev = k_p;
+            A.kappa_cur = k_c;
+            A.w = nullptr;
+            A.kbar = H.kbar;
+            A.kbar_prev = nullptr;
+            A.rhs = S;
+            A.theta_bar = H.theta_bar;
+            A.glob = H.glob;
+            A.psi = H.psi;
+            A.yld = H.yld;
+            A.netc = H.netc;
+            A.mat = H.mat;
+            A.mode = 0;
+            GD_CUDA(&H, gd::launch_adjoint(H.dim, A, H.num_sms, H.stream));
+            // y = K^T e_r
+            gd::SolverCtx cT = solver_ctx(H, H.vals_T);
+            if (fbar != 0.0) GD_CUDA(&H, gd::launch_spmv(cT, er, y, 0));
+            GD_CUDA(&H, gd::launch_adj_rhs(H.n_dofs, S, fbar != 0.0 ? y : nullptr, fbar, H.fixed, rhs, H.stream));
+            // K^T lambda = rhs on the free dofs (FP64)
+            int kit = 0;
+            double rel = 0.0;
+            if ((st = krylov(H, H.vals_T, rhs, lam, kit, rel, H.opt.krylov_rtol, false,
+                             std::max(H.opt.krylov_rtol, 1e-10))))
+                break;
+            GD_CUDA(&H, gd::launch_axpby(H.n_dofs, w, lam, fbar, er, H.stream));
+            A.mode = 1;
+            A.w = w;
+            A.kbar_prev = H.kbar2;
+            A.rhs = nullptr;
+            GD_CUDA(&H, gd::launch_adjoint(H.dim, A, H.num_sms, H.stream));
+            std::swap(H.kbar, H.kbar2);
+        }
+    }
+    H.replaying = false;
+    if (st == GD_OK) {
+        GD_CUDA(&H, gd::launch_adjoint_globals(H.psi, H.yld, H.mat.energy, H.glob, H.theta_bar, H.stream));
+        if (n_theta > 0)
+            GD_CUDA(&H, cudaMemcpyAsync(dL_dtheta, H.theta_bar, sizeof(double) * n_theta, cudaMemcpyDeviceToHost,
+                                        H.stream));
+    }
+    // back to the end of the path
+    gd_status s2 = restore_ckpt(H, end);
+    dfree(end.dofs);
+    dfree(end.dofs_prev);
+    dfree(end.kappa);
+    H.next_step = end_step;
+    GD_CUDA(&H, cudaStreamSynchronize(H.stream));
+    return st ? st : s2;
 }
 
 }  // extern "C"

@@ -40,6 +40,18 @@ struct MatF {
 struct NcF {
     float psi_N0, psi_n, y_N0, y_s;
 };
+__device__ __forceinline__ NcF ncf(const NetConst &n)
+{
+    NcF r = {(float)n.psi_N0, (float)n.psi_n, (float)n.y_N0, (float)n.y_s};
+    return r;
+}
+template <class Args>
+__device__ __forceinline__ int spec_of(const Args &A, int64_t e) { return A.elem_spec ? __ldg(A.elem_spec + e) : 0; }
+template <class Args>
+__device__ __forceinline__ const DevNet &psi_of(const Args &A, int s) { return A.psi_tab ? A.psi_tab[s] : A.psi; }
+template <class Args>
+__device__ __forceinline__ const DevNet &yld_of(const Args &A, int s) { return A.yld_tab ? A.yld_tab[s] : A.yld; }
+
 __device__ __forceinline__ MatF to_f(const MatConst &m)
 {
     MatF r;
@@ -282,7 +294,7 @@ __device__ void yield_unit(const DevNet &net, const NcF &nc, float q, float &G, 
 
 // r(kappa) = G(q(kappa)) - kappa and dr/dkappa (Eq. (potential_function)),
 // q = psi_e + qcoef (phi - kappa) / f_d(kappa) (Eq. (ostwald_potential)).
-__device__ __forceinline__ void r_slope(const AsmArgs &A, const MatF &m, const NcF &nc, float pe, float phi,
+__device__ __forceinline__ void r_slope(const DevNet &yld, const MatF &m, const NcF &nc, float pe, float phi,
                                         float kappa, float &r, float &dr, float &Gp, float *buf, int lane)
 {
     bool dmg = kappa > m.kappa_d;
@@ -290,7 +302,7 @@ __device__ __forceinline__ void r_slope(const AsmArgs &A, const MatF &m, const N
     float q = pe + m.qcoef * (phi - kappa) / f;
     float dq = m.qcoef * (-1.0f / f + (dmg ? (phi - kappa) * m.eta_d / f : 0.0f));
     float G;
-    yield_unit(A.yld, nc, q, G, Gp, buf, lane);
+    yield_unit(yld, nc, q, G, Gp, buf, lane);
     r = G - kappa;
     dr = Gp * dq - 1.0f;
 }
@@ -303,8 +315,7 @@ __global__ void __launch_bounds__(32 * kWarps) asm_fp32_kernel(AsmArgs A)
     extern __shared__ float smem_f[];
     float *smem = smem_f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wpsi = A.psi.width, wy = A.yld.width;
-    const int wmax = wpsi > wy ? wpsi : wy;
+    const int wmax = A.wmax;
     // per-warp scratch
     const int scratch = EPW * NEN * (DIM + NDOF) + 32 * Q_REC + 32 * 4 + 32 * 10 + 5 * wmax + 2 * NQ * NEN * V_REC;
     float *ws = smem + warp * scratch;
@@ -315,7 +326,6 @@ __global__ void __launch_bounds__(32 * kWarps) asm_fp32_kernel(AsmArgs A)
     float *sOut = sIn + 32 * 4;                      // [32][10]: N, grad, Hess / local-solve results
     float *sBuf = sOut + 32 * 10;                    // unit-mode buffers
     float *sVec = sBuf + 5 * wmax;                   // [EPR*NQ*NEN][V_REC]
-    const NcF nc = {(float)A.netc->psi_N0, (float)A.netc->psi_n, (float)A.netc->y_N0, (float)A.netc->y_s};
     const MatF m = to_f(A.mat);
 
     const int64_t n_batches = (A.n_elems + EPW - 1) / EPW;
@@ -345,6 +355,7 @@ __global__ void __launch_bounds__(32 * kWarps) asm_fp32_kernel(AsmArgs A)
         const int el = lane / NQ, q = lane % NQ;
         const int64_t e_me = e0 + el;
         const bool valid = e_me < A.n_elems;
+        const NcF nc = ncf(A.netc[valid ? spec_of(A, e_me) : 0]);
         float *rec = sRec + lane * Q_REC;
         float F[3][3], H[3][3], phi = 0.0f, g[3] = {0.0f, 0.0f, 0.0f}, x[3], Jdet;
         {
@@ -474,7 +485,7 @@ __global__ void __launch_bounds__(32 * kWarps) asm_fp32_kernel(AsmArgs A)
             for (int p = 0; p < 32; ++p) {
                 if (e0 + p / NQ >= A.n_elems) break;
                 float y[3] = {sIn[p * 4], sIn[p * 4 + 1], sIn[p * 4 + 2]}, out[10];
-                psi_net_unit(A.psi, y, out, sBuf, lane);
+                psi_net_unit(psi_of(A, spec_of(A, e0 + p / NQ)), y, out, sBuf, lane);
                 if (lane == 0)
 #pragma unroll
                     for (int c = 0; c < 10; ++c) sOut[p * 10 + c] = out[c];
@@ -540,10 +551,13 @@ __global__ void __launch_bounds__(32 * kWarps) asm_fp32_kernel(AsmArgs A)
         for (int p = 0; p < 32; ++p) {
             if (e0 + p / NQ >= A.n_elems) break;
             const float ppe = sIn[p * 4], pphi = sIn[p * 4 + 1], kn = sIn[p * 4 + 2];
+            const int sp = spec_of(A, e0 + p / NQ);
+            const DevNet &yn = yld_of(A, sp);
+            const NcF ncp = ncf(A.netc[sp]);
             const double kn_d = __ldg(A.kappa_n + e0 * NQ + p);
             float r, dr, Gp;
             int n_eval = 1;
-            r_slope(A, m, nc, ppe, pphi, kn, r, dr, Gp, sBuf, lane);
+            r_slope(yn, m, ncp, ppe, pphi, kn, r, dr, Gp, sBuf, lane);
             // loading/unloading decided in FP64: Phi_d(kappa_n) = G(q(kappa_n)) - kappa_n > 0
             const double phi_trial = (double)(r + kn) - kn_d;
             float kappa = kn, fail = 0.0f, loading = 0.0f;
@@ -552,19 +566,19 @@ __global__ void __launch_bounds__(32 * kWarps) asm_fp32_kernel(AsmArgs A)
                 float lo = kn, step = r > 1e-12 ? r : 1e-12, hi = kn + step;
                 int grow = 0;
                 float rh, drh, gph;
-                r_slope(A, m, nc, ppe, pphi, hi, rh, drh, gph, sBuf, lane);
+                r_slope(yn, m, ncp, ppe, pphi, hi, rh, drh, gph, sBuf, lane);
                 ++n_eval;
                 while (rh > 0.0f && grow < 200) {
                     lo = hi;
                     step *= 2.0f;
                     hi = kn + step;
                     ++grow;
-                    r_slope(A, m, nc, ppe, pphi, hi, rh, drh, gph, sBuf, lane);
+                    r_slope(yn, m, ncp, ppe, pphi, hi, rh, drh, gph, sBuf, lane);
                     ++n_eval;
                 }
                 if (grow >= 200) fail = 1.0f;
                 kappa = lo;
-                r_slope(A, m, nc, ppe, pphi, kappa, r, dr, Gp, sBuf, lane);
+                r_slope(yn, m, ncp, ppe, pphi, kappa, r, dr, Gp, sBuf, lane);
                 ++n_eval;
                 float dx_prev = hi - lo, dx = dx_prev;
                 int it;
@@ -581,7 +595,7 @@ __global__ void __launch_bounds__(32 * kWarps) asm_fp32_kernel(AsmArgs A)
                         dx = 0.5f * (hi - lo);
                         kappa = lo + dx;
                     }
-                    r_slope(A, m, nc, ppe, pphi, kappa, r, dr, Gp, sBuf, lane);
+                    r_slope(yn, m, ncp, ppe, pphi, kappa, r, dr, Gp, sBuf, lane);
                     ++n_eval;
                     if (r > 0.0f) lo = kappa; else hi = kappa;
                 }
@@ -837,8 +851,7 @@ size_t smem_bytes(int wmax)
 template <int DIM>
 cudaError_t launch_dim(const AsmArgs &a, int num_sms, cudaStream_t s)
 {
-    int wmax = a.psi.width > a.yld.width ? a.psi.width : a.yld.width;
-    size_t sm = smem_bytes<DIM>(wmax);
+    size_t sm = smem_bytes<DIM>(a.wmax);
     cudaError_t err = cudaFuncSetAttribute(asm_fp32_kernel<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
     int per_sm = 0;

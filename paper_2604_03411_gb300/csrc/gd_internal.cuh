@@ -54,10 +54,43 @@ struct AsmArgs {
     const int32_t *slot;     // [E * nen * nen] CSR position of (row node a dof 0, col node b dof 0)
     const int32_t *rowptr;   // [n_dofs + 1]
     DevNet psi, yld;
-    const NetConst *netc;
+    const NetConst *netc;    // [n_spec]
     MatConst mat;
     int tangent;
     int *counters;           // [0] local-solve failures, [1] loading points, [2] yield-network evaluations
+    // batched specimens (null for a single specimen): specimen of every element and
+    // the per-specimen networks; netc is then indexed by specimen
+    const int32_t *elem_spec;
+    const DevNet *psi_tab, *yld_tab;
+    int wmax;                // widest network over all specimens
+};
+
+// adjoint element kernel (gd_adjoint.cu)
+struct AdjArgs {
+    int64_t n_elems;
+    const int32_t *conn;
+    const double *X;
+    const double *dofs;        // d_n
+    const double *kappa_prev;  // kappa_{n-1}
+    const double *kappa_cur;   // kappa_n
+    const double *w;           // nodal adjoint weights (mode 1)
+    const double *kbar;        // dL/dkappa_n
+    double *kbar_prev;         // out (mode 1): dL/dkappa_{n-1}
+    double *rhs;               // out (mode 0): (dkappa/dd)^T kbar, accumulated
+    double *theta_bar;         // out (mode 1): packed [psi | yield] gradient, accumulated
+    double *glob;              // out (mode 1): weights of N(0), n, N_k(0), N_k'(0), accumulated
+    DevNet psi, yld;
+    const NetConst *netc;
+    MatConst mat;
+    int mode;
+};
+
+// a stored state of the load path (for the adjoint's recomputation)
+struct Checkpoint {
+    int commit = 0;                 // number of commits before this state
+    double *dofs = nullptr, *dofs_prev = nullptr, *kappa = nullptr;
+    double load_prev = 0.0, load_prevprev = 0.0;
+    bool have_prev = false;
 };
 
 struct Handle {
@@ -80,15 +113,31 @@ struct Handle {
     std::vector<int32_t> h_rowptr, h_colidx;
     // constitutive data
     DevNet psi, yld;
-    NetConst *netc = nullptr;
+    NetConst *netc = nullptr;                            // [n_spec]
     MatConst mat{};
+    // batched specimens
+    int n_spec = 1;
+    int wmax = 0;
+    int32_t *elem_spec = nullptr;                        // [n_elems] (null: one specimen)
+    DevNet *psi_tab = nullptr, *yld_tab = nullptr;       // [n_spec] device tables
+    std::vector<DevNet> h_psi_tab, h_yld_tab;            // host copies (own the parameter buffers)
+    std::vector<std::vector<double>> paths;              // per-specimen load paths
+    int n_steps_max = 0;
+    int32_t *node_spec = nullptr, *bc_spec = nullptr;    // [n_nodes], [n_bc] (batches only)
+    int64_t *react_off = nullptr;                        // [n_spec + 1] device (batches only)
+    int64_t *node_off = nullptr;                         // [n_spec + 1] device (batches only)
+    std::vector<int64_t> h_node_off, h_elem_off;         // [n_spec + 1]
+    std::vector<int64_t> spec_nbc;                       // prescribed dofs per specimen
+    double *d_load = nullptr, *d_factor = nullptr;       // [n_spec] device (batches only)
+    double *d_norm = nullptr, *d_coef = nullptr;         // [2 n_spec], [n_spec] device (batches only)
+    std::vector<double> last_reac;                       // per-specimen reactions of the last commit
     gd_options opt{};
     cudaStream_t stream = nullptr;
     std::vector<double> load;
     // state
     double *dofs = nullptr, *kappa = nullptr;            // committed
     double *dofs_prev = nullptr;                         // state before the last committed step
-    double load_prev = 0.0, load_prevprev = 0.0;
+    double load_prev = 0.0, load_prevprev = 0.0;         // step coordinates t of the last two commits
     bool have_prev = false;
     int next_step = 0;
     // work arrays
@@ -102,6 +151,8 @@ struct Handle {
     double *kv[10] = {};
     double *diag = nullptr;
     double *binv = nullptr;                              // node-block Jacobi inverses
+    float *vals_f32 = nullptr;                           // FP32 tangent copy for the inner solve (FP64 mode)
+    double *kx = nullptr;                                // FP32 iterate storage
     int krylov_grid = 0;
     double *red = nullptr;                               // device reduction buffers
     double *scal = nullptr;                              // device scalars
@@ -111,6 +162,18 @@ struct Handle {
     double assembly_ms = 0.0, krylov_ms = 0.0;
     int assemblies = 0;
     long long launches = 0;                              // kernels launched by this handle
+    // record of the forward path for the adjoint
+    bool rec_on = false;
+    bool replaying = false;
+    int rec_start_step = 0;
+    std::vector<double> rec_load;                        // load of every commit
+    std::vector<int> rec_step;                           // path step finished by the commit, or -1
+    std::vector<Checkpoint> ckpts;
+    // adjoint work space (allocated by the first gd_backward)
+    int32_t *perm_T = nullptr;
+    double *vals_T = nullptr, *adj_v[6] = {}, *kbar = nullptr, *kbar2 = nullptr, *theta_bar = nullptr,
+           *glob = nullptr, *seg = nullptr;
+    int seg_cap = 0;
     std::string err;
     int num_sms = 0;
 };
@@ -123,6 +186,9 @@ cudaError_t launch_prep_nets(const DevNet &psi, const DevNet &yld, int energy, N
 cudaError_t launch_transpose(const DevNet &net, cudaStream_t s);
 cudaError_t launch_assemble_fp64(int dim, const AsmArgs &a, int num_sms, cudaStream_t s);
 cudaError_t launch_assemble_fp32(int dim, const AsmArgs &a, int num_sms, cudaStream_t s);
+cudaError_t launch_adjoint(int dim, const AdjArgs &a, int num_sms, cudaStream_t s);
+cudaError_t launch_adjoint_globals(const DevNet &psi, const DevNet &yld, int energy, const double *glob,
+                                   double *theta_bar, cudaStream_t s);
 // FP32 copies of a network's parameters and transposed W2
 cudaError_t launch_net_to_float(const DevNet &net, cudaStream_t s);
 
@@ -150,11 +216,27 @@ int bicgstab(const SolverCtx &c, const double *diag, const double *b, double *x,
              double rtol, int max_it, double *final_rel);
 cudaError_t launch_norm2_free(const SolverCtx &c, const double *v, double *out_dev, double *out_fixed_dev);
 cudaError_t launch_axpy_free(const SolverCtx &c, double *y, const double *x, double alpha);
+// r = b - y on free dofs (0 on prescribed), *out_norm = ||r|| (device)
+cudaError_t launch_residual(const SolverCtx &c, const double *b, const double *y, double *r, double *out_norm);
 cudaError_t launch_predictor(int64_t n, double *out, const double *cur, const double *prev, double factor,
                              const int32_t *bc_dof, const double *bc_scale, int64_t n_bc, double load,
                              cudaStream_t s);
 cudaError_t launch_reaction(const double *R, const int32_t *react_dof, int64_t n_react, double *out,
                             cudaStream_t s);
+cudaError_t launch_gather(const double *in, const int32_t *perm, double *out, int64_t n, cudaStream_t s);
+cudaError_t launch_predictor_batch(int64_t n, int ndof, double *out, const double *cur, const double *prev,
+                                   const double *factor, const int32_t *node_spec, const int32_t *bc_dof,
+                                   const double *bc_scale, const int32_t *bc_spec, const double *load, int64_t n_bc,
+                                   cudaStream_t s);
+cudaError_t launch_norms_batch(const double *R, const uint8_t *fixed, const int64_t *node_off, int ndof, int n_spec,
+                               double *out, cudaStream_t s);
+cudaError_t launch_scale_spec(int64_t n, int ndof, double *out, const double *in, const double *coef,
+                              const int32_t *node_spec, const uint8_t *fixed, int accumulate, cudaStream_t s);
+cudaError_t launch_reaction_batch(const double *R, const int32_t *react_dof, const int64_t *off, int n_spec,
+                                  double *out, cudaStream_t s);
+cudaError_t launch_adj_rhs(int64_t n, const double *sv, const double *y, double fbar, const uint8_t *fixed,
+                           double *out, cudaStream_t s);
+cudaError_t launch_axpby(int64_t n, double *out, const double *x, double b, const double *y, cudaStream_t s);
 cudaError_t launch_damage_max(const double *kappa, int64_t n, double eta_d, double kappa_d, double *out,
                               cudaStream_t s);
 
@@ -166,6 +248,7 @@ struct KrylovCtx {
     const uint8_t *fixed;
     double *binv;               // [n_nodes * ndof * ndof]
     double *work[8];            // [n_nodes * ndof] each
+    double *work_x;             // iterate when the vectors are FP32
     double *red;                // [8 * blocks]
     double *out;                // [3] device: iterations, relative residual, status
     cudaStream_t stream;
@@ -174,7 +257,9 @@ struct KrylovCtx {
 };
 int krylov_blocks(int ndof, bool fp32_vals, int num_sms);
 // Solves K x = b on the free dofs; the result and statistics land in x and c.out.
+// fp32_vectors: the iteration runs on FP32 values and vectors (dot products stay FP64).
 cudaError_t krylov_solve(const KrylovCtx &c, const void *vals, bool fp32_vals, const double *b, double *x,
-                         double rtol, int max_it);
+                         double rtol, int max_it, bool fp32_vectors = false);
+cudaError_t narrow_to_float(const double *in, float *out, int64_t n, cudaStream_t s);
 
 }  // namespace gd

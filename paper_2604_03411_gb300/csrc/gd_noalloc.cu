@@ -77,6 +77,7 @@ extern "C" gd_status gd_solve_noalloc(int32_t ndof, int64_t n_nodes, const int32
     kc.colidx = colidx;
     kc.fixed = fixed;
     for (int k = 0; k < 8; ++k) kc.work[k] = base + (size_t)k * n;
+    kc.work_x = nullptr;
     kc.binv = base + 8 * kVec;
     kc.red = base + 12 * kVec;
     kc.out = kc.red + 8 * (size_t)kMaxBlocks;

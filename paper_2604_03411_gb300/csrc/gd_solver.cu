@@ -326,6 +326,80 @@ __global__ void set_bc_kernel(double *out, const int32_t *bc_dof, const double *
         out[bc_dof[i]] = bc_scale[i] * load;
 }
 
+// batched specimens: per-specimen extrapolation factor and prescribed load
+__global__ void predictor_batch_kernel(int64_t n, int ndof, double *out, const double *cur, const double *prev,
+                                       const double *factor, const int32_t *node_spec)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double f = factor[node_spec[i / ndof]];
+        out[i] = (prev && f != 0.0) ? cur[i] + f * (cur[i] - prev[i]) : cur[i];
+    }
+}
+__global__ void set_bc_batch_kernel(double *out, const int32_t *bc_dof, const double *bc_scale, const int32_t *bc_spec,
+                                    const double *load, int64_t n_bc)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_bc; i += (int64_t)gridDim.x * blockDim.x)
+        out[bc_dof[i]] = bc_scale[i] * load[bc_spec[i]];
+}
+// one block per specimen: sum of R over its reaction dofs [off[s], off[s+1])
+__global__ void reaction_batch_kernel(const double *R, const int32_t *react_dof, const int64_t *off, double *out)
+{
+    const int s = blockIdx.x;
+    double acc = 0.0;
+    for (int64_t j = off[s] + threadIdx.x; j < off[s + 1]; j += blockDim.x) acc += R[react_dof[j]];
+    __shared__ double sh[32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = (threadIdx.x < blockDim.x / 32) ? sh[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) out[s] = t;
+    }
+}
+
+// one block per specimen: ||R|| over its free and its prescribed dofs
+// (dofs [node_off[s] * ndof, node_off[s + 1] * ndof))
+__global__ void norms_batch_kernel(const double *R, const uint8_t *fixed, const int64_t *node_off, int ndof,
+                                   double *out)
+{
+    const int s = blockIdx.x;
+    double a = 0.0, b = 0.0;
+    for (int64_t i = node_off[s] * ndof + threadIdx.x; i < node_off[s + 1] * ndof; i += blockDim.x) {
+        const double r = R[i];
+        if (fixed[i]) b += r * r;
+        else a += r * r;
+    }
+    __shared__ double sa[32], sb[32];
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if ((threadIdx.x & 31) == 0) {
+        sa[threadIdx.x >> 5] = a;
+        sb[threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const bool in = threadIdx.x < blockDim.x / 32;
+        a = warp_sum(in ? sa[threadIdx.x] : 0.0);
+        b = warp_sum(in ? sb[threadIdx.x] : 0.0);
+        if (threadIdx.x == 0) {
+            out[2 * s] = sqrt(a);
+            out[2 * s + 1] = sqrt(b);
+        }
+    }
+}
+
+// free dofs: out = coef[spec] * in (accumulate = 0) or out += coef[spec] * in
+// (accumulate = 1); prescribed dofs: 0 (accumulate = 0) or unchanged
+__global__ void scale_spec_kernel(int64_t n, int ndof, double *out, const double *in, const double *coef,
+                                  const int32_t *node_spec, const uint8_t *fixed, int accumulate)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = fixed[i] ? 0.0 : coef[node_spec[i / ndof]] * in[i];
+        out[i] = accumulate ? out[i] + v : v;
+    }
+}
+
 __global__ void reaction_kernel(const double *R, const int32_t *react_dof, int64_t n_react, double *out)
 {
     double s = 0.0;
@@ -360,6 +434,40 @@ __global__ void damage_max_kernel(const double *kappa, int64_t n, double eta_d, 
 inline void count(const SolverCtx &c, int n = 1)
 {
     if (c.launches) *c.launches += n;
+}
+
+__global__ void gather_kernel(const double *in, const int32_t *perm, double *out, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[perm[i]];
+}
+// out = -(fbar y + s) on free dofs, 0 on prescribed dofs
+__global__ void adj_rhs_kernel(int64_t n, const double *s, const double *y, double fbar, const uint8_t *fixed,
+                               double *out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = fixed[i] ? 0.0 : -(fbar * (y ? y[i] : 0.0) + s[i]);
+}
+// r = b - y on free dofs, 0 on prescribed dofs; partial ||r||^2
+__global__ void __launch_bounds__(kThreads) resid_kernel(int64_t n, const double *b, const double *y,
+                                                         const uint8_t *fixed, double *r, double *red, int nb)
+{
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = fixed[i] ? 0.0 : b[i] - y[i];
+        r[i] = v;
+        s += v * v;
+    }
+    double v2[2] = {s, 0.0};
+    const int sl[2] = {S_MISC, S_MISC + 1};
+    block_partials<2>(v2, red, sl, nb);
+}
+
+// out = x + b y
+__global__ void axpby_kernel(int64_t n, double *out, const double *x, double b, const double *y)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = x[i] + b * y[i];
 }
 
 int vec_grid(int64_t n, int nb) { return (int)((n + kThreads - 1) / kThreads < nb ? (n + kThreads - 1) / kThreads : nb); }
@@ -471,6 +579,64 @@ cudaError_t launch_predictor(int64_t n, double *out, const double *cur, const do
         if (gb > 1024) gb = 1024;
         set_bc_kernel<<<gb, kThreads, 0, s>>>(out, bc_dof, bc_scale, n_bc, load);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const SolverCtx &c, const double *b, const double *y, double *r, double *out_norm)
+{
+    count(c, 2);
+    resid_kernel<<<c.blocks, kThreads, 0, c.stream>>>(c.n, b, y, c.fixed, r, c.red, c.blocks);
+    norm_finish_kernel<<<1, kThreads, 0, c.stream>>>(c.red, c.blocks, out_norm, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const double *in, const int32_t *perm, double *out, int64_t n, cudaStream_t s)
+{
+    gather_kernel<<<1024, 256, 0, s>>>(in, perm, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_rhs(int64_t n, const double *sv, const double *y, double fbar, const uint8_t *fixed, double *out,
+                           cudaStream_t s)
+{
+    adj_rhs_kernel<<<512, 256, 0, s>>>(n, sv, y, fbar, fixed, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(int64_t n, double *out, const double *x, double b, const double *y, cudaStream_t s)
+{
+    axpby_kernel<<<512, 256, 0, s>>>(n, out, x, b, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_predictor_batch(int64_t n, int ndof, double *out, const double *cur, const double *prev,
+                                   const double *factor, const int32_t *node_spec, const int32_t *bc_dof,
+                                   const double *bc_scale, const int32_t *bc_spec, const double *load, int64_t n_bc,
+                                   cudaStream_t s)
+{
+    predictor_batch_kernel<<<1024, kThreads, 0, s>>>(n, ndof, out, cur, prev, factor, node_spec);
+    if (n_bc > 0) set_bc_batch_kernel<<<256, kThreads, 0, s>>>(out, bc_dof, bc_scale, bc_spec, load, n_bc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norms_batch(const double *R, const uint8_t *fixed, const int64_t *node_off, int ndof, int n_spec,
+                               double *out, cudaStream_t s)
+{
+    norms_batch_kernel<<<n_spec, 256, 0, s>>>(R, fixed, node_off, ndof, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_spec(int64_t n, int ndof, double *out, const double *in, const double *coef,
+                              const int32_t *node_spec, const uint8_t *fixed, int accumulate, cudaStream_t s)
+{
+    scale_spec_kernel<<<1024, kThreads, 0, s>>>(n, ndof, out, in, coef, node_spec, fixed, accumulate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reaction_batch(const double *R, const int32_t *react_dof, const int64_t *off, int n_spec, double *out,
+                                  cudaStream_t s)
+{
+    reaction_batch_kernel<<<n_spec, 256, 0, s>>>(R, react_dof, off, out);
     return cudaGetLastError();
 }
 

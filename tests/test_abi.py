@@ -152,3 +152,27 @@ def test_notched_mesh_geometry():
     xs = np.unique(np.round(x, 12))
     dx = np.diff(xs)
     assert dx[np.argmin(np.abs(xs[:-1] - 1.0))] < 0.3 * dx.max()
+
+
+def test_batch_create_rejects_bad_specimens(B):
+    """gd_create_batch validates every specimen on the host before touching a
+    device, naming the specimen in the message."""
+    mat = I.Material()
+    good = [I.Problem(f"s{i}", I.uniaxial_bc_2d(I.structured_q4(3 + i, 2)), *I.icnn_pair(i, 4, 4), mat,
+                      np.linspace(0, 0.1, 3)[1:]) for i in range(3)]
+    hexp = I.Problem("h", I.biaxial_bc_3d(I.structured_hex8(2, 2, 2)), *I.icnn_pair(9, 4, 4), mat,
+                     np.linspace(0, 0.1, 3)[1:])
+    with pytest.raises(B.GDError) as ei:
+        B.gd_create_batch([good[0], hexp])
+    assert ei.value.status == 1 and "specimen 1" in B.gd_last_error()
+    bad = I.uniaxial_bc_2d(I.structured_q4(4, 2))
+    bad.conn = bad.conn.copy()
+    bad.conn[1, 2] = bad.n_nodes                    # one past this specimen's nodes
+    with pytest.raises(B.GDError) as ei:
+        B.gd_create_batch(good[:2] + [I.Problem("b", bad, *I.icnn_pair(5, 4, 4), mat, good[0].load)])
+    assert ei.value.status == 2 and "specimen 2" in B.gd_last_error()
+    flipped = I.uniaxial_bc_2d(I.structured_q4(3, 2))
+    flipped.conn = flipped.conn[:, ::-1].copy()
+    with pytest.raises(B.GDError) as ei:
+        B.gd_create_batch(good[:1] + [I.Problem("f", flipped, *I.icnn_pair(6, 4, 4), mat, good[0].load)])
+    assert ei.value.status == 2

@@ -1,0 +1,120 @@
+"""gd_backward: gradient of a reaction-curve loss through the whole quasi-static
+path with history, against central finite differences (CUDA forward path and
+the FP64 oracle's LU path), and invariance to the checkpoint interval.
+Bar: 1e-5 relative to finite differences."""
+import numpy as np
+import pytest
+
+from paper_2604_03411_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_03411_gb300 import build as build_mod
+    build_mod.build()
+    import oracle
+    import paper_2604_03411_gb300.binding as B
+    return torch, B, oracle
+
+
+def small_problem(n_long=16, n_wide=6, w=8, steps=6, energy=I.ENERGY_ICNN_RAW, seed=4):
+    mesh = I.uniaxial_bc_2d(I.notched_plate_q4(n_long, n_wide))
+    psi, yld = I.icnn_pair(seed, w, w)
+    # kappa_d = 0 and a path to 35% nominal strain: the damage, and with it the
+    # yield network's influence on the reaction, grows enough to be resolved by
+    # central differences
+    mat = I.Material(c_d=10.0 * 0.08 ** 2, energy=energy, kappa_d=0.0)
+    load = np.linspace(0.0, 0.7, steps + 1)[1:]
+    return I.Problem("adj", mesh, psi, yld, mat, load)
+
+
+def opts(B, k=2):
+    return B.gd_default_options(newton_rtol=1e-13, newton_atol=1e-15, krylov_rtol=1e-13, krylov_max=50000,
+                                checkpoint_every=k)
+
+
+def loss_and_grad_target(reac, target):
+    r = reac - target
+    return float(np.sum(r * r)), 2.0 * r
+
+
+def gpu_loss(B, prob, theta, target, k=2):
+    h = B.gd_create(prob, opts(B, k))
+    n_psi = prob.psi.params.size
+    B.gd_set_params(h, theta[:n_psi], theta[n_psi:])
+    reac, _ = B.gd_run_load_path(h)
+    return loss_and_grad_target(reac, target)[0], h, reac
+
+
+@pytest.mark.parametrize("energy", [I.ENERGY_ICNN_RAW, I.ENERGY_ICNN_ISO])
+def test_adjoint_vs_central_differences(env, energy):
+    torch, B, oracle = env
+    prob = small_problem(energy=energy)
+    theta0 = np.concatenate([prob.psi.params, prob.yld.params])
+    h = B.gd_create(prob, opts(B))
+    reac0, _ = B.gd_run_load_path(h)
+    target = 0.9 * reac0 + 0.001
+    L0, dL = loss_and_grad_target(reac0, target)
+    g = B.gd_backward(h, dL)
+    assert g.shape == theta0.shape and np.all(np.isfinite(g))
+    rng = np.random.default_rng(41)
+    n_psi = prob.psi.params.size
+    idx = np.concatenate([rng.choice(n_psi, 12, replace=False), n_psi + rng.choice(theta0.size - n_psi, 8, replace=False)])
+    fd = []
+    for i in idx:
+        step = 1e-4 * max(abs(theta0[i]), 1e-1)
+        tp = theta0.copy(); tp[i] += step
+        tm = theta0.copy(); tm[i] -= step
+        Lp = gpu_loss(B, prob, tp, target)[0]
+        Lm = gpu_loss(B, prob, tm, target)[0]
+        fd.append((Lp - Lm) / (2 * step))
+    fd = np.array(fd)
+    scale = np.abs(fd).max()
+    assert scale > 0
+    err = np.abs(g[idx] - fd) / np.maximum(np.abs(fd), 1e-3 * scale)
+    assert err.max() < 1e-5, (err.max(), g[idx], fd)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient(env):
+    torch, B, oracle = env
+    prob = small_problem(steps=7)
+    grads = []
+    for k in (1, 3, 100):
+        h = B.gd_create(prob, opts(B, k))
+        reac, _ = B.gd_run_load_path(h)
+        grads.append(B.gd_backward(h, np.linspace(1.0, 2.0, reac.size)))
+        # the handle is back at the end of the path
+        with pytest.raises(B.GDError):
+            B.gd_newton_step(h)
+    for g in grads[1:]:
+        assert np.abs(g - grads[0]).max() <= 1e-9 * np.abs(grads[0]).max()
+
+
+def test_adjoint_vs_oracle_finite_differences(env):
+    """The oracle's FP64 gradient: central differences of its LU-based path."""
+    torch, B, oracle = env
+    prob = small_problem(n_long=6, n_wide=3, w=8, steps=4)
+    theta0 = np.concatenate([prob.psi.params, prob.yld.params])
+    n_psi = prob.psi.params.size
+    h = B.gd_create(prob, opts(B))
+    reac0, _ = B.gd_run_load_path(h)
+    target = 0.95 * reac0
+    _, dL = loss_and_grad_target(reac0, target)
+    g = B.gd_backward(h, dL)
+
+    def oracle_loss(theta):
+        m = oracle.Model(2, prob.mat, theta[:n_psi], prob.psi.width, theta[n_psi:], prob.yld.width)
+        res = oracle.run_load_path(m, prob.mesh, prob.load, rtol=1e-13, atol=1e-15)
+        return loss_and_grad_target(res["reaction"], target)[0]
+
+    for i in (3, n_psi + 5, n_psi - 2):
+        step = 1e-4 * max(abs(theta0[i]), 1e-1)
+        tp = theta0.copy(); tp[i] += step
+        tm = theta0.copy(); tm[i] -= step
+        fd = (oracle_loss(tp) - oracle_loss(tm)) / (2 * step)
+        assert abs(g[i] - fd) <= 1e-5 * max(abs(fd), 1e-8), (i, g[i], fd)
