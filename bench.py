@@ -238,6 +238,11 @@ def run_gd(args):
     h_state = {"next": 0}
     for k in range(args.warmup):
         step(k)
+    # launch shapes from the library's own timings at the warmed-up state
+    tune = B.gd_autotune(h)
+    tuning = {"asm_warps": tune.asm_warps, "krylov_ctas_per_sm": tune.krylov_ctas_per_sm,
+              "asm_ms_by_warps": dict(zip(("2", "4", "8"), [round(x, 4) for x in tune.asm_ms])),
+              "krylov_us_by_ctas_per_sm": dict(zip(("1", "2", "3", "4"), [round(x, 3) for x in tune.krylov_us]))}
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -287,20 +292,37 @@ def run_gd(args):
     solves = max(newton, 1)
     kry_avg = kry_ms / solves
     iters_per_solve = krylov / solves
-    # algorithmic bytes of one BiCGStab iteration on the FP32 inner system: two SpMVs
-    # (values, the column list once per node block, row pointers, gathered x, y) and
-    # the vector phases (p, y, s, z, x, r updates: 15 vector reads/writes), 4-byte data
-    spmv_b = nnz * 4 + (nnz // ndof) * 4 + (n_nodes_all + 1) * 4 * 2 + n_dofs * (4 + 4 + 1)
-    iter_b = 2 * spmv_b + 15 * n_dofs * 4
+    # One BiCGStab iteration (three-barrier form): two SpMVs and the vector phases.
+    # Algorithmic bytes: per SpMV the values, the column list once per node block, the
+    # row pointers, the gathered x and the written y; the vector phases read/write 25
+    # vectors (p, v, y, q, s, t, x~, r, u, rh updates and reads).  Algorithmic FLOPs:
+    # 2 per stored value per SpMV, 2 per node-block inverse entry twice, and 2 per
+    # element of the 14 vector FMAs / dot products.
+    fp32_inner = sum(r.krylov_fp32_iterations for r in reps) * 2 > krylov
+    vb = 4 if fp32_inner else 8
+    spmv_b = nnz * vb + (nnz // ndof) * 4 + (n_nodes_all + 1) * 4 * 2 + n_dofs * (vb + vb + 1)
+    iter_b = 2 * spmv_b + 25 * n_dofs * vb
+    iter_f = 2 * (2 * nnz) + 2 * (2 * n_dofs * ndof) + 14 * 2 * n_dofs
     if kry_ms >= asm_ms:
         bytes_launch = iter_b * iters_per_solve
-        achieved = bytes_launch / (kry_avg / 1e3) / 1e9
-        roof = {"kernel": "bicgstab_kernel (persistent Krylov solve of one Newton system)", "bound": "hbm",
-                "achieved": achieved, "peak": peak_bw, "unit": "GB/s", "frac": achieved / peak_bw, "traffic": None,
-                "peak_source": f"{peak_kind} copy bandwidth", "avg_launch_ms": kry_avg,
-                "algorithmic_bytes_per_launch": bytes_launch, "iterations_per_launch": iters_per_solve,
-                "note": "the FP32 inner system (%.0f MB) stays L2-resident across the iterations of a launch"
-                        % (spmv_b / 1e6)}
+        flops_launch = iter_f * iters_per_solve
+        hbm_achieved = bytes_launch / (kry_avg / 1e3) / 1e9
+        alu_achieved = flops_launch / (kry_avg / 1e3) / 1e12
+        common = {"kernel": "bicgstab3_kernel (persistent Krylov solve of one Newton system)",
+                  "avg_launch_ms": kry_avg, "iterations_per_launch": iters_per_solve,
+                  "algorithmic_bytes_per_launch": bytes_launch, "algorithmic_flops_per_launch": flops_launch,
+                  "traffic_note": "the system (%.0f MB) stays L2-resident across the iterations of a launch, so "
+                                  "DRAM traffic is far below the algorithmic bytes" % (spmv_b / 1e6)}
+        if fp32_inner:
+            roof = dict(common, bound="hbm", achieved=hbm_achieved, peak=peak_bw, unit="GB/s",
+                        frac=hbm_achieved / peak_bw, traffic=None, peak_source=f"{peak_kind} copy bandwidth")
+        else:
+            # FP64 arithmetic issues at 1/64 of the FP32 rate on this part: the FP64 solve is
+            # bounded by the FP64 pipe and by its grid barriers, not by memory
+            roof = dict(common, bound="alu", achieved=alu_achieved, peak=FP64_PEAK_TFLOPS_NOMINAL, unit="TFLOP/s",
+                        frac=alu_achieved / FP64_PEAK_TFLOPS_NOMINAL, traffic=None,
+                        peak_source="nominal FP64 rate (1.25 TFLOP/s)",
+                        hbm_view={"achieved_gbs": hbm_achieved, "frac_of_measured_copy": hbm_achieved / peak_bw})
     else:
         # element kernel: FP64 (or FP32) ALU bound; algorithmic FLOPs (FMA = 2) of the dense parts
         nq = mesh0.nq
@@ -319,24 +341,31 @@ def run_gd(args):
                 "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "avg_launch_ms": asm_avg,
                 "algorithmic_flops_per_launch": flops / max(asm, 1)}
 
-    # --- end to end through the C ABI with host buffers ---
-    d_host, k_host = B.gd_get_fields(h)
-    nxt = h_state["next"] if h_state["next"] < n_path else 0
-    if nxt == 0:
-        d_host[:] = 0.0
-        k_host[:] = 0.0
+    # --- end to end through the C ABI with host buffers: each step uploads the
+    # committed state (dofs, the previous step's dofs for the predictor, kappa) from
+    # pinned host memory and reads the new state back ---
+    d_np, dp_np, k_np, nxt = B.gd_get_state(h)
+    if nxt >= n_path - args.steps:
+        nxt = 1
+        B.gd_set_state(h, np.zeros_like(d_np), np.zeros_like(k_np), 0)
+        B.gd_newton_step(h)
+        d_np, dp_np, k_np, nxt = B.gd_get_state(h)
+    d_host = torch.from_numpy(d_np).pin_memory().numpy()
+    dp_host = torch.from_numpy(dp_np).pin_memory().numpy()
+    k_host = torch.from_numpy(k_np).pin_memory().numpy()
     e2e_ms = 0.0
     e2e_units = 0
     for k in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        B.gd_set_state(h, d_host, k_host, nxt)           # host -> device
+        B.gd_set_state(h, d_host, k_host, nxt, dofs_prev=dp_host)    # host -> device
         r = B.gd_newton_step(h)
-        d_out, k_out = B.gd_get_fields(h)                # device -> host
+        d2, dp2, k2, nxt2 = B.gd_get_state(h)                         # device -> host
         e2e_ms += (time.perf_counter() - t0) * 1e3
         e2e_units += n_qp * (r.iterations + 1 + 2 * r.step_cuts)
-    h2d = d_host.nbytes + k_host.nbytes
+        d_host[:], dp_host[:], k_host[:], nxt = d2, dp2, k2, nxt2
+    h2d = d_host.nbytes + dp_host.nbytes + k_host.nbytes
     e2e = {"value": e2e_units / (e2e_ms / 1e3) * (world if world > 1 else 1), "unit": UNIT,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d)}
 
@@ -357,7 +386,7 @@ def run_gd(args):
         "krylov_share_of_step": kry_ms / total_ms,
         "krylov_ms_per_newton": kry_avg, "krylov_iterations_per_newton": iters_per_solve,
         "krylov_fp32_iterations": sum(r.krylov_fp32_iterations for r in reps),
-        "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "tuning": tuning,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(max(probs, key=lambda p: p.mesh.n_elems), args.cpu_seconds)

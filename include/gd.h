@@ -295,6 +295,25 @@ gd_status gd_solve_noalloc(int32_t ndof, int64_t n_nodes, const int32_t *rowptr,
                            const double *vals, const uint8_t *fixed, const double *b, double *x, double rtol,
                            int32_t max_it, void *stream, int32_t *iterations, double *rel_residual);
 
+/* Launch shapes chosen by gd_autotune and the times it measured. */
+typedef struct gd_tune_report {
+    int32_t asm_warps;           /* warps per CTA of the element kernel (2, 4 or 8)            */
+    int32_t krylov_ctas_per_sm;  /* CTAs per SM of the cooperative Krylov grid                 */
+    double asm_ms[3];            /* element-kernel pass (tangent) with 2, 4, 8 warps; -1: does
+                                    not fit in shared memory                                    */
+    double krylov_us[4];         /* Krylov iteration time with 1..4 CTAs per SM; -1: not
+                                    co-resident                                                 */
+} gd_tune_report;
+
+/* Times the element kernel (one tangent pass at the committed state) for each CTA
+ * width and the Krylov solve (a fixed 40-iteration run on that tangent, in the
+ * handle's inner-solve precision) for each grid size, and keeps the fastest
+ * shapes for the handle's later calls (the paper has no counterpart: a launch
+ * tuning step).  Results do not depend on the choice beyond summation order.
+ * rep may be NULL.  Uses the handle's work buffers; the committed state is
+ * unchanged.  Errors: GD_ERR_CUDA. */
+gd_status gd_autotune(gd_handle *h, gd_tune_report *rep);
+
 /* Advances the next load step of the path to convergence (monolithic Newton,
  * Sec. 3.2, with a line search and nested step halving on failure); commits
  * kappa and the fields on success.  rep may be NULL. */
@@ -312,11 +331,24 @@ gd_status gd_run_load_path(gd_handle *h, double *reaction, gd_path_report *rep);
 gd_status gd_backward(gd_handle *h, const double *dL_dreaction, double *dL_dtheta);
 
 /* Copies the committed fields to host: dofs [n_nodes*ndof], kappa [n_elems*nq]
- * (either may be NULL). */
-gd_status gd_get_fields(gd_handle *h, double *dofs, double *kappa);
+ * and the damage d = 1 - f_d(kappa) = 1 - exp(-eta_d <kappa - kappa_d>_+) at every
+ * quadrature point [n_elems*nq] (Eq. (degradation_function)); any may be NULL. */
+gd_status gd_get_fields(gd_handle *h, double *dofs, double *kappa, double *damage);
 
-/* Overwrites the committed state from host arrays and sets the next step index. */
-gd_status gd_set_state(gd_handle *h, const double *dofs, const double *kappa, int32_t next_step);
+/* Overwrites the committed state from host arrays and sets the next step index.
+ * dofs, kappa as in gd_get_fields (NULL keeps the handle's).  dofs_prev (may be
+ * NULL) is the converged state of step next_step - 1's predecessor, i.e. the
+ * state one step before `dofs`: with it the next step's initial guess
+ * extrapolates the last increment exactly as an uninterrupted run does; without
+ * it the next step starts from `dofs` itself. */
+gd_status gd_set_state(gd_handle *h, const double *dofs, const double *dofs_prev, const double *kappa,
+                       int32_t next_step);
+
+/* Copies the committed state to host: dofs, dofs_prev (the state one committed
+ * step earlier, the predictor's second point) [n_nodes*ndof], kappa
+ * [n_elems*nq]; any may be NULL.  next_step (may be NULL) receives the index of
+ * the next load step.  gd_set_state(dofs, dofs_prev, kappa, next_step) restores it. */
+gd_status gd_get_state(gd_handle *h, double *dofs, double *dofs_prev, double *kappa, int32_t *next_step);
 
 /* Message for the last non-OK status of this handle (or of gd_create when h is NULL). */
 const char *gd_last_error(const gd_handle *h);

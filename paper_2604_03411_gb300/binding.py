@@ -78,6 +78,11 @@ class GdPathReport(ctypes.Structure):
                 ("assembly_ms", ctypes.c_double), ("krylov_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
 
 
+class GdTuneReport(ctypes.Structure):
+    _fields_ = [("asm_warps", ctypes.c_int32), ("krylov_ctas_per_sm", ctypes.c_int32),
+                ("asm_ms", ctypes.c_double * 3), ("krylov_us", ctypes.c_double * 4)]
+
+
 _H = ctypes.c_void_p
 
 # name -> (restype, argtypes); mirrors include/gd.h
@@ -103,11 +108,13 @@ PROTOTYPES = {
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_double, ctypes.c_int32, ctypes.c_void_p,
                                         ctypes.POINTER(ctypes.c_int32), _dp]),
+    "gd_autotune": (ctypes.c_int, [_H, ctypes.POINTER(GdTuneReport)]),
     "gd_newton_step": (ctypes.c_int, [_H, ctypes.POINTER(GdNewtonReport)]),
     "gd_run_load_path": (ctypes.c_int, [_H, _dp, ctypes.POINTER(GdPathReport)]),
     "gd_backward": (ctypes.c_int, [_H, _dp, _dp]),
-    "gd_get_fields": (ctypes.c_int, [_H, _dp, _dp]),
-    "gd_set_state": (ctypes.c_int, [_H, _dp, _dp, ctypes.c_int32]),
+    "gd_get_fields": (ctypes.c_int, [_H, _dp, _dp, _dp]),
+    "gd_set_state": (ctypes.c_int, [_H, _dp, _dp, _dp, ctypes.c_int32]),
+    "gd_get_state": (ctypes.c_int, [_H, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_int32)]),
     "gd_last_error": (ctypes.c_char_p, [_H]),
     "gd_destroy": (None, [_H]),
 }
@@ -287,7 +294,9 @@ def gd_set_params(h: Handle, theta_psi=None, theta_yield=None):
         if a is None:
             return None
         if hasattr(a, "is_cuda"):
-            return _dptr(a)
+            if a.is_cuda:
+                return _dptr(a)
+            a = a.numpy()
         a = np.ascontiguousarray(a, np.float64)
         keep.append(a)
         return a.ctypes.data
@@ -336,6 +345,12 @@ def gd_solve_noalloc(ndof, n_nodes, rowptr, colidx, vals, fixed, b, x, rtol, max
     return it.value, rel.value
 
 
+def gd_autotune(h: Handle) -> GdTuneReport:
+    rep = GdTuneReport()
+    _check(lib().gd_autotune(h.ptr, ctypes.byref(rep)), h.ptr)
+    return rep
+
+
 def gd_newton_step(h: Handle) -> GdNewtonReport:
     rep = GdNewtonReport()
     _check(lib().gd_newton_step(h.ptr, ctypes.byref(rep)), h.ptr)
@@ -361,17 +376,34 @@ def gd_backward(h: Handle, dL_dreaction: np.ndarray) -> np.ndarray:
     return out
 
 
-def gd_get_fields(h: Handle):
+def gd_get_fields(h: Handle, damage: bool = False):
+    """(dofs, kappa [n_elems, nq]) of the committed state, plus the damage field
+    d = 1 - f_d(kappa) [n_elems, nq] when damage=True."""
     d = np.zeros(h.meta["n_nodes"] * h.meta["ndof"])
     k = np.zeros(h.meta["n_elems"] * h.meta["nq"])
-    _check(lib().gd_get_fields(h.ptr, _hp(d), _hp(k)), h.ptr)
-    return d, k.reshape(h.meta["n_elems"], h.meta["nq"])
+    dm = np.zeros_like(k) if damage else None
+    _check(lib().gd_get_fields(h.ptr, _hp(d), _hp(k), _hp(dm)), h.ptr)
+    shape = (h.meta["n_elems"], h.meta["nq"])
+    if damage:
+        return d, k.reshape(shape), dm.reshape(shape)
+    return d, k.reshape(shape)
 
 
-def gd_set_state(h: Handle, dofs=None, kappa=None, next_step: int = 0):
+def gd_set_state(h: Handle, dofs=None, kappa=None, next_step: int = 0, dofs_prev=None):
     d = np.ascontiguousarray(dofs, np.float64).ravel() if dofs is not None else None
+    dp = np.ascontiguousarray(dofs_prev, np.float64).ravel() if dofs_prev is not None else None
     k = np.ascontiguousarray(kappa, np.float64).ravel() if kappa is not None else None
-    _check(lib().gd_set_state(h.ptr, _hp(d), _hp(k), int(next_step)), h.ptr)
+    _check(lib().gd_set_state(h.ptr, _hp(d), _hp(dp), _hp(k), int(next_step)), h.ptr)
+
+
+def gd_get_state(h: Handle):
+    """(dofs, dofs_prev, kappa [n_elems, nq], next_step) of the committed state."""
+    d = np.zeros(h.meta["n_nodes"] * h.meta["ndof"])
+    dp = np.zeros_like(d)
+    k = np.zeros(h.meta["n_elems"] * h.meta["nq"])
+    ns = ctypes.c_int32()
+    _check(lib().gd_get_state(h.ptr, _hp(d), _hp(dp), _hp(k), ctypes.byref(ns)), h.ptr)
+    return d, dp, k.reshape(h.meta["n_elems"], h.meta["nq"]), ns.value
 
 
 def gd_last_error(h: Optional[Handle] = None) -> str:

@@ -24,8 +24,6 @@
 namespace gd {
 namespace {
 
-constexpr int kWarps = 1;
-
 #include "gd_device_fp64.cuh"
 
 // Reverse sweep of  F = alpha * (grad N(x) . d) + beta * N(x)  with respect to
@@ -35,8 +33,9 @@ constexpr int kWarps = 1;
 __device__ void net_reverse_unit(const double *P, const double *W2T, int n_in, int w, const double *x,
                                  const double *d, double alpha, double beta, double *acc, double *buf, int lane)
 {
-    const double *W1 = P, *b1 = W1 + w * n_in, *W2 = b1 + w, *A2 = W2 + w * w, *b2 = A2 + w * n_in, *w3 = b2 + w,
-                 *a3 = w3 + w;
+    // a3 enters F linearly (grad N . d = ... + a3 . d, N = ... + a3 . x): its gradient
+    // needs no parameter value
+    const double *W1 = P, *b1 = W1 + w * n_in, *W2 = b1 + w, *A2 = W2 + w * w, *b2 = A2 + w * n_in, *w3 = b2 + w;
     double *aW1 = acc, *ab1 = aW1 + w * n_in, *aW2 = ab1 + w, *aA2 = aW2 + w * (w + 1), *ab2 = aA2 + w * n_in,
            *aw3 = ab2 + w, *aa3 = aw3 + w;
     double *sZ = buf, *sZd = buf + w, *sH = buf + 2 * w, *sHd = buf + 3 * w;

@@ -111,6 +111,9 @@ void free_handle(gd::Handle &H)
     dfree(H.d_load);
     dfree(H.d_norm);
     dfree(H.d_coef);
+    dfree(H.bk_i32);
+    dfree(H.bk_f64);
+    dfree(H.bk_cnt);
     dfree(H.psi_tab);
     dfree(H.yld_tab);
     for (gd::DevNet &n : H.h_psi_tab) {
@@ -183,8 +186,9 @@ gd_status assemble_pass(gd::Handle &H, const double *dofs, const double *kappa_n
     GD_CUDA(&H, cudaMemsetAsync(H.counters, 0, sizeof(int) * 8, H.stream));
     GD_CUDA(&H, cudaEventRecord(H.ev0, H.stream));
     gd::AsmArgs a = asm_args(H, dofs, kappa_n, R, vals, kappa_out, loading, tangent);
-    if (H.opt.precision == GD_FP64 || force_fp64) GD_CUDA(&H, gd::launch_assemble_fp64(H.dim, a, H.num_sms, H.stream));
-    else GD_CUDA(&H, gd::launch_assemble_fp32(H.dim, a, H.num_sms, H.stream));
+    if (H.opt.precision == GD_FP64 || force_fp64)
+        GD_CUDA(&H, gd::launch_assemble_fp64(H.dim, a, H.num_sms, H.stream, H.asm_tune));
+    else GD_CUDA(&H, gd::launch_assemble_fp32(H.dim, a, H.num_sms, H.stream, H.asm_tune));
     ++H.launches;
     GD_CUDA(&H, cudaEventRecord(H.ev1, H.stream));
     ++H.assemblies;
@@ -334,6 +338,98 @@ gd_status solve_direction(gd::Handle &H, const double *rhs, double *delta, doubl
 }
 
 gd_status norms_batch(gd::Handle &H, const double *R, std::vector<double> &nf, std::vector<double> &nx);
+
+// Per-specimen BiCGStab on the batch system: specimen s stops at ||r_s|| <=
+// eta[s] ||b_s||.  iters = the largest count over the specimens.
+gd_status krylov_batch(gd::Handle &H, const std::vector<double> &eta, const double *b, double *x, int &iters,
+                       bool inner_fp32, double accept)
+{
+    gd::KrylovCtx kc;
+    kc.n_nodes = H.n_nodes;
+    kc.ndof = H.ndof;
+    kc.rowptr = H.rowptr;
+    kc.colidx = H.colidx;
+    kc.fixed = H.fixed;
+    kc.binv = H.binv;
+    for (int k = 0; k < 8; ++k) kc.work[k] = H.kv[k];
+    kc.work_x = H.kx;
+    kc.red = H.red;
+    kc.out = H.scal + 24;
+    kc.stream = H.stream;
+    kc.blocks = H.krylov_grid;
+    kc.num_sms = H.num_sms;
+    const int S = H.n_spec;
+    GD_CUDA(&H, cudaMemcpyAsync((void *)H.bk.rtol, eta.data(), sizeof(double) * S, cudaMemcpyHostToDevice, H.stream));
+    GD_CUDA(&H, cudaEventRecord(H.kv0, H.stream));
+    const void *vals = H.vals;
+    bool fp32_vals = H.opt.precision == GD_MIXED;
+    if (inner_fp32 && !fp32_vals) {
+        GD_CUDA(&H, gd::narrow_to_float((const double *)vals, H.vals_f32, H.nnz, H.stream));
+        ++H.launches;
+        vals = H.vals_f32;
+        fp32_vals = true;
+    }
+    GD_CUDA(&H, gd::krylov_solve_batch(kc, H.bk, vals, fp32_vals, b, x, H.opt.krylov_max, inner_fp32));
+    H.launches += 2;
+    GD_CUDA(&H, cudaEventRecord(H.kv1, H.stream));
+    H.bk_out.resize((size_t)3 * S);
+    GD_CUDA(&H, cudaMemcpyAsync(H.bk_out.data(), H.bk.out, sizeof(double) * 3 * S, cudaMemcpyDeviceToHost, H.stream));
+    GD_CUDA(&H, cudaStreamSynchronize(H.stream));
+    float kms = 0.0f;
+    cudaEventElapsedTime(&kms, H.kv0, H.kv1);
+    H.krylov_ms += kms;
+    iters = 0;
+    for (int s = 0; s < S; ++s) {
+        if (eta[s] < 0.0) continue;                   // skipped specimen
+        iters = std::max(iters, (int)H.bk_out[3 * s]);
+        const double rel = H.bk_out[3 * s + 1], status = H.bk_out[3 * s + 2];
+        if (status != 0.0 && !(status != 2.0 && std::isfinite(rel) && rel <= std::max(accept, eta[s])))
+            return fail(&H, GD_ERR_KRYLOV, "BiCGStab of specimen " + std::to_string(s) + " stopped (status " +
+                                               std::to_string((int)status) + ", relative residual " +
+                                               std::to_string(rel) + ")");
+    }
+    return GD_OK;
+}
+
+// Newton directions of a batch with per-specimen tolerances (policy as solve_direction):
+// in GD_MIXED the specimens whose tolerance allows it are solved in FP32 first, and
+// only the specimens that need it (tighter tolerance, or an FP32 solve that did not
+// reach a tenfold reduction) are then solved in FP64, the others kept as they are.
+gd_status solve_direction_batch(gd::Handle &H, const double *rhs, double *delta, const std::vector<double> &eta,
+                                gd_newton_report &rep)
+{
+    const int S = H.n_spec;
+    int kit = 0;
+    std::vector<double> todo = eta;
+    bool any64 = true;
+    if (H.opt.inner_solve == GD_INNER_AUTO && H.opt.precision == GD_MIXED) {
+        std::vector<double> e32(S, -1.0);
+        bool any32 = false;
+        for (int s = 0; s < S; ++s)
+            if (eta[s] >= 1e-5) {
+                e32[s] = eta[s];
+                any32 = true;
+            }
+        if (any32) {
+            // every specimen is solved or skipped; failures are collected, not returned
+            gd_status st = krylov_batch(H, e32, rhs, delta, kit, true, 1e300);
+            if (st) return st;
+            rep.krylov_iterations += kit;
+            rep.krylov_fp32_iterations += kit;
+            any64 = false;
+            for (int s = 0; s < S; ++s) {
+                const double rel = H.bk_out[3 * s + 1], status = H.bk_out[3 * s + 2];
+                const bool ok = e32[s] >= 0.0 && (status == 0.0 || (status != 2.0 && std::isfinite(rel) && rel <= 0.1));
+                todo[s] = ok ? -1.0 : eta[s];
+                any64 = any64 || !ok;
+            }
+        }
+    }
+    if (!any64) return GD_OK;
+    gd_status st = krylov_batch(H, todo, rhs, delta, kit, false, 0.1);
+    rep.krylov_iterations += kit;
+    return st;
+}
 
 // GD_MIXED: rounding noise of the FP32 residual at the current iterate, measured
 // as ||R_fp32 - R_fp64|| on the free dofs (one residual-only FP64 pass), per
@@ -520,19 +616,25 @@ gd_status newton_batch(gd::Handle &H, gd_newton_report &rep)
         if (it == H.opt.newton_max) break;
         // right-hand side -R on the unconverged specimens only
         double bn2 = 0.0, need = 1e300;
+        std::vector<double> eta_s(S, 1.0);
         for (int s = 0; s < S; ++s) {
             coef[s] = done[s] ? 0.0 : -1.0;
             if (done[s]) continue;
             bn2 += nf[s] * nf[s];
-            const double eta_s = std::min(1e-2, std::max(H.opt.krylov_rtol, 0.1 * ntol[s] / nf[s]));
-            need = std::min(need, eta_s * nf[s]);
+            eta_s[s] = std::min(1e-2, std::max(H.opt.krylov_rtol, 0.1 * ntol[s] / nf[s]));
+            need = std::min(need, eta_s[s] * nf[s]);
         }
         if ((st = set_coef(H, coef))) return st;
         GD_CUDA(&H, gd::launch_scale_spec(H.n_dofs, H.ndof, rhs, H.R, H.d_coef, H.node_spec, H.fixed, 0, H.stream));
         ++H.launches;
-        // ||r_s|| <= ||r|| <= eta ||b||: eta = min_s eta_s ||b_s|| / ||b|| meets every block's tolerance
-        const double eta = std::max(1e-14, need / std::sqrt(bn2));
-        if ((st = solve_direction(H, rhs, delta, eta, rep))) return st;
+        if (H.bk_ok && H.opt.inner_solve != GD_INNER_REFINED) {
+            // every specimen runs its own recurrences to its own tolerance
+            if ((st = solve_direction_batch(H, rhs, delta, eta_s, rep))) return st;
+        } else {
+            // one union solve: ||r_s|| <= ||r|| <= eta ||b|| with eta = min_s eta_s ||b_s|| / ||b||
+            const double eta = std::max(1e-14, need / std::sqrt(bn2));
+            if ((st = solve_direction(H, rhs, delta, eta, rep))) return st;
+        }
         // backtracking line search per specimen on its own ||R_free||
         bool near_floor = H.opt.precision == GD_MIXED;
         for (int s = 0; s < S; ++s) {
@@ -924,6 +1026,61 @@ static gd_status stage_net(gd::Handle &H, gd::DevNet &d, int n_in, int w, const 
     return GD_OK;
 }
 
+// Per-specimen Krylov layout of a batch for the current cooperative grid: block b
+// owns nodes [b chunk, (b+1) chunk); its first specimen and count, every
+// specimen's first and last block, and the partial and result buffers.  Batches
+// whose blocks would overlap more than kMaxSpecPerBlock specimens use the union
+// solve instead (bk_ok = false).
+gd_status build_batch_krylov(gd::Handle &H)
+{
+    dfree(H.bk_i32);
+    dfree(H.bk_f64);
+    dfree(H.bk_cnt);
+    H.bk_i32 = nullptr;
+    H.bk_f64 = nullptr;
+    H.bk_cnt = nullptr;
+    H.bk_ok = false;
+    const int nb = H.krylov_grid, S = H.n_spec;
+    const int64_t NN = H.n_nodes;
+    const int64_t chunk = (NN + nb - 1) / nb;
+    std::vector<int32_t> ns_of((size_t)NN);
+    for (int s = 0; s < S; ++s)
+        for (int64_t n = H.h_node_off[s]; n < H.h_node_off[s + 1]; ++n) ns_of[n] = s;
+    std::vector<int32_t> lay((size_t)2 * nb + 2 * S, 0);
+    int J = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int64_t n0 = (int64_t)b * chunk, n1 = std::min<int64_t>(n0 + chunk, NN);
+        if (n0 >= n1) continue;
+        lay[b] = ns_of[n0];
+        lay[nb + b] = ns_of[n1 - 1] - ns_of[n0] + 1;
+        J = std::max(J, (int)lay[nb + b]);
+    }
+    for (int s = 0; s < S; ++s) {
+        lay[2 * nb + s] = (int32_t)(H.h_node_off[s] / chunk);
+        lay[2 * nb + S + s] = (int32_t)((H.h_node_off[s + 1] - 1) / chunk);
+    }
+    if (J > gd::kMaxSpecPerBlock) return GD_OK;
+    GD_CUDA(&H, dalloc(&H.bk_i32, lay.size()));
+    GD_CUDA(&H, cudaMemcpy(H.bk_i32, lay.data(), sizeof(int32_t) * lay.size(), cudaMemcpyHostToDevice));
+    GD_CUDA(&H, dalloc(&H.bk_f64, (size_t)S + (size_t)5 * nb * J + (size_t)3 * S));
+    GD_CUDA(&H, dalloc(&H.bk_cnt, 2));
+    gd::BatchKrylov &L = H.bk;
+    L.node_spec = H.node_spec;
+    L.blk_fs = H.bk_i32;
+    L.blk_ns = H.bk_i32 + nb;
+    L.spec_b0 = H.bk_i32 + 2 * nb;
+    L.spec_b1 = H.bk_i32 + 2 * nb + S;
+    L.rtol = H.bk_f64;
+    L.red = H.bk_f64 + S;
+    L.out = H.bk_f64 + S + (size_t)5 * nb * J;
+    L.active_cnt = H.bk_cnt;
+    L.chunk = chunk;
+    L.J = J;
+    L.n_spec = S;
+    H.bk_ok = true;
+    return GD_OK;
+}
+
 // The meshes of a batch laid end to end: node, element, boundary and reaction
 // numbering shifted by the counts of the specimens before; per-specimen
 // reaction dofs carry each specimen's own react_comp.
@@ -1194,7 +1351,11 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
         H.err = "no cooperative grid fits on this device";
         return bail(GD_ERR_CUDA);
     }
-    H.red_blocks = 2 * H.num_sms;
+    if (n_spec > 1) {
+        gd_status sb = build_batch_krylov(H);
+        if (sb) return bail(sb);
+    }
+    H.red_blocks = 4 * H.num_sms;                    // room for Krylov grids up to 4 CTAs per SM
     GD_CREATE_CUDA(dalloc(&H.red, (size_t)8 * H.red_blocks));
     GD_CREATE_CUDA(dalloc(&H.scal, 64));
     GD_CREATE_CUDA(cudaMemsetAsync(H.dofs, 0, sizeof(double) * n_dofs, H.stream));
@@ -1323,6 +1484,87 @@ gd_status gd_solve(gd_handle *h, const void *csr_vals, const double *b, double *
     return st;
 }
 
+gd_status gd_autotune(gd_handle *h, gd_tune_report *rep)
+{
+    if (!h) return fail(nullptr, GD_ERR_ARG, "null handle");
+    gd::Handle &H = h->h;
+    gd_tune_report r{};
+    for (double &v : r.asm_ms) v = -1.0;
+    for (double &v : r.krylov_us) v = -1.0;
+    // element kernel: one tangent pass at the committed state per CTA width
+    const gd::AsmTune keep = H.asm_tune;
+    const int widths[3] = {2, 4, 8};
+    double best = 1e300;
+    gd::AsmTune pick = keep;
+    for (int wi = 0; wi < 3; ++wi) {
+        H.asm_tune.warps = widths[wi];
+        H.asm_tune.cta_per_sm = 0;
+        double tmin = 1e300;
+        bool ok = true;
+        for (int rep_i = 0; rep_i < 3 && ok; ++rep_i) {
+            if (assemble_pass(H, H.dofs, H.kappa, H.R_trial, H.vals_trial, H.kappa_trial2, H.loading2, 1)) {
+                ok = false;
+                break;
+            }
+            GD_CUDA(&H, cudaStreamSynchronize(H.stream));
+            if (rep_i > 0) tmin = std::min(tmin, elapsed_ms(H));   // the first pass warms up
+        }
+        cudaGetLastError();
+        if (!ok) continue;
+        r.asm_ms[wi] = tmin;
+        if (tmin < best) {
+            best = tmin;
+            pick = H.asm_tune;
+        }
+    }
+    H.asm_tune = pick;
+    r.asm_warps = pick.warps;
+    // Krylov: a fixed number of iterations on that tangent per grid size
+    std::swap(H.vals, H.vals_trial);                 // the tangent just assembled
+    const int keep_grid = H.krylov_grid, keep_max = H.opt.krylov_max;
+    const bool fp32 = H.opt.precision == GD_MIXED && H.opt.inner_solve == GD_INNER_AUTO;
+    const int iters = 40;
+    H.opt.krylov_max = iters;
+    double kbest = 1e300;
+    int kpick = H.krylov_cpsm;
+    gd_status st = GD_OK;
+    // right-hand side: ones on the free dofs (the committed residual may be zero)
+    GD_CUDA(&H, gd::launch_fill(H.kv[9], 1.0, H.n_dofs, H.stream));
+    ++H.launches;
+    for (int cap = 1; cap <= 4; ++cap) {
+        const int grid = gd::krylov_blocks(H.ndof, H.opt.precision == GD_MIXED, H.num_sms, cap);
+        if (grid != cap * H.num_sms) continue;       // not co-resident at this width
+        if ((size_t)grid > (size_t)4 * H.num_sms) continue;
+        H.krylov_grid = grid;
+        if (grid > H.red_blocks) continue;           // beyond the reduction buffers
+        double tmin = 1e300;
+        for (int rep_i = 0; rep_i < 2; ++rep_i) {
+            int kit = 0;
+            double rel = 0.0;
+            const double k0 = H.krylov_ms;
+            st = krylov(H, H.vals, H.kv[9], H.kv[8], kit, rel, 1e-300, fp32, 1e300);
+            if (st) break;
+            if (rep_i > 0 && kit > 0) tmin = std::min(tmin, (H.krylov_ms - k0) * 1e3 / kit);
+        }
+        if (st) break;
+        r.krylov_us[cap - 1] = tmin;
+        if (tmin < kbest) {
+            kbest = tmin;
+            kpick = cap;
+        }
+    }
+    std::swap(H.vals, H.vals_trial);
+    H.opt.krylov_max = keep_max;
+    H.krylov_cpsm = kpick;
+    H.krylov_grid = gd::krylov_blocks(H.ndof, H.opt.precision == GD_MIXED, H.num_sms, kpick);
+    if (H.krylov_grid < 1) H.krylov_grid = keep_grid;
+    r.krylov_ctas_per_sm = kpick;
+    if (st) return st;
+    if (H.n_spec > 1 && (st = build_batch_krylov(H))) return st;
+    if (rep) *rep = r;
+    return GD_OK;
+}
+
 gd_status gd_newton_step(gd_handle *h, gd_newton_report *rep)
 {
     if (!h) return fail(nullptr, GD_ERR_ARG, "null handle");
@@ -1388,31 +1630,56 @@ gd_status gd_run_load_path(gd_handle *h, double *reaction, gd_path_report *rep)
     return st;
 }
 
-gd_status gd_get_fields(gd_handle *h, double *dofs, double *kappa)
+gd_status gd_get_fields(gd_handle *h, double *dofs, double *kappa, double *damage)
 {
     if (!h) return fail(nullptr, GD_ERR_ARG, "null handle");
     gd::Handle &H = h->h;
+    const int64_t nq_tot = H.n_elems * H.nq;
     if (dofs) GD_CUDA(&H, cudaMemcpyAsync(dofs, H.dofs, sizeof(double) * H.n_dofs, cudaMemcpyDeviceToHost, H.stream));
     if (kappa)
-        GD_CUDA(&H, cudaMemcpyAsync(kappa, H.kappa, sizeof(double) * H.n_elems * H.nq, cudaMemcpyDeviceToHost, H.stream));
+        GD_CUDA(&H, cudaMemcpyAsync(kappa, H.kappa, sizeof(double) * nq_tot, cudaMemcpyDeviceToHost, H.stream));
+    if (damage && nq_tot > 0) {
+        // H.kappa_trial2 is scratch between Newton steps
+        GD_CUDA(&H, gd::launch_damage_field(H.kappa, nq_tot, H.mat.eta_d, H.mat.kappa_d, H.kappa_trial2, H.stream));
+        ++H.launches;
+        GD_CUDA(&H, cudaMemcpyAsync(damage, H.kappa_trial2, sizeof(double) * nq_tot, cudaMemcpyDeviceToHost, H.stream));
+    }
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));
     return GD_OK;
 }
 
-gd_status gd_set_state(gd_handle *h, const double *dofs, const double *kappa, int32_t next_step)
+gd_status gd_set_state(gd_handle *h, const double *dofs, const double *dofs_prev, const double *kappa,
+                       int32_t next_step)
 {
     if (!h) return fail(nullptr, GD_ERR_ARG, "null handle");
     gd::Handle &H = h->h;
     if (next_step < 0 || next_step > H.n_steps_max) return fail(&H, GD_ERR_ARG, "next_step out of range");
+    if (dofs_prev && next_step < 1) return fail(&H, GD_ERR_ARG, "dofs_prev needs next_step >= 1");
     if (dofs) GD_CUDA(&H, cudaMemcpyAsync(H.dofs, dofs, sizeof(double) * H.n_dofs, cudaMemcpyHostToDevice, H.stream));
+    if (dofs_prev)
+        GD_CUDA(&H, cudaMemcpyAsync(H.dofs_prev, dofs_prev, sizeof(double) * H.n_dofs, cudaMemcpyHostToDevice, H.stream));
     if (kappa)
         GD_CUDA(&H, cudaMemcpyAsync(H.kappa, kappa, sizeof(double) * H.n_elems * H.nq, cudaMemcpyHostToDevice, H.stream));
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));
     H.next_step = next_step;
     H.rec_on = false;
-    H.have_prev = false;
+    H.have_prev = dofs_prev != nullptr;
     H.load_prev = (double)next_step;
-    H.load_prevprev = H.load_prev;
+    H.load_prevprev = dofs_prev ? (double)(next_step - 1) : H.load_prev;
+    return GD_OK;
+}
+
+gd_status gd_get_state(gd_handle *h, double *dofs, double *dofs_prev, double *kappa, int32_t *next_step)
+{
+    if (!h) return fail(nullptr, GD_ERR_ARG, "null handle");
+    gd::Handle &H = h->h;
+    if (dofs) GD_CUDA(&H, cudaMemcpyAsync(dofs, H.dofs, sizeof(double) * H.n_dofs, cudaMemcpyDeviceToHost, H.stream));
+    if (dofs_prev)
+        GD_CUDA(&H, cudaMemcpyAsync(dofs_prev, H.dofs_prev, sizeof(double) * H.n_dofs, cudaMemcpyDeviceToHost, H.stream));
+    if (kappa)
+        GD_CUDA(&H, cudaMemcpyAsync(kappa, H.kappa, sizeof(double) * H.n_elems * H.nq, cudaMemcpyDeviceToHost, H.stream));
+    GD_CUDA(&H, cudaStreamSynchronize(H.stream));
+    if (next_step) *next_step = H.next_step;
     return GD_OK;
 }
 

@@ -25,12 +25,13 @@
 namespace gd {
 namespace {
 
-constexpr int kWarps = 4;                           // warps per CTA
 
 #include "gd_device_fp64.cuh"
 
-template <int DIM>
-__global__ void __launch_bounds__(32 * kWarps) asm_fp64_kernel(AsmArgs A)
+// KW warps per CTA (a tuning choice: warps are independent, so it only sets the
+// granularity of residency and of the persistent grid)
+template <int DIM, int KW>
+__global__ void __launch_bounds__(32 * KW) asm_fp64_kernel(AsmArgs A)
 {
     using G_ = Geo<DIM>;
     constexpr int NEN = G_::NEN, NQ = G_::NQ, NDOF = G_::NDOF, ND = G_::ND, EPW = G_::EPW, EPR = G_::EPR;
@@ -50,8 +51,8 @@ __global__ void __launch_bounds__(32 * kWarps) asm_fp64_kernel(AsmArgs A)
     const MatConst &m = A.mat;
 
     const int64_t n_batches = (A.n_elems + EPW - 1) / EPW;
-    for (int64_t batch = (int64_t)blockIdx.x * kWarps + warp; batch < n_batches;
-         batch += (int64_t)gridDim.x * kWarps) {
+    for (int64_t batch = (int64_t)blockIdx.x * KW + warp; batch < n_batches;
+         batch += (int64_t)gridDim.x * KW) {
         const int64_t e0 = batch * EPW;
         // ---- load element nodes (lane = (element, node)) ----
         for (int t = lane; t < EPW * NEN; t += 32) {
@@ -559,35 +560,51 @@ size_t smem_bytes(int wmax)
     using G_ = Geo<DIM>;
     size_t scratch = G_::EPW * G_::NEN * (DIM + G_::NDOF) + 32 * Q_REC + 32 * 4 + 32 * 10 + 5 * wmax +
                      2 * G_::NQ * G_::NEN * V_REC;
-    return scratch * sizeof(double) * kWarps;
+    return scratch * sizeof(double);          // per warp
 }
 
-template <int DIM>
-cudaError_t launch_dim(const AsmArgs &a, int num_sms, cudaStream_t s)
+template <int DIM, int KW>
+cudaError_t launch_kw(const AsmArgs &a, int num_sms, int cta_per_sm, cudaStream_t s)
 {
-    size_t sm = smem_bytes<DIM>(a.wmax);
-    cudaError_t err = cudaFuncSetAttribute(asm_fp64_kernel<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    size_t sm = smem_bytes<DIM>(a.wmax) * KW;
+    int dev = 0, optin = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e0 != cudaSuccess) return e0;
+    if (sm > (size_t)optin) return cudaErrorInvalidConfiguration;   // this CTA width does not fit
+    cudaError_t err = cudaFuncSetAttribute(asm_fp64_kernel<DIM, KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
     int per_sm = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, asm_fp64_kernel<DIM>, 32 * kWarps, sm);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, asm_fp64_kernel<DIM, KW>, 32 * KW, sm);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) per_sm = 1;
+    if (cta_per_sm > 0 && cta_per_sm < per_sm) per_sm = cta_per_sm;
     using G_ = Geo<DIM>;
     int64_t batches = (a.n_elems + G_::EPW - 1) / G_::EPW;
-    int64_t need = (batches + kWarps - 1) / kWarps;
+    int64_t need = (batches + KW - 1) / KW;
     int64_t grid = (int64_t)num_sms * per_sm;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    asm_fp64_kernel<DIM><<<(unsigned)grid, 32 * kWarps, sm, s>>>(a);
+    asm_fp64_kernel<DIM, KW><<<(unsigned)grid, 32 * KW, sm, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int DIM>
+cudaError_t launch_dim(const AsmArgs &a, int num_sms, const AsmTune &t, cudaStream_t s)
+{
+    switch (t.warps) {
+    case 2: return launch_kw<DIM, 2>(a, num_sms, t.cta_per_sm, s);
+    case 8: return launch_kw<DIM, 8>(a, num_sms, t.cta_per_sm, s);
+    default: return launch_kw<DIM, 4>(a, num_sms, t.cta_per_sm, s);
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_assemble_fp64(int dim, const AsmArgs &a, int num_sms, cudaStream_t s)
+cudaError_t launch_assemble_fp64(int dim, const AsmArgs &a, int num_sms, cudaStream_t s, const AsmTune &t)
 {
     if (a.n_elems <= 0) return cudaSuccess;
-    return dim == 2 ? launch_dim<2>(a, num_sms, s) : launch_dim<3>(a, num_sms, s);
+    return dim == 2 ? launch_dim<2>(a, num_sms, t, s) : launch_dim<3>(a, num_sms, t, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -93,6 +93,30 @@ struct Checkpoint {
     bool have_prev = false;
 };
 
+// launch shape of the element kernels (chosen by gd_autotune): warps per CTA
+// (2, 4 or 8) and a cap on resident CTAs per SM for the persistent grid (0: none)
+struct AsmTune {
+    int warps = 4;
+    int cta_per_sm = 0;
+};
+// Batched specimens: the Krylov grid's blocks take contiguous node chunks and
+// every specimen runs its own BiCGStab recurrences (own scalars, own stopping
+// test) inside one cooperative launch.
+constexpr int kMaxSpecPerBlock = 32;
+struct BatchKrylov {
+    const int32_t *node_spec = nullptr;   // [n_nodes] specimen of every node
+    const int32_t *blk_fs = nullptr;      // [blocks] first specimen overlapping block b
+    const int32_t *blk_ns = nullptr;      // [blocks] specimens overlapping block b (<= kMaxSpecPerBlock)
+    const int32_t *spec_b0 = nullptr;     // [n_spec] first block overlapping specimen s
+    const int32_t *spec_b1 = nullptr;     // [n_spec] last block overlapping specimen s
+    const double *rtol = nullptr;         // [n_spec] relative tolerance of every specimen
+    int *active_cnt = nullptr;            // [2] device counters (zeroed by the launcher)
+    double *red = nullptr;                // [5][blocks][J] block partials
+    double *out = nullptr;                // [n_spec][3] iterations, relative residual, status
+    int64_t chunk = 0;                    // nodes per block
+    int J = 0;                            // max specimens per block
+    int n_spec = 0;
+};
 struct Handle {
     // sizes
     int dim = 0, nen = 0, nq = 0, ndof = 0;
@@ -130,6 +154,13 @@ struct Handle {
     std::vector<int64_t> spec_nbc;                       // prescribed dofs per specimen
     double *d_load = nullptr, *d_factor = nullptr;       // [n_spec] device (batches only)
     double *d_norm = nullptr, *d_coef = nullptr;         // [2 n_spec], [n_spec] device (batches only)
+    // per-specimen Krylov layout (batches whose specimens are not too small for the grid)
+    bool bk_ok = false;
+    BatchKrylov bk;
+    int32_t *bk_i32 = nullptr;                           // device storage of the layout arrays
+    double *bk_f64 = nullptr;
+    int *bk_cnt = nullptr;
+    std::vector<double> bk_out;                          // host copy of the per-specimen results
     std::vector<double> last_reac;                       // per-specimen reactions of the last commit
     gd_options opt{};
     cudaStream_t stream = nullptr;
@@ -157,6 +188,9 @@ struct Handle {
     double *red = nullptr;                               // device reduction buffers
     double *scal = nullptr;                              // device scalars
     int red_blocks = 0;
+    // launch shapes (gd_autotune)
+    AsmTune asm_tune;
+    int krylov_cpsm = 2;
     // timing
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, kv0 = nullptr, kv1 = nullptr;
     double assembly_ms = 0.0, krylov_ms = 0.0;
@@ -184,8 +218,8 @@ gd_status set_error(gd_status st, const std::string &msg);
 // launchers (return the launch status)
 cudaError_t launch_prep_nets(const DevNet &psi, const DevNet &yld, int energy, NetConst *out, cudaStream_t s);
 cudaError_t launch_transpose(const DevNet &net, cudaStream_t s);
-cudaError_t launch_assemble_fp64(int dim, const AsmArgs &a, int num_sms, cudaStream_t s);
-cudaError_t launch_assemble_fp32(int dim, const AsmArgs &a, int num_sms, cudaStream_t s);
+cudaError_t launch_assemble_fp64(int dim, const AsmArgs &a, int num_sms, cudaStream_t s, const AsmTune &t = AsmTune());
+cudaError_t launch_assemble_fp32(int dim, const AsmArgs &a, int num_sms, cudaStream_t s, const AsmTune &t = AsmTune());
 cudaError_t launch_adjoint(int dim, const AdjArgs &a, int num_sms, cudaStream_t s);
 cudaError_t launch_adjoint_globals(const DevNet &psi, const DevNet &yld, int energy, const double *glob,
                                    double *theta_bar, cudaStream_t s);
@@ -232,6 +266,9 @@ cudaError_t launch_norms_batch(const double *R, const uint8_t *fixed, const int6
                                double *out, cudaStream_t s);
 cudaError_t launch_scale_spec(int64_t n, int ndof, double *out, const double *in, const double *coef,
                               const int32_t *node_spec, const uint8_t *fixed, int accumulate, cudaStream_t s);
+cudaError_t launch_fill(double *v, double val, int64_t n, cudaStream_t s);
+cudaError_t launch_damage_field(const double *kappa, int64_t n, double eta_d, double kappa_d, double *out,
+                                cudaStream_t s);
 cudaError_t launch_reaction_batch(const double *R, const int32_t *react_dof, const int64_t *off, int n_spec,
                                   double *out, cudaStream_t s);
 cudaError_t launch_adj_rhs(int64_t n, const double *sv, const double *y, double fbar, const uint8_t *fixed,
@@ -255,7 +292,10 @@ struct KrylovCtx {
     int blocks;                 // cooperative grid size (all blocks co-resident)
     int num_sms;
 };
-int krylov_blocks(int ndof, bool fp32_vals, int num_sms);
+cudaError_t krylov_solve_batch(const KrylovCtx &c, const BatchKrylov &L, const void *vals, bool fp32_vals,
+                               const double *b, double *x, int max_it, bool fp32_vectors);
+// cooperative grid of the Krylov kernels: SMs x co-resident CTAs per SM (at most cap)
+int krylov_blocks(int ndof, bool fp32_vals, int num_sms, int cap = 2);
 // Solves K x = b on the free dofs; the result and statistics land in x and c.out.
 // fp32_vectors: the iteration runs on FP32 values and vectors (dot products stay FP64).
 cudaError_t krylov_solve(const KrylovCtx &c, const void *vals, bool fp32_vals, const double *b, double *x,

@@ -95,131 +95,147 @@ __device__ __forceinline__ void totals(const double *red, const int (&slot)[K], 
     __syncthreads();
 }
 
-// out = B^-1 in (node blocks), zero on prescribed dofs
-template <int NDOF, class T>
-__device__ __forceinline__ void apply_binv(const T *binv, const uint8_t *fixed, int64_t nd, const T *in, T *out)
-{
-    T u[NDOF];
-#pragma unroll
-    for (int i = 0; i < NDOF; ++i) u[i] = in[nd * NDOF + i];
-    const T *Bi = binv + nd * NDOF * NDOF;
-#pragma unroll
-    for (int i = 0; i < NDOF; ++i) {
-        T s = T(0);
-#pragma unroll
-        for (int k = 0; k < NDOF; ++k) s += Bi[i * NDOF + k] * u[k];
-        out[nd * NDOF + i] = fixed[nd * NDOF + i] ? T(0) : s;
-    }
-}
 
-// y = A x on free rows (x is zero on prescribed dofs), y = 0 on prescribed rows;
-// group of G lanes per node; accumulates this thread's partials <d, y> and <y, y>.
-template <int NDOF, int G, class V, class T>
-__device__ __forceinline__ void spmv_phase(const KArgs<V, T> &A, const T *x, T *yv, const T *d, double &part,
-                                           double &part_yy)
+// ---------------------------------------------------------------------------
+// Single system, three grid barriers per iteration.
+//
+// Right-preconditioned BiCGStab on B = A M^-1 (M the node-block diagonal; the
+// solution is x = M^-1 x~).  The classic iteration multiplies B p and B s, whose
+// inputs are only known after a reduction, so it needs five barriers.  Here the
+// products kept are u = B r and q = B v: with v_n = B p_n and t_n = B s_n,
+//   t_n     = u_n - alpha q_n,
+//   v_{n+1} = u_{n+1} + beta (v_n - omega q_n),
+// so v and t follow elementwise, and every dot product is still taken directly
+// (no expanded inner products).  One iteration:
+//   1  p = r + beta (p - omega v), v = u + beta (v - omega q), y = M^-1 v, <rh, v>
+//   -- barrier: sigma = <rh, v>, alpha = rho / sigma
+//   2  q = A y, s = r - alpha v (stored in r), t = u - alpha q, <t, s>, <t, t>
+//   -- barrier: omega
+//   3  x~ += alpha p + omega s, r = s - omega t, y = M^-1 r, <rh, r>, <r, r>
+//   -- barrier: rho, ||r||, stop test, beta
+//   4  u = A y   (phase 1 of the next iteration reads only rows this lane wrote)
+// All phases give each row to the same lane (FP64: one lane per row; FP32: G lanes
+// per node, the row's lane holding the reduced value), so nothing but the two
+// products reads another lane's rows.  A zero <rh, r> or omega with the residual
+// still above tolerance restarts the recurrences with rh = r (at most 16 times).
+// ---------------------------------------------------------------------------
+template <int NDOF, int G, class T>
+struct RowMap {
+    static constexpr int LPN = std::is_same<T, double>::value ? NDOF : G;   // lanes per node
+    static constexpr int NPW = 32 / LPN;                                    // nodes per warp pass
+};
+
+// U independent row products per lane (U node groups of the warp at once): the
+// loads of the U rows are issued together, so a lane waits for one chain of
+// dependent loads (row pointer, column index, x) instead of U of them in turn.
+// The product phases are bound by that latency, not by bandwidth or arithmetic.
+template <int NDOF, int LPN, int U, class V, class T>
+__device__ __forceinline__ void row_products(const KArgs<V, T> &A, const int64_t (&nd)[U], const bool (&ok)[U],
+                                             int sub, const T *x, T (&out)[U])
 {
-    const int tid = blockIdx.x * kThreads + threadIdx.x;
-    const int sub = threadIdx.x & (G - 1);
-    const int64_t g0 = tid / G, ng = ((int64_t)gridDim.x * kThreads) / G;
-    part = 0.0;
-    part_yy = 0.0;
-    // every lane of a warp iterates the same number of times (uniform trip count)
-    const int64_t iters = (A.n_nodes + ng - 1) / ng;
-    for (int64_t it = 0; it < iters; ++it) {
-        const int64_t nd = g0 + it * ng;
-        const bool ok = nd < A.n_nodes;
-        T acc[NDOF];
+    int32_t base[U], len[U];
+    int lmax = 0;
 #pragma unroll
-        for (int i = 0; i < NDOF; ++i) acc[i] = T(0);
-        if (ok) {
-            const int64_t r0 = nd * NDOF;
-            const int32_t base = A.rowptr[r0];
-            const int32_t len = A.rowptr[r0 + 1] - base;
-            for (int j = sub; j < len; j += G) {
-                const T xv = x[A.colidx[base + j]];
+    for (int u = 0; u < U; ++u) {
+        base[u] = ok[u] ? A.rowptr[nd[u] * NDOF] : 0;
+        len[u] = ok[u] ? A.rowptr[nd[u] * NDOF + 1] - base[u] : 0;
+        lmax = len[u] > lmax ? len[u] : lmax;
+    }
+    if constexpr (LPN == NDOF) {
 #pragma unroll
-                for (int i = 0; i < NDOF; ++i) acc[i] += (T)A.vals[base + (int64_t)i * len + j] * xv;
-            }
+        for (int u = 0; u < U; ++u) out[u] = T(0);
+#pragma unroll 4
+        for (int j = 0; j < lmax; ++j) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (j < len[u])
+                    out[u] += (T)A.vals[base[u] + (int64_t)sub * len[u] + j] * x[A.colidx[base[u] + j]];
+        }
+    } else {
+        T acc[U][NDOF];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int i = 0; i < NDOF; ++i) acc[u][i] = T(0);
+#pragma unroll 4
+        for (int j = sub; j < lmax; j += LPN) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (j < len[u]) {
+                    const T xv = x[A.colidx[base[u] + j]];
+#pragma unroll
+                    for (int i = 0; i < NDOF; ++i) acc[u][i] += (T)A.vals[base[u] + (int64_t)i * len[u] + j] * xv;
+                }
         }
 #pragma unroll
-        for (int i = 0; i < NDOF; ++i)
+        for (int u = 0; u < U; ++u) {
 #pragma unroll
-            for (int o = G / 2; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
-        if (ok && sub < NDOF) {
+            for (int i = 0; i < NDOF; ++i)
+#pragma unroll
+                for (int o = LPN / 2; o > 0; o >>= 1) acc[u][i] += __shfl_xor_sync(0xffffffffu, acc[u][i], o);
             T v = T(0);
 #pragma unroll
             for (int i = 0; i < NDOF; ++i)
-                if (i == sub) v = acc[i];
-            const int64_t r = nd * NDOF + sub;
-            if (A.fixed[r]) v = T(0);
-            yv[r] = v;
-            part += (double)d[r] * (double)v;
-            part_yy += (double)v * (double)v;
+                if (i == sub) v = acc[u][i];
+            out[u] = v;
         }
     }
 }
 
-// The same product with one lane per row: a warp takes 32 / NDOF consecutive nodes
-// and each lane runs its own row, so no partial sums cross lanes.  On this part
-// FP64 arithmetic issues at a small fraction of the FP32 rate, and the cross-lane
-// reduction of the grouped form nearly doubles the FP64 instructions of the
-// product; the FP64 solve therefore uses this form.  The NDOF lanes of a node
-// read the same column index and x value (one broadcast per load).
-template <int NDOF, class V, class T>
-__device__ __forceinline__ void spmv_rows(const KArgs<V, T> &A, const T *x, T *yv, const T *d, double &part,
-                                          double &part_yy)
+// row sub of M^-1 w for the node whose NDOF row values sit in lanes base..base+NDOF-1
+template <int NDOF, class T>
+__device__ __forceinline__ T node_apply(const T *binv, int64_t nd, bool node_ok, int sub, int base, T w, bool fixed)
 {
-    constexpr int NPW = 32 / NDOF;
-    const int lane = threadIdx.x & 31;
-    const int slot = lane / NDOF, i = lane - slot * NDOF;
-    const int64_t wg = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * kThreads) >> 5;
-    part = 0.0;
-    part_yy = 0.0;
-    if (slot >= NPW) return;
-    for (int64_t nd = wg * NPW + slot; nd < A.n_nodes; nd += nw * NPW) {
-        const int64_t r = nd * NDOF + i;
-        const int32_t base = A.rowptr[nd * NDOF];
-        const int32_t len = A.rowptr[nd * NDOF + 1] - base;
-        const V *vr = A.vals + base + (int64_t)i * len;
-        const int32_t *cr = A.colidx + base;
-        T acc = T(0);
-#pragma unroll 4
-        for (int j = 0; j < len; ++j) acc += (T)vr[j] * x[cr[j]];
-        if (A.fixed[r]) acc = T(0);
-        yv[r] = acc;
-        part += (double)d[r] * (double)acc;
-        part_yy += (double)acc * (double)acc;
+    T out = T(0);
+#pragma unroll
+    for (int k = 0; k < NDOF; ++k) {
+        const T wk = __shfl_sync(0xffffffffu, w, base + k);
+        if (node_ok && sub < NDOF) out += binv[(nd * NDOF + sub) * NDOF + k] * wk;
     }
+    return fixed ? T(0) : out;
 }
 
 template <int NDOF, int G, class V, class T>
-__device__ __forceinline__ void spmv_any(const KArgs<V, T> &A, const T *x, T *yv, const T *d, double &part,
-                                         double &part_yy)
+__global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
 {
-    if constexpr (std::is_same<T, double>::value) spmv_rows<NDOF, V, T>(A, x, yv, d, part, part_yy);
-    else spmv_phase<NDOF, G, V, T>(A, x, yv, d, part, part_yy);
-}
-
-template <int NDOF, int G, class V, class T>
-__global__ void __launch_bounds__(kThreads) bicgstab_kernel(KArgs<V, T> A)
-{
+    using M = RowMap<NDOF, G, T>;
+    constexpr int LPN = M::LPN, NPW = M::NPW;
+    constexpr int UP = std::is_same<T, double>::value ? 2 : 4;   // node groups per product round
     cg::grid_group grid = cg::this_grid();
-    const int64_t tid = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    const int64_t nth = (int64_t)gridDim.x * kThreads;
-    enum { S_RHO = 0, S_RR = 1, S_RHV = 2, S_TS = 3, S_TT = 4 };
+    const int lane = threadIdx.x & 31;
+    const int slot = lane / LPN, sub = lane - slot * LPN, nbase = slot * LPN;
+    const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * kThreads) >> 5;
+    const int64_t n_nodes = A.n_nodes;
+    const int64_t passes = (n_nodes + nw * NPW - 1) / (nw * NPW);   // warp-uniform
+    // vector roles: r (also s), rh, p, v, q, t, y (= M^-1 v or M^-1 r), u
+    T *r = A.r, *rh = A.rh, *p = A.p, *v = A.v, *q = A.s, *t = A.t, *y = A.y, *u = A.z, *xt = A.x;
+    // partial-sum slots: consecutive phases use different slots, so that a block
+    // writing the next phase's partials never overwrites ones another block is
+    // still summing after the barrier
+    enum { S_RHO = 0, S_RR = 1, S_SIG = 2, S_TS = 3, S_TT = 4 };
 
-    // r = b (free), rh = r, x = p = v = 0
+    // init: r = b (free), rh = r, p = r, v = q = x~ = 0, y = M^-1 r; <r, r>
     {
         double rr = 0.0;
-        for (int64_t i = tid; i < A.n_nodes * NDOF; i += nth) {
-            const T bv = A.fixed[i] ? T(0) : (T)A.b[i];
-            A.r[i] = bv;
-            A.rh[i] = bv;
-            A.x[i] = T(0);
-            A.p[i] = T(0);
-            A.v[i] = T(0);
-            rr += (double)bv * (double)bv;
+        for (int64_t ps = 0; ps < passes; ++ps) {
+            const int64_t nd = (gw + ps * nw) * NPW + slot;
+            const bool node_ok = slot < NPW && nd < n_nodes;
+            const bool own = node_ok && sub < NDOF;
+            const int64_t row = nd * NDOF + sub;
+            const bool fx = own ? A.fixed[row] != 0 : true;
+            const T bv = (own && !fx) ? (T)A.b[row] : T(0);
+            const T yv = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, bv, fx);
+            if (own) {
+                r[row] = bv;
+                rh[row] = bv;
+                p[row] = bv;
+                v[row] = T(0);
+                q[row] = T(0);
+                xt[row] = T(0);
+                y[row] = yv;
+                rr += (double)bv * (double)bv;
+            }
         }
         double pv[2] = {rr, rr};
         const int sl[2] = {S_RHO, S_RR};
@@ -232,73 +248,124 @@ __global__ void __launch_bounds__(kThreads) bicgstab_kernel(KArgs<V, T> A)
         totals<2>(A.red, sl, tot);
     }
     const double bnorm = sqrt(tot[1]);
-    double rho = tot[0], rho_old = 1.0, alpha = 1.0, omega = 1.0;
-    double rel = 0.0;
-    int it = 0, status = 0;
-    if (bnorm == 0.0) {
-        rel = 0.0;
+    double rho = tot[0], alpha = 0.0, omega = 1.0, beta = 0.0, rel = 0.0;
+    int it = 0, status = 0, restarts = 0;
+    if (!(bnorm > 0.0)) {
+        if (!(bnorm == 0.0)) status = 2;
     } else {
-        for (it = 0; it < A.max_it; ++it) {
-            // phase A: p = r + beta (p - omega v), y = B^-1 p
-            const double beta = (it == 0 || rho_old == 0.0 || omega == 0.0) ? 0.0 : (rho / rho_old) * (alpha / omega);
-            for (int64_t nd = tid; nd < A.n_nodes; nd += nth) {
+        // u = A y
+        for (int64_t ps0 = 0; ps0 < passes; ps0 += UP) {
+            int64_t ndu[UP];
+            bool oku[UP];
+            T au[UP];
 #pragma unroll
-                for (int i = 0; i < NDOF; ++i) {
-                    const int64_t k = nd * NDOF + i;
-                    A.p[k] = A.r[k] + (T)beta * (A.p[k] - (T)omega * A.v[k]);
-                }
-                apply_binv<NDOF, T>(A.binv, A.fixed, nd, A.p, A.y);
+            for (int k = 0; k < UP; ++k) {
+                ndu[k] = (gw + (ps0 + k) * nw) * NPW + slot;
+                oku[k] = ps0 + k < passes && slot < NPW && ndu[k] < n_nodes;
             }
-            grid.sync();
-            // phase B: v = A y, <rh, v>
+            row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, y, au);
+#pragma unroll
+            for (int k = 0; k < UP; ++k)
+                if (oku[k] && sub < NDOF) {
+                    const int64_t row = ndu[k] * NDOF + sub;
+                    u[row] = A.fixed[row] ? T(0) : au[k];
+                }
+        }
+        for (it = 0; it < A.max_it; ++it) {
+            // phase 1
             {
-                double prhv, pvv;
-                spmv_any<NDOF, G, V, T>(A, A.y, A.v, A.rh, prhv, pvv);
-                double pv[1] = {prhv};
-                const int sl[1] = {S_RHV};
+                double s1 = 0.0;
+                const T tb = (T)beta, tbo = (T)(beta * omega);
+                for (int64_t ps = 0; ps < passes; ++ps) {
+                    const int64_t nd = (gw + ps * nw) * NPW + slot;
+                    const bool node_ok = slot < NPW && nd < n_nodes;
+                    const bool own = node_ok && sub < NDOF;
+                    const int64_t row = nd * NDOF + sub;
+                    T vn = T(0);
+                    bool fx = true;
+                    if (own) {
+                        fx = A.fixed[row] != 0;
+                        const T vo = v[row];
+                        p[row] = r[row] + tb * p[row] - tbo * vo;
+                        vn = u[row] + tb * vo - tbo * q[row];
+                        v[row] = vn;
+                        s1 += (double)rh[row] * (double)vn;
+                    }
+                    const T yv = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, vn, fx);
+                    if (own) y[row] = yv;
+                }
+                double pv[1] = {s1};
+                const int sl[1] = {S_SIG};
                 partials<1>(pv, A.red, sl);
             }
             grid.sync();
-            double t1[1];
             {
-                const int sl[1] = {S_RHV};
+                double t1[1];
+                const int sl[1] = {S_SIG};
                 totals<1>(A.red, sl, t1);
+                alpha = t1[0] != 0.0 ? rho / t1[0] : 0.0;
             }
-            alpha = t1[0] != 0.0 ? rho / t1[0] : 0.0;
-            // phase C: s = r - alpha v, z = B^-1 s
-            for (int64_t nd = tid; nd < A.n_nodes; nd += nth) {
-#pragma unroll
-                for (int i = 0; i < NDOF; ++i) {
-                    const int64_t k = nd * NDOF + i;
-                    A.s[k] = A.r[k] - (T)alpha * A.v[k];
-                }
-                apply_binv<NDOF, T>(A.binv, A.fixed, nd, A.s, A.z);
-            }
-            grid.sync();
-            // phase D: t = A z, <t, s>, <t, t>
+            // phase 2
             {
-                double ts, tt;
-                spmv_any<NDOF, G, V, T>(A, A.z, A.t, A.s, ts, tt);
+                double ts = 0.0, tt = 0.0;
+                const T ta = (T)alpha;
+                for (int64_t ps0 = 0; ps0 < passes; ps0 += UP) {
+                    int64_t ndu[UP];
+                    bool oku[UP];
+                    T au[UP];
+#pragma unroll
+                    for (int k = 0; k < UP; ++k) {
+                        ndu[k] = (gw + (ps0 + k) * nw) * NPW + slot;
+                        oku[k] = ps0 + k < passes && slot < NPW && ndu[k] < n_nodes;
+                    }
+                    row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, y, au);
+#pragma unroll
+                    for (int k = 0; k < UP; ++k)
+                        if (oku[k] && sub < NDOF) {
+                            const int64_t row = ndu[k] * NDOF + sub;
+                            const T qn = A.fixed[row] ? T(0) : au[k];
+                            q[row] = qn;
+                            const T sv = r[row] - ta * v[row];
+                            const T tv = u[row] - ta * qn;
+                            r[row] = sv;
+                            t[row] = tv;
+                            ts += (double)tv * (double)sv;
+                            tt += (double)tv * (double)tv;
+                        }
+                }
                 double pv[2] = {ts, tt};
                 const int sl[2] = {S_TS, S_TT};
                 partials<2>(pv, A.red, sl);
             }
             grid.sync();
-            double t2[2];
             {
+                double t2[2];
                 const int sl[2] = {S_TS, S_TT};
                 totals<2>(A.red, sl, t2);
+                omega = t2[1] != 0.0 ? t2[0] / t2[1] : 0.0;
             }
-            omega = t2[1] != 0.0 ? t2[0] / t2[1] : 0.0;
-            // phase E: x += alpha y + omega z, r = s - omega t, <rh, r>, <r, r>
+            // phase 3
             {
-                double prhr = 0.0, prr = 0.0;
-                for (int64_t i = tid; i < A.n_nodes * NDOF; i += nth) {
-                    A.x[i] += (T)alpha * A.y[i] + (T)omega * A.z[i];
-                    const T rv = A.s[i] - (T)omega * A.t[i];
-                    A.r[i] = rv;
-                    prhr += (double)A.rh[i] * (double)rv;
-                    prr += (double)rv * (double)rv;
+                double prr = 0.0, prhr = 0.0;
+                const T ta = (T)alpha, to = (T)omega;
+                for (int64_t ps = 0; ps < passes; ++ps) {
+                    const int64_t nd = (gw + ps * nw) * NPW + slot;
+                    const bool node_ok = slot < NPW && nd < n_nodes;
+                    const bool own = node_ok && sub < NDOF;
+                    const int64_t row = nd * NDOF + sub;
+                    T rn = T(0);
+                    bool fx = true;
+                    if (own) {
+                        fx = A.fixed[row] != 0;
+                        const T sv = r[row];
+                        xt[row] += ta * p[row] + to * sv;
+                        rn = sv - to * t[row];
+                        r[row] = rn;
+                        prhr += (double)rh[row] * (double)rn;
+                        prr += (double)rn * (double)rn;
+                    }
+                    const T yv = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, rn, fx);
+                    if (own) y[row] = yv;
                 }
                 double pv[2] = {prhr, prr};
                 const int sl[2] = {S_RHO, S_RR};
@@ -310,10 +377,8 @@ __global__ void __launch_bounds__(kThreads) bicgstab_kernel(KArgs<V, T> A)
                 const int sl[2] = {S_RHO, S_RR};
                 totals<2>(A.red, sl, t3);
             }
-            rho_old = rho;
-            rho = t3[0];
             rel = sqrt(t3[1]) / bnorm;
-            if (!(rel == rel)) {            // NaN
+            if (!(rel == rel)) {
                 status = 2;
                 ++it;
                 break;
@@ -322,20 +387,486 @@ __global__ void __launch_bounds__(kThreads) bicgstab_kernel(KArgs<V, T> A)
                 ++it;
                 break;
             }
-            if (rho == 0.0 || omega == 0.0) {   // breakdown with a non-zero residual
-                status = 1;
-                ++it;
-                break;
+            bool restart = false;
+            if (t3[0] == 0.0 || omega == 0.0 || rho == 0.0) {
+                if (restarts >= 16) {
+                    status = 1;
+                    ++it;
+                    break;
+                }
+                ++restarts;
+                restart = true;
+                beta = 0.0;
+                rho = t3[1];
+            } else {
+                beta = (t3[0] / rho) * (alpha / omega);
+                rho = t3[0];
+            }
+            // phase 4: u = A y (and rh = r on a restart)
+            for (int64_t ps0 = 0; ps0 < passes; ps0 += UP) {
+                int64_t ndu[UP];
+                bool oku[UP];
+                T au[UP];
+#pragma unroll
+                for (int k = 0; k < UP; ++k) {
+                    ndu[k] = (gw + (ps0 + k) * nw) * NPW + slot;
+                    oku[k] = ps0 + k < passes && slot < NPW && ndu[k] < n_nodes;
+                }
+                row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, y, au);
+#pragma unroll
+                for (int k = 0; k < UP; ++k)
+                    if (oku[k] && sub < NDOF) {
+                        const int64_t row = ndu[k] * NDOF + sub;
+                        u[row] = A.fixed[row] ? T(0) : au[k];
+                        if (restart) rh[row] = r[row];
+                    }
             }
         }
-        if (it >= A.max_it && rel > A.rtol) status = 3;
+        if (it >= A.max_it && rel > A.rtol && status == 0) status = 3;
     }
-    if ((void *)A.x != (void *)A.x_out)
-        for (int64_t i = tid; i < A.n_nodes * NDOF; i += nth) A.x_out[i] = (double)A.x[i];
+    // x = M^-1 x~ (in place when x~ is the FP64 output)
+    for (int64_t ps = 0; ps < passes; ++ps) {
+        const int64_t nd = (gw + ps * nw) * NPW + slot;
+        const bool node_ok = slot < NPW && nd < n_nodes;
+        const bool own = node_ok && sub < NDOF;
+        const int64_t row = nd * NDOF + sub;
+        const bool fx = own ? A.fixed[row] != 0 : true;
+        const T xv = own ? xt[row] : T(0);
+        const T xo = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, xv, fx);
+        if (own) A.x_out[row] = (double)xo;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         A.out[0] = it;
         A.out[1] = rel;
         A.out[2] = status;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Batched specimens: independent BiCGStab recurrences per specimen in one
+// cooperative launch.  Block b owns the contiguous nodes [b chunk, (b+1) chunk)
+// and so at most a few specimens (the union mesh lays them end to end); each
+// specimen has its own alpha, omega, rho, stopping test and breakdown status, so
+// a specimen stops when its own residual meets its own tolerance and its nodes
+// are skipped from then on.  Dot products are reduced per specimen: a warp keeps
+// a running sum while its 32 consecutive nodes belong to one specimen and adds
+// it to a per-warp shared-memory row when the specimen changes; the block writes
+// one partial per (slot, specimen), and every block that owns a specimen sums
+// that specimen's partials over the blocks it spans in the same order, so all
+// owners take the same decisions.  The loop ends when no specimen is active:
+// the first owner block of every active specimen counts it into a device
+// counter that all blocks read after the next grid barrier.
+// ---------------------------------------------------------------------------
+constexpr int kWarpsPB = kThreads / 32;
+constexpr int kBSlots = 2;                 // partial sums per phase
+enum { BS_RHO = 0, BS_RR = 1, BS_RHV = 2, BS_TS = 3, BS_TT = 4 };
+
+struct BShared {
+    double acc[kWarpsPB][kBSlots][kMaxSpecPerBlock];
+    double rho[kMaxSpecPerBlock], rho_old[kMaxSpecPerBlock], alpha[kMaxSpecPerBlock], omega[kMaxSpecPerBlock];
+    double bn[kMaxSpecPerBlock], rel[kMaxSpecPerBlock], tot[kBSlots][kMaxSpecPerBlock];
+    int act[kMaxSpecPerBlock], its[kMaxSpecPerBlock], st[kMaxSpecPerBlock], rst[kMaxSpecPerBlock],
+        keep[kMaxSpecPerBlock];
+    int cnt;
+};
+
+// running per-specimen sums of one warp (j = block-local specimen, -1 = none)
+struct WarpAcc {
+    double v[kBSlots];
+    int j;
+};
+
+__device__ __forceinline__ void wacc_flush(WarpAcc &a, BShared &S, int w, int lane)
+{
+    if (a.j >= 0) {
+#pragma unroll
+        for (int k = 0; k < kBSlots; ++k) {
+            const double s = warp_sum(a.v[k]);
+            if (lane == 0) S.acc[w][k][a.j] += s;
+        }
+    }
+    a.j = -1;
+#pragma unroll
+    for (int k = 0; k < kBSlots; ++k) a.v[k] = 0.0;
+}
+
+// every lane of the warp calls this once per group (valid = the lane holds a value)
+__device__ __forceinline__ void wacc_add(WarpAcc &a, BShared &S, int w, int lane, bool valid, int j,
+                                         const double (&val)[kBSlots])
+{
+    const unsigned vm = __ballot_sync(0xffffffffu, valid);
+    if (vm == 0u) return;
+    const int j0 = __shfl_sync(0xffffffffu, j, __ffs(vm) - 1);
+    const bool uniform = __all_sync(0xffffffffu, !valid || j == j0);
+    if (uniform && j0 == a.j) {
+        if (valid)
+#pragma unroll
+            for (int k = 0; k < kBSlots; ++k) a.v[k] += val[k];
+        return;
+    }
+    wacc_flush(a, S, w, lane);
+    if (uniform) {
+        a.j = j0;
+        if (valid)
+#pragma unroll
+            for (int k = 0; k < kBSlots; ++k) a.v[k] = val[k];
+        return;
+    }
+    // the group straddles specimens: reduce each one separately
+    int jmin = valid ? j : 1 << 30, jmax = valid ? j : -1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        jmin = min(jmin, __shfl_xor_sync(0xffffffffu, jmin, o));
+        jmax = max(jmax, __shfl_xor_sync(0xffffffffu, jmax, o));
+    }
+    for (int jj = jmin; jj <= jmax; ++jj) {
+#pragma unroll
+        for (int k = 0; k < kBSlots; ++k) {
+            const double s = warp_sum((valid && j == jj) ? val[k] : 0.0);
+            if (lane == 0) S.acc[w][k][jj] += s;
+        }
+    }
+}
+
+// block partials of the phase -> red[(slot * nb + b) * J + j]; clears the rows
+__device__ __forceinline__ void bpartials(BShared &S, const gd::BatchKrylov &L, int ns, int slot0, int slot1)
+{
+    __syncthreads();
+    const int nb = gridDim.x;
+    for (int t = threadIdx.x; t < kBSlots * ns; t += blockDim.x) {
+        const int k = t / ns, j = t - k * ns;
+        double s = 0.0;
+        for (int w = 0; w < kWarpsPB; ++w) s += S.acc[w][k][j];
+        const int slot = k == 0 ? slot0 : slot1;
+        if (slot >= 0) L.red[((size_t)slot * nb + blockIdx.x) * L.J + j] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kWarpsPB * kBSlots * kMaxSpecPerBlock; t += blockDim.x)
+        (&S.acc[0][0][0])[t] = 0.0;
+    __syncthreads();
+}
+
+// totals of the block's specimens (after a grid barrier) -> S.tot[k][j]
+__device__ __forceinline__ void btotals(BShared &S, const gd::BatchKrylov &L, int fs, int ns, int slot0, int slot1)
+{
+    const int nb = gridDim.x;
+    for (int t = threadIdx.x; t < kBSlots * ns; t += blockDim.x) {
+        const int k = t / ns, j = t - k * ns;
+        const int slot = k == 0 ? slot0 : slot1;
+        double s = 0.0;
+        if (slot >= 0) {
+            const int sp = fs + j;
+            for (int bb = L.spec_b0[sp]; bb <= L.spec_b1[sp]; ++bb)
+                s += L.red[((size_t)slot * nb + bb) * L.J + (sp - L.blk_fs[bb])];
+        }
+        S.tot[k][j] = s;
+    }
+    __syncthreads();
+}
+
+// The batch kernel: the three-barrier iteration of bicgstab3_kernel with every
+// scalar per specimen.  Block b owns nodes [n0, n1) = [b chunk, (b+1) chunk); its
+// warps take node groups of that range in the row mapping of RowMap.
+template <int NDOF, int G, class V, class T>
+__global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A, gd::BatchKrylov L)
+{
+    using M = RowMap<NDOF, G, T>;
+    constexpr int LPN = M::LPN, NPW = M::NPW;
+    constexpr int UP = std::is_same<T, double>::value ? 2 : 4;   // node groups per product round
+    cg::grid_group grid = cg::this_grid();
+    __shared__ BShared S;
+    const int b = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int slot = lane / LPN, sub = lane - slot * LPN, nbase = slot * LPN;
+    const int64_t n0 = (int64_t)b * L.chunk;
+    const int64_t n1 = n0 + L.chunk < A.n_nodes ? n0 + L.chunk : A.n_nodes;
+    const int fs = n0 < n1 ? L.blk_fs[b] : 0;
+    const int ns = n0 < n1 ? L.blk_ns[b] : 0;
+    const int64_t passes = (L.chunk + (int64_t)kWarpsPB * NPW - 1) / ((int64_t)kWarpsPB * NPW);   // grid-uniform
+    T *r = A.r, *rh = A.rh, *p = A.p, *v = A.v, *q = A.s, *t = A.t, *y = A.y, *u = A.z, *xt = A.x;
+    for (int i = threadIdx.x; i < kWarpsPB * kBSlots * kMaxSpecPerBlock; i += blockDim.x) (&S.acc[0][0][0])[i] = 0.0;
+    for (int j = threadIdx.x; j < kMaxSpecPerBlock; j += blockDim.x) {
+        S.act[j] = 1;
+        S.its[j] = 0;
+        S.st[j] = 0;
+        S.rel[j] = 0.0;
+        S.alpha[j] = 0.0;
+        S.omega[j] = 1.0;
+        S.rho_old[j] = 0.0;     // holds beta between phase 3 and the next phase 1
+        S.rst[j] = 0;
+        S.keep[j] = 0;
+    }
+    __syncthreads();
+    // node of this lane in pass ps, its block-local specimen (-1: none) and row ownership
+    auto node_of = [&](int64_t ps, int64_t &nd, bool &node_ok, int &j) {
+        nd = n0 + (w + ps * kWarpsPB) * NPW + slot;
+        node_ok = slot < NPW && nd < n1;
+        j = node_ok ? L.node_spec[nd] - fs : -1;
+    };
+    // init: r = b (free), rh = p = r, v = q = x~ = 0, y = M^-1 r; per-specimen ||b||^2
+    {
+        WarpAcc acc;
+        acc.j = -1;
+        acc.v[0] = acc.v[1] = 0.0;
+        for (int64_t ps = 0; ps < passes; ++ps) {
+            int64_t nd;
+            bool node_ok;
+            int j;
+            node_of(ps, nd, node_ok, j);
+            const bool own = node_ok && sub < NDOF;
+            const int64_t row = nd * NDOF + sub;
+            const bool fx = own ? A.fixed[row] != 0 : true;
+            const T bv = (own && !fx) ? (T)A.b[row] : T(0);
+            const T yv = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, bv, fx);
+            double val[kBSlots] = {0.0, 0.0};
+            if (own) {
+                r[row] = bv;
+                rh[row] = bv;
+                p[row] = bv;
+                v[row] = T(0);
+                q[row] = T(0);
+                // x~ may be the output itself (FP64): a skipped specimen keeps its x
+                if (L.rtol[fs + j] >= 0.0) xt[row] = T(0);
+                y[row] = yv;
+                val[0] = val[1] = (double)bv * (double)bv;
+            }
+            wacc_add(acc, S, w, lane, own, j, val);
+        }
+        wacc_flush(acc, S, w, lane);
+        bpartials(S, L, ns, BS_RHO, BS_RR);
+    }
+    grid.sync();
+    btotals(S, L, fs, ns, BS_RHO, BS_RR);
+    for (int j = threadIdx.x; j < ns; j += blockDim.x) {
+        const int sp = fs + j;
+        S.bn[j] = sqrt(S.tot[1][j]);
+        S.rho[j] = S.tot[0][j];
+        S.act[j] = S.bn[j] > 0.0 ? 1 : 0;             // a zero right-hand side is solved by x = 0
+        if (!(S.bn[j] == S.bn[j])) S.st[j] = 2;
+        S.keep[j] = L.rtol[sp] < 0.0 ? 1 : 0;         // skipped: x of this specimen is left as it is
+        if (S.keep[j]) S.act[j] = 0;
+        if (S.act[j] && b == L.spec_b0[sp]) atomicAdd(&L.active_cnt[0], 1);
+    }
+    __syncthreads();
+    // u = A y
+    for (int64_t ps0 = 0; ps0 < passes; ps0 += UP) {
+        int64_t ndu[UP];
+        bool oku[UP];
+        T au[UP];
+#pragma unroll
+        for (int k = 0; k < UP; ++k) {
+            int jk;
+            bool nok;
+            node_of(ps0 + k, ndu[k], nok, jk);
+            oku[k] = ps0 + k < passes && nok && S.act[jk];
+        }
+        row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, y, au);
+#pragma unroll
+        for (int k = 0; k < UP; ++k)
+            if (oku[k] && sub < NDOF) {
+                const int64_t row = ndu[k] * NDOF + sub;
+                u[row] = A.fixed[row] ? T(0) : au[k];
+            }
+    }
+    int it = 0;
+    for (it = 0; it < A.max_it; ++it) {
+        // phase 1: p, v, y = M^-1 v, <rh, v>
+        {
+            WarpAcc acc;
+            acc.j = -1;
+            acc.v[0] = acc.v[1] = 0.0;
+            for (int64_t ps = 0; ps < passes; ++ps) {
+                int64_t nd;
+                bool node_ok;
+                int j;
+                node_of(ps, nd, node_ok, j);
+                const bool on = node_ok && S.act[j];
+                const bool own = on && sub < NDOF;
+                const int64_t row = nd * NDOF + sub;
+                T vn = T(0);
+                bool fx = true;
+                double val[kBSlots] = {0.0, 0.0};
+                if (own) {
+                    const T tb = (T)S.rho_old[j], tbo = (T)(S.rho_old[j] * S.omega[j]);
+                    fx = A.fixed[row] != 0;
+                    const T vo = v[row];
+                    p[row] = r[row] + tb * p[row] - tbo * vo;
+                    vn = u[row] + tb * vo - tbo * q[row];
+                    v[row] = vn;
+                    val[0] = (double)rh[row] * (double)vn;
+                }
+                const T yv = node_apply<NDOF, T>(A.binv, nd, on, sub, nbase, vn, fx);
+                if (own) y[row] = yv;
+                wacc_add(acc, S, w, lane, own, j, val);
+            }
+            wacc_flush(acc, S, w, lane);
+            bpartials(S, L, ns, BS_RHV, -1);
+        }
+        grid.sync();
+        if (threadIdx.x == 0) {
+            S.cnt = *(volatile int *)&L.active_cnt[it & 1];
+            if (b == 0) L.active_cnt[(it + 1) & 1] = 0;
+        }
+        btotals(S, L, fs, ns, BS_RHV, -1);            // ends with __syncthreads (S.cnt visible)
+        if (S.cnt == 0) break;
+        for (int j = threadIdx.x; j < ns; j += blockDim.x)
+            if (S.act[j]) S.alpha[j] = S.tot[0][j] != 0.0 ? S.rho[j] / S.tot[0][j] : 0.0;
+        __syncthreads();
+        // phase 2: q = A y, s = r - alpha v, t = u - alpha q, <t, s>, <t, t>
+        {
+            WarpAcc acc;
+            acc.j = -1;
+            acc.v[0] = acc.v[1] = 0.0;
+            for (int64_t ps0 = 0; ps0 < passes; ps0 += UP) {
+                int64_t ndu[UP];
+                bool oku[UP];
+                int ju[UP];
+                T au[UP];
+#pragma unroll
+                for (int k = 0; k < UP; ++k) {
+                    bool nok;
+                    node_of(ps0 + k, ndu[k], nok, ju[k]);
+                    oku[k] = ps0 + k < passes && nok && S.act[ju[k]];
+                }
+                row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, y, au);
+#pragma unroll
+                for (int k = 0; k < UP; ++k) {
+                    const bool own = oku[k] && sub < NDOF;
+                    const int j = ju[k];
+                    double val[kBSlots] = {0.0, 0.0};
+                    if (own) {
+                        const int64_t row = ndu[k] * NDOF + sub;
+                        const T ta = (T)S.alpha[j];
+                        const T qn = A.fixed[row] ? T(0) : au[k];
+                        q[row] = qn;
+                        const T sv = r[row] - ta * v[row];
+                        const T tv = u[row] - ta * qn;
+                        r[row] = sv;
+                        t[row] = tv;
+                        val[0] = (double)tv * (double)sv;
+                        val[1] = (double)tv * (double)tv;
+                    }
+                    wacc_add(acc, S, w, lane, own, j, val);
+                }
+            }
+            wacc_flush(acc, S, w, lane);
+            bpartials(S, L, ns, BS_TS, BS_TT);
+        }
+        grid.sync();
+        btotals(S, L, fs, ns, BS_TS, BS_TT);
+        for (int j = threadIdx.x; j < ns; j += blockDim.x)
+            if (S.act[j]) S.omega[j] = S.tot[1][j] != 0.0 ? S.tot[0][j] / S.tot[1][j] : 0.0;
+        __syncthreads();
+        // phase 3: x~ += alpha p + omega s, r = s - omega t, y = M^-1 r, <rh, r>, <r, r>
+        {
+            WarpAcc acc;
+            acc.j = -1;
+            acc.v[0] = acc.v[1] = 0.0;
+            for (int64_t ps = 0; ps < passes; ++ps) {
+                int64_t nd;
+                bool node_ok;
+                int j;
+                node_of(ps, nd, node_ok, j);
+                const bool on = node_ok && S.act[j];
+                const bool own = on && sub < NDOF;
+                const int64_t row = nd * NDOF + sub;
+                T rn = T(0);
+                bool fx = true;
+                double val[kBSlots] = {0.0, 0.0};
+                if (own) {
+                    const T ta = (T)S.alpha[j], to = (T)S.omega[j];
+                    fx = A.fixed[row] != 0;
+                    const T sv = r[row];
+                    xt[row] += ta * p[row] + to * sv;
+                    rn = sv - to * t[row];
+                    r[row] = rn;
+                    val[0] = (double)rh[row] * (double)rn;
+                    val[1] = (double)rn * (double)rn;
+                }
+                const T yv = node_apply<NDOF, T>(A.binv, nd, on, sub, nbase, rn, fx);
+                if (own) y[row] = yv;
+                wacc_add(acc, S, w, lane, own, j, val);
+            }
+            wacc_flush(acc, S, w, lane);
+            bpartials(S, L, ns, BS_RHO, BS_RR);
+        }
+        grid.sync();
+        btotals(S, L, fs, ns, BS_RHO, BS_RR);
+        // per-specimen decisions (S.st = 4 marks a restart for phase 4)
+        for (int j = threadIdx.x; j < ns; j += blockDim.x) {
+            if (!S.act[j]) continue;
+            const int sp = fs + j;
+            const double rel = sqrt(S.tot[1][j]) / S.bn[j];
+            S.rel[j] = rel;
+            S.its[j] = it + 1;
+            if (!(rel == rel)) {
+                S.st[j] = 2;
+                S.act[j] = 0;
+            } else if (rel <= L.rtol[sp]) {
+                S.act[j] = 0;
+            } else if (S.tot[0][j] == 0.0 || S.omega[j] == 0.0 || S.rho[j] == 0.0) {
+                // restart the recurrences with rh = r (at most 16 times)
+                if (S.rst[j] >= 16) {
+                    S.st[j] = 1;
+                    S.act[j] = 0;
+                } else {
+                    ++S.rst[j];
+                    S.st[j] = 4;
+                    S.rho_old[j] = 0.0;            // beta = 0
+                    S.rho[j] = S.tot[1][j];
+                }
+            } else {
+                S.rho_old[j] = (S.tot[0][j] / S.rho[j]) * (S.alpha[j] / S.omega[j]);   // beta
+                S.rho[j] = S.tot[0][j];
+            }
+            if (S.act[j] && b == L.spec_b0[sp]) atomicAdd(&L.active_cnt[(it + 1) & 1], 1);
+        }
+        __syncthreads();
+        // phase 4: u = A y (and rh = r on a restart)
+        for (int64_t ps0 = 0; ps0 < passes; ps0 += UP) {
+            int64_t ndu[UP];
+            bool oku[UP];
+            int ju[UP];
+            T au[UP];
+#pragma unroll
+            for (int k = 0; k < UP; ++k) {
+                bool nok;
+                node_of(ps0 + k, ndu[k], nok, ju[k]);
+                oku[k] = ps0 + k < passes && nok && S.act[ju[k]];
+            }
+            row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, y, au);
+#pragma unroll
+            for (int k = 0; k < UP; ++k)
+                if (oku[k] && sub < NDOF) {
+                    const int64_t row = ndu[k] * NDOF + sub;
+                    u[row] = A.fixed[row] ? T(0) : au[k];
+                    if (S.st[ju[k]] == 4) rh[row] = r[row];
+                }
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < ns; j += blockDim.x)
+            if (S.st[j] == 4) S.st[j] = 0;
+        __syncthreads();
+    }
+    // x = M^-1 x~ (not for skipped specimens)
+    for (int64_t ps = 0; ps < passes; ++ps) {
+        int64_t nd;
+        bool node_ok;
+        int j;
+        node_of(ps, nd, node_ok, j);
+        if (node_ok && S.keep[j]) node_ok = false;     // warp-uniform use below only through node_ok
+        const bool own = node_ok && sub < NDOF;
+        const int64_t row = nd * NDOF + sub;
+        const bool fx = own ? A.fixed[row] != 0 : true;
+        const T xv = own ? xt[row] : T(0);
+        const T xo = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, xv, fx);
+        if (own) A.x_out[row] = (double)xo;
+    }
+    for (int j = threadIdx.x; j < ns; j += blockDim.x) {
+        const int sp = fs + j;
+        if (b != L.spec_b0[sp] || S.keep[j]) continue;
+        L.out[3 * sp + 0] = S.its[j];
+        L.out[3 * sp + 1] = S.rel[j];
+        L.out[3 * sp + 2] = S.act[j] ? 3 : S.st[j];   // still active: iteration cap
     }
 }
 
@@ -443,20 +974,66 @@ cudaError_t solve_t(const KrylovCtx &c, const V *vals, const double *b, double *
     A.rtol = rtol;
     A.max_it = max_it;
     void *args[] = {&A};
-    return cudaLaunchCooperativeKernel((void *)bicgstab_kernel<NDOF, G, V, T>, dim3(c.blocks), dim3(kThreads), args, 0,
-                                       c.stream);
+    return cudaLaunchCooperativeKernel((void *)bicgstab3_kernel<NDOF, G, V, T>, dim3(c.blocks), dim3(kThreads), args,
+                                       0, c.stream);
 }
 
 template <int NDOF, class V, class T>
-int coop_blocks(int num_sms)
+cudaError_t solve_batch_t(const KrylovCtx &c, const gd::BatchKrylov &L, const V *vals, const double *b, double *x,
+                          int max_it)
 {
     constexpr int G = NDOF == 3 ? 8 : 32;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bicgstab_kernel<NDOF, G, V, T>, kThreads, 0) !=
+    T *binv = (T *)c.binv;
+    block_inverse_kernel<NDOF, V, T><<<c.num_sms * 4, 256, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, vals,
+                                                                          c.fixed, binv);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(L.active_cnt, 0, 2 * sizeof(int), c.stream);
+    if (e != cudaSuccess) return e;
+    KArgs<V, T> A;
+    A.n_nodes = c.n_nodes;
+    A.rowptr = c.rowptr;
+    A.colidx = c.colidx;
+    A.vals = vals;
+    A.fixed = c.fixed;
+    A.binv = binv;
+    A.b = b;
+    A.x_out = x;
+    T *w[9];
+    for (int k = 0; k < 8; ++k) w[k] = (T *)c.work[k];
+    w[8] = (T *)c.work_x;
+    A.x = std::is_same<T, double>::value ? (T *)x : w[8];
+    A.r = w[0];
+    A.rh = w[1];
+    A.p = w[2];
+    A.v = w[3];
+    A.s = w[4];
+    A.t = w[5];
+    A.y = w[6];
+    A.z = w[7];
+    A.red = nullptr;
+    A.out = nullptr;
+    A.rtol = 0.0;
+    A.max_it = max_it;
+    gd::BatchKrylov Lc = L;
+    void *args[] = {&A, &Lc};
+    return cudaLaunchCooperativeKernel((void *)bicgstab3_batch_kernel<NDOF, G, V, T>, dim3(c.blocks), dim3(kThreads),
+                                       args, 0, c.stream);
+}
+
+// co-resident CTAs per SM of the solve kernels of one variant
+template <int NDOF, class V, class T>
+int coop_per_sm()
+{
+    constexpr int G = NDOF == 3 ? 8 : 32;
+    int per_sm = 0, per_sm_b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bicgstab3_kernel<NDOF, G, V, T>, kThreads, 0) !=
         cudaSuccess)
         return 0;
-    if (per_sm > 2) per_sm = 2;
-    return per_sm * num_sms;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, bicgstab3_batch_kernel<NDOF, G, V, T>, kThreads, 0) !=
+        cudaSuccess)
+        return 0;
+    return per_sm_b < per_sm ? per_sm_b : per_sm;
 }
 
 __global__ void narrow_kernel(const double *in, float *out, int64_t n)
@@ -467,13 +1044,17 @@ __global__ void narrow_kernel(const double *in, float *out, int64_t n)
 
 }  // namespace
 
-int krylov_blocks(int ndof, bool fp32_vals, int num_sms)
+int krylov_blocks(int ndof, bool fp32_vals, int num_sms, int cap)
 {
     // the smallest co-resident grid over the variants, so one size fits every launch
-    int a = ndof == 3 ? coop_blocks<3, double, double>(num_sms) : coop_blocks<4, double, double>(num_sms);
-    int b = ndof == 3 ? coop_blocks<3, float, float>(num_sms) : coop_blocks<4, float, float>(num_sms);
+    int a = ndof == 3 ? coop_per_sm<3, double, double>() : coop_per_sm<4, double, double>();
+    int b = ndof == 3 ? coop_per_sm<3, float, float>() : coop_per_sm<4, float, float>();
+    int c = ndof == 3 ? coop_per_sm<3, float, double>() : coop_per_sm<4, float, double>();
     (void)fp32_vals;
-    return a < b ? a : b;
+    int per_sm = a < b ? a : b;
+    if (c < per_sm) per_sm = c;
+    if (cap > 0 && per_sm > cap) per_sm = cap;
+    return per_sm * num_sms;
 }
 
 cudaError_t krylov_solve(const KrylovCtx &c, const void *vals, bool fp32_vals, const double *b, double *x,
@@ -489,6 +1070,21 @@ cudaError_t krylov_solve(const KrylovCtx &c, const void *vals, bool fp32_vals, c
                          : solve_t<3, double, double>(c, (const double *)vals, b, x, rtol, max_it);
     return fp32_vals ? solve_t<4, float, double>(c, (const float *)vals, b, x, rtol, max_it)
                      : solve_t<4, double, double>(c, (const double *)vals, b, x, rtol, max_it);
+}
+
+cudaError_t krylov_solve_batch(const KrylovCtx &c, const BatchKrylov &L, const void *vals, bool fp32_vals,
+                               const double *b, double *x, int max_it, bool fp32_vectors)
+{
+    if (fp32_vectors) {
+        if (!fp32_vals) return cudaErrorInvalidValue;
+        return c.ndof == 3 ? solve_batch_t<3, float, float>(c, L, (const float *)vals, b, x, max_it)
+                           : solve_batch_t<4, float, float>(c, L, (const float *)vals, b, x, max_it);
+    }
+    if (c.ndof == 3)
+        return fp32_vals ? solve_batch_t<3, float, double>(c, L, (const float *)vals, b, x, max_it)
+                         : solve_batch_t<3, double, double>(c, L, (const double *)vals, b, x, max_it);
+    return fp32_vals ? solve_batch_t<4, float, double>(c, L, (const float *)vals, b, x, max_it)
+                     : solve_batch_t<4, double, double>(c, L, (const double *)vals, b, x, max_it);
 }
 
 cudaError_t narrow_to_float(const double *in, float *out, int64_t n, cudaStream_t s)

@@ -415,6 +415,15 @@ __global__ void reaction_kernel(const double *R, const int32_t *react_dof, int64
     }
 }
 
+// d = 1 - f_d(kappa) = 1 - exp(-eta_d <kappa - kappa_d>_+) at every quadrature point
+__global__ void damage_field_kernel(const double *kappa, int64_t n, double eta_d, double kappa_d, double *out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double k = kappa[i];
+        out[i] = k > kappa_d ? -expm1(-eta_d * (k - kappa_d)) : 0.0;
+    }
+}
+
 __global__ void damage_max_kernel(const double *kappa, int64_t n, double eta_d, double kappa_d, double *out)
 {
     double mx = 0.0;
@@ -633,6 +642,18 @@ cudaError_t launch_scale_spec(int64_t n, int ndof, double *out, const double *in
     return cudaGetLastError();
 }
 
+__global__ void fill_kernel(double *v, double val, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = val;
+}
+
+cudaError_t launch_fill(double *v, double val, int64_t n, cudaStream_t s)
+{
+    fill_kernel<<<256, kThreads, 0, s>>>(v, val, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_reaction_batch(const double *R, const int32_t *react_dof, const int64_t *off, int n_spec, double *out,
                                   cudaStream_t s)
 {
@@ -650,6 +671,13 @@ cudaError_t launch_damage_max(const double *kappa, int64_t n, double eta_d, doub
                               cudaStream_t s)
 {
     damage_max_kernel<<<1, 1024, 0, s>>>(kappa, n, eta_d, kappa_d, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_damage_field(const double *kappa, int64_t n, double eta_d, double kappa_d, double *out,
+                                cudaStream_t s)
+{
+    damage_field_kernel<<<256, kThreads, 0, s>>>(kappa, n, eta_d, kappa_d, out);
     return cudaGetLastError();
 }
 

@@ -46,7 +46,7 @@ def test_header_functions_exported(B):
 def test_struct_layout_matches_header(B):
     structs = {"gd_mesh": B.GdMesh, "gd_icnn": B.GdIcnn, "gd_material": B.GdMaterial,
                "gd_load_path": B.GdLoadPath, "gd_options": B.GdOptions, "gd_newton_report": B.GdNewtonReport,
-               "gd_path_report": B.GdPathReport}
+               "gd_path_report": B.GdPathReport, "gd_tune_report": B.GdTuneReport}
     prog = "#include <stdio.h>\n#include <stddef.h>\n#include \"gd.h\"\nint main(void){\n"
     for n in structs:
         prog += f'printf("{n} %zu\\n", sizeof({n}));\n'

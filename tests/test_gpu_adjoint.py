@@ -47,7 +47,10 @@ def gpu_loss(B, prob, theta, target, k=2):
     h = B.gd_create(prob, opts(B, k))
     n_psi = prob.psi.params.size
     B.gd_set_params(h, theta[:n_psi], theta[n_psi:])
-    reac, _ = B.gd_run_load_path(h)
+    reac, rep = B.gd_run_load_path(h)
+    # a halved step adds commits to the path; differences across runs with different
+    # commit sequences would not be derivatives of one discrete path
+    assert rep.step_cuts == 0
     return loss_and_grad_target(reac, target)[0], h, reac
 
 
@@ -57,7 +60,8 @@ def test_adjoint_vs_central_differences(env, energy):
     prob = small_problem(energy=energy)
     theta0 = np.concatenate([prob.psi.params, prob.yld.params])
     h = B.gd_create(prob, opts(B))
-    reac0, _ = B.gd_run_load_path(h)
+    reac0, rep0 = B.gd_run_load_path(h)
+    assert rep0.step_cuts == 0
     target = 0.9 * reac0 + 0.001
     L0, dL = loss_and_grad_target(reac0, target)
     g = B.gd_backward(h, dL)
@@ -118,3 +122,28 @@ def test_adjoint_vs_oracle_finite_differences(env):
         tm = theta0.copy(); tm[i] -= step
         fd = (oracle_loss(tp) - oracle_loss(tm)) / (2 * step)
         assert abs(g[i] - fd) <= 1e-5 * max(abs(fd), 1e-8), (i, g[i], fd)
+
+
+def test_autograd_function_matches_backward(env):
+    """GDLoadPath (torch.autograd.Function): forward gives gd_run_load_path's curve
+    from the undeformed state at theta, backward gives gd_backward's gradient."""
+    torch, B, oracle = env
+    from paper_2604_03411_gb300.autograd import reaction_curve
+    prob = small_problem(n_long=8, n_wide=4, steps=4)
+    theta0 = np.concatenate([prob.psi.params, prob.yld.params])
+    h = B.gd_create(prob, opts(B))
+    theta = torch.tensor(theta0 * 1.01, dtype=torch.float64, device="cuda", requires_grad=True)
+    reac = reaction_curve(theta, h)
+    w = torch.linspace(1.0, 2.0, reac.numel(), dtype=torch.float64, device="cuda")
+    (w * reac).sum().backward()
+    h2 = B.gd_create(prob, opts(B))
+    n_psi = prob.psi.params.size
+    B.gd_set_params(h2, theta0[:n_psi] * 1.01, theta0[n_psi:] * 1.01)
+    r2, _ = B.gd_run_load_path(h2)
+    g2 = B.gd_backward(h2, w.cpu().numpy())
+    assert np.abs(reac.detach().cpu().numpy() - r2).max() <= 1e-10 * np.abs(r2).max()
+    g = theta.grad.cpu().numpy()
+    assert np.abs(g - g2).max() <= 1e-8 * np.abs(g2).max()
+    # a second call on the same handle restarts the path from the undeformed state
+    reac_again = reaction_curve(theta.detach(), h)
+    assert torch.allclose(reac_again, reac.detach(), rtol=1e-10, atol=0)

@@ -34,12 +34,16 @@ def test_cfg1_load_unload_reload_path(env):
     h = B.gd_create(prob, tight(B))
     reac, rep = B.gd_run_load_path(h)
     assert rep.steps_done == 40
-    dofs, kappa = B.gd_get_fields(h)
+    dofs, kappa, dmg = B.gd_get_fields(h, damage=True)
     model = oracle.Model.from_problem(prob)
     ref = oracle.run_load_path(model, prob.mesh, prob.load, rtol=1e-12, atol=1e-14)
     assert rel_err(reac, ref["reaction"]) < 1e-10
     assert rel_err(dofs, ref["dofs"]) < 1e-10
     assert rel_err(kappa, ref["kappa"]) < 1e-10
+    # damage field: d = 1 - exp(-eta_d <kappa - kappa_d>_+) (the degradation function's definition)
+    m = prob.mat
+    d_ref = 1.0 - np.exp(-m.eta_d * np.maximum(ref["kappa"] - m.kappa_d, 0.0))
+    assert np.abs(dmg - d_ref).max() < 1e-10 and dmg.min() >= 0.0 and dmg.max() < 1.0 and dmg.max() > 0.0
 
 
 def test_homogeneous_patch_32x32_matches_material_point(env):
@@ -94,6 +98,20 @@ def test_newton_step_reports_and_state_roundtrip(env):
     # path to the same solution: agreement to the Newton tolerance
     assert rel_err(d2b, d2) < 1e-10 and rel_err(k2b, k2) < 1e-10
     assert abs(r2b.reaction - r2.reaction) <= 1e-10 * abs(r2.reaction)
+    # a full save/restore (with the previous state for the predictor) repeats the
+    # uninterrupted step: same Newton path, same result up to summation order
+    h2 = B.gd_create(prob, tight(B))
+    B.gd_newton_step(h2)
+    saved = B.gd_get_state(h2)
+    assert saved[3] == 1
+    r2c = B.gd_newton_step(h2)
+    d2c, dp2c, k2c, ns2c = B.gd_get_state(h2)
+    assert ns2c == 2 and rel_err(dp2c, saved[0]) == 0.0
+    B.gd_set_state(h2, saved[0], saved[2], saved[3], dofs_prev=saved[1])
+    r2d = B.gd_newton_step(h2)
+    d2d, _, k2d, _ = B.gd_get_state(h2)
+    assert r2d.iterations == r2c.iterations
+    assert rel_err(d2d, d2c) < 1e-12 and rel_err(k2d, k2c) < 1e-12
 
 
 def test_errors_are_reported_not_faulted(env):
@@ -155,3 +173,21 @@ def test_krylov_solve_matches_sparse_lu(env):
     assert true_rel < 1e-10
     # forward error is bounded by cond(K) x residual; the Newton systems here have cond ~1e4-1e5
     assert rel_err(x[free], xr) < 1e-6
+
+
+def test_autotune_keeps_results(env):
+    """gd_autotune picks launch shapes from its own timings; a tuned handle gives the
+    untuned handle's load path to the Newton tolerance."""
+    torch, B, oracle = env
+    prob = I.config2(n_long=40, n_wide=16)
+    prob.load = prob.load[:3]
+    h0 = B.gd_create(prob, tight(B))
+    r0, _ = B.gd_run_load_path(h0)
+    h1 = B.gd_create(prob, tight(B))
+    t = B.gd_autotune(h1)
+    assert t.asm_warps in (2, 4, 8) and 1 <= t.krylov_ctas_per_sm <= 4
+    times = [x for x in t.asm_ms if x > 0]
+    assert times and t.asm_ms[[2, 4, 8].index(t.asm_warps)] == min(times)
+    assert t.krylov_us[t.krylov_ctas_per_sm - 1] > 0
+    r1, _ = B.gd_run_load_path(h1)
+    assert np.abs(r1 - r0).max() <= 1e-9 * np.abs(r0).max()
