@@ -283,7 +283,7 @@ gd_status gd_solve(gd_handle *h, const void *csr_vals, const double *b, double *
  * solve.  Work runs on `stream` (a cudaStream_t, NULL for the legacy default
  * stream), which the call synchronises.
  * Work space: one fixed device array inside the library, sized for
- * GD_NOALLOC_MAX_DOFS dofs (about 12.6 MB), held by every GPU that loads the
+ * GD_NOALLOC_MAX_DOFS dofs (about 13.7 MB), held by every GPU that loads the
  * library until the process exits; larger systems are rejected with GD_ERR_ARG.
  * The first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture.  Every call

@@ -233,6 +233,7 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
     kc.fixed = H.fixed;
     kc.binv = H.binv;
     for (int k = 0; k < 8; ++k) kc.work[k] = H.kv[k];
+    kc.work[8] = H.kv[10];
     kc.work_x = H.kx;
     kc.red = H.red;
     kc.out = H.scal + 24;
@@ -352,6 +353,7 @@ gd_status krylov_batch(gd::Handle &H, const std::vector<double> &eta, const doub
     kc.fixed = H.fixed;
     kc.binv = H.binv;
     for (int k = 0; k < 8; ++k) kc.work[k] = H.kv[k];
+    kc.work[8] = H.kv[10];
     kc.work_x = H.kx;
     kc.red = H.red;
     kc.out = H.scal + 24;

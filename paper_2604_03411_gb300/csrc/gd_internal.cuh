@@ -179,7 +179,7 @@ struct Handle {
     int8_t *loading = nullptr, *loading2 = nullptr;
     int *counters = nullptr;                             // device [8]
     // Krylov workspace (FP64 vectors of n_dofs)
-    double *kv[10] = {};
+    double *kv[11] = {};                                 // Krylov: 0..7 and 10; Newton: 8, 9
     double *diag = nullptr;
     double *binv = nullptr;                              // node-block Jacobi inverses
     float *vals_f32 = nullptr;                           // FP32 tangent copy for the inner solve (FP64 mode)
@@ -241,13 +241,10 @@ struct SolverCtx {
     int blocks;
     long long *launches;        // host counter of kernel launches (may be null)
 };
-cudaError_t launch_jacobi_diag(const SolverCtx &c, double *diag);
 // y = A x; free_only: prescribed rows copy x, prescribed columns skipped
 cudaError_t launch_spmv(const SolverCtx &c, const double *x, double *y, int free_only);
 // Solves A x = b on the free dofs (A = vals with prescribed rows/cols removed);
 // x is overwritten; returns iterations (>= 0) or -1 on breakdown / cap.
-int bicgstab(const SolverCtx &c, const double *diag, const double *b, double *x, double *work[8],
-             double rtol, int max_it, double *final_rel);
 cudaError_t launch_norm2_free(const SolverCtx &c, const double *v, double *out_dev, double *out_fixed_dev);
 cudaError_t launch_axpy_free(const SolverCtx &c, double *y, const double *x, double alpha);
 // r = b - y on free dofs (0 on prescribed), *out_norm = ||r|| (device)
@@ -284,7 +281,7 @@ struct KrylovCtx {
     const int32_t *rowptr, *colidx;
     const uint8_t *fixed;
     double *binv;               // [n_nodes * ndof * ndof]
-    double *work[8];            // [n_nodes * ndof] each
+    double *work[9];            // [n_nodes * ndof] each
     double *work_x;             // iterate when the vectors are FP32
     double *red;                // [8 * blocks]
     double *out;                // [3] device: iterations, relative residual, status

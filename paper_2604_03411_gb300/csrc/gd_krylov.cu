@@ -36,7 +36,7 @@ struct KArgs {
     const double *b;
     double *x_out;            // solution (FP64)
     T *x;                     // iterate (x_out itself when T is double)
-    T *r, *rh, *p, *v, *s, *t, *y, *z;
+    T *r, *rh, *p, *v, *s, *t, *y, *z, *w;
     double *red;              // [8][nb] block partials
     double *out;              // [0] iterations, [1] final relative residual, [2] status
     double rtol;
@@ -208,8 +208,11 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
     const int64_t nw = ((int64_t)gridDim.x * kThreads) >> 5;
     const int64_t n_nodes = A.n_nodes;
     const int64_t passes = (n_nodes + nw * NPW - 1) / (nw * NPW);   // warp-uniform
-    // vector roles: r (also s), rh, p, v, q, t, y (= M^-1 v or M^-1 r), u
-    T *r = A.r, *rh = A.rh, *p = A.p, *v = A.v, *q = A.s, *t = A.t, *y = A.y, *u = A.z, *xt = A.x;
+    // vector roles: r (also s), rh, p, v, q, t, y = M^-1 v (read by phase 2's product),
+    // w = M^-1 r (read by phase 4's product), u.  y and w must differ: phase 1 of the
+    // next iteration writes y with no barrier after phase 4, whose product still reads
+    // other lanes' w
+    T *r = A.r, *rh = A.rh, *p = A.p, *v = A.v, *q = A.s, *t = A.t, *y = A.y, *wv = A.w, *u = A.z, *xt = A.x;
     // partial-sum slots: consecutive phases use different slots, so that a block
     // writing the next phase's partials never overwrites ones another block is
     // still summing after the barrier
@@ -233,7 +236,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                 v[row] = T(0);
                 q[row] = T(0);
                 xt[row] = T(0);
-                y[row] = yv;
+                wv[row] = yv;
                 rr += (double)bv * (double)bv;
             }
         }
@@ -253,7 +256,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
     if (!(bnorm > 0.0)) {
         if (!(bnorm == 0.0)) status = 2;
     } else {
-        // u = A y
+        // u = A w
         for (int64_t ps0 = 0; ps0 < passes; ps0 += UP) {
             int64_t ndu[UP];
             bool oku[UP];
@@ -263,7 +266,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                 ndu[k] = (gw + (ps0 + k) * nw) * NPW + slot;
                 oku[k] = ps0 + k < passes && slot < NPW && ndu[k] < n_nodes;
             }
-            row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, y, au);
+            row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, wv, au);
 #pragma unroll
             for (int k = 0; k < UP; ++k)
                 if (oku[k] && sub < NDOF) {
@@ -364,8 +367,8 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                         prhr += (double)rh[row] * (double)rn;
                         prr += (double)rn * (double)rn;
                     }
-                    const T yv = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, rn, fx);
-                    if (own) y[row] = yv;
+                    const T wn = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, rn, fx);
+                    if (own) wv[row] = wn;
                 }
                 double pv[2] = {prhr, prr};
                 const int sl[2] = {S_RHO, S_RR};
@@ -402,7 +405,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                 beta = (t3[0] / rho) * (alpha / omega);
                 rho = t3[0];
             }
-            // phase 4: u = A y (and rh = r on a restart)
+            // phase 4: u = A w (and rh = r on a restart)
             for (int64_t ps0 = 0; ps0 < passes; ps0 += UP) {
                 int64_t ndu[UP];
                 bool oku[UP];
@@ -412,7 +415,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                     ndu[k] = (gw + (ps0 + k) * nw) * NPW + slot;
                     oku[k] = ps0 + k < passes && slot < NPW && ndu[k] < n_nodes;
                 }
-                row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, y, au);
+                row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, wv, au);
 #pragma unroll
                 for (int k = 0; k < UP; ++k)
                     if (oku[k] && sub < NDOF) {
@@ -582,7 +585,8 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
     const int fs = n0 < n1 ? L.blk_fs[b] : 0;
     const int ns = n0 < n1 ? L.blk_ns[b] : 0;
     const int64_t passes = (L.chunk + (int64_t)kWarpsPB * NPW - 1) / ((int64_t)kWarpsPB * NPW);   // grid-uniform
-    T *r = A.r, *rh = A.rh, *p = A.p, *v = A.v, *q = A.s, *t = A.t, *y = A.y, *u = A.z, *xt = A.x;
+    // y = M^-1 v and w = M^-1 r are separate for the reason given at bicgstab3_kernel
+    T *r = A.r, *rh = A.rh, *p = A.p, *v = A.v, *q = A.s, *t = A.t, *y = A.y, *wv = A.w, *u = A.z, *xt = A.x;
     for (int i = threadIdx.x; i < kWarpsPB * kBSlots * kMaxSpecPerBlock; i += blockDim.x) (&S.acc[0][0][0])[i] = 0.0;
     for (int j = threadIdx.x; j < kMaxSpecPerBlock; j += blockDim.x) {
         S.act[j] = 1;
@@ -626,7 +630,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
                 q[row] = T(0);
                 // x~ may be the output itself (FP64): a skipped specimen keeps its x
                 if (L.rtol[fs + j] >= 0.0) xt[row] = T(0);
-                y[row] = yv;
+                wv[row] = yv;
                 val[0] = val[1] = (double)bv * (double)bv;
             }
             wacc_add(acc, S, w, lane, own, j, val);
@@ -647,7 +651,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
         if (S.act[j] && b == L.spec_b0[sp]) atomicAdd(&L.active_cnt[0], 1);
     }
     __syncthreads();
-    // u = A y
+    // u = A w
     for (int64_t ps0 = 0; ps0 < passes; ps0 += UP) {
         int64_t ndu[UP];
         bool oku[UP];
@@ -659,7 +663,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
             node_of(ps0 + k, ndu[k], nok, jk);
             oku[k] = ps0 + k < passes && nok && S.act[jk];
         }
-        row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, y, au);
+        row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, wv, au);
 #pragma unroll
         for (int k = 0; k < UP; ++k)
             if (oku[k] && sub < NDOF) {
@@ -782,8 +786,8 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
                     val[0] = (double)rh[row] * (double)rn;
                     val[1] = (double)rn * (double)rn;
                 }
-                const T yv = node_apply<NDOF, T>(A.binv, nd, on, sub, nbase, rn, fx);
-                if (own) y[row] = yv;
+                const T wn = node_apply<NDOF, T>(A.binv, nd, on, sub, nbase, rn, fx);
+                if (own) wv[row] = wn;
                 wacc_add(acc, S, w, lane, own, j, val);
             }
             wacc_flush(acc, S, w, lane);
@@ -821,7 +825,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
             if (S.act[j] && b == L.spec_b0[sp]) atomicAdd(&L.active_cnt[(it + 1) & 1], 1);
         }
         __syncthreads();
-        // phase 4: u = A y (and rh = r on a restart)
+        // phase 4: u = A w (and rh = r on a restart)
         for (int64_t ps0 = 0; ps0 < passes; ps0 += UP) {
             int64_t ndu[UP];
             bool oku[UP];
@@ -833,7 +837,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
                 node_of(ps0 + k, ndu[k], nok, ju[k]);
                 oku[k] = ps0 + k < passes && nok && S.act[ju[k]];
             }
-            row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, y, au);
+            row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, wv, au);
 #pragma unroll
             for (int k = 0; k < UP; ++k)
                 if (oku[k] && sub < NDOF) {
@@ -957,10 +961,11 @@ cudaError_t solve_t(const KrylovCtx &c, const V *vals, const double *b, double *
     A.binv = binv;
     A.b = b;
     A.x_out = x;
-    T *w[9];
-    for (int k = 0; k < 8; ++k) w[k] = (T *)c.work[k];
-    w[8] = (T *)c.work_x;
-    A.x = std::is_same<T, double>::value ? (T *)x : w[8];
+    T *w[10];
+    for (int k = 0; k < 9; ++k) w[k] = (T *)c.work[k];
+    w[9] = (T *)c.work_x;
+    A.x = std::is_same<T, double>::value ? (T *)x : w[9];
+    A.w = w[8];
     A.r = w[0];
     A.rh = w[1];
     A.p = w[2];
@@ -999,10 +1004,11 @@ cudaError_t solve_batch_t(const KrylovCtx &c, const gd::BatchKrylov &L, const V 
     A.binv = binv;
     A.b = b;
     A.x_out = x;
-    T *w[9];
-    for (int k = 0; k < 8; ++k) w[k] = (T *)c.work[k];
-    w[8] = (T *)c.work_x;
-    A.x = std::is_same<T, double>::value ? (T *)x : w[8];
+    T *w[10];
+    for (int k = 0; k < 9; ++k) w[k] = (T *)c.work[k];
+    w[9] = (T *)c.work_x;
+    A.x = std::is_same<T, double>::value ? (T *)x : w[9];
+    A.w = w[8];
     A.r = w[0];
     A.rh = w[1];
     A.p = w[2];

@@ -5,7 +5,7 @@
 // captured, an application that hands the whole device to its own memory pool,
 // or an embedding runtime that forbids allocation after start-up.  For them this
 // entry point takes the CSR system and the vectors from the caller and keeps all
-// of its work space (the eight BiCGStab vectors, the node-block inverses, the
+// of its work space (the nine BiCGStab vectors, the node-block inverses, the
 // reduction partials and the result words) in one file-scope device array of
 // fixed size.  Every GPU that loads the library holds that array until the
 // process exits.
@@ -25,8 +25,8 @@ namespace {
 constexpr int64_t kMaxDofs = GD_NOALLOC_MAX_DOFS;
 constexpr int kMaxBlocks = 4096;                      // cooperative grid cap (reduction partial slots)
 constexpr size_t kVec = (size_t)kMaxDofs;
-// 8 Krylov vectors, node-block inverses (n_nodes * ndof^2 <= 4 * n_dofs), partials, result words
-constexpr size_t kScratchDoubles = 8 * kVec + 4 * kVec + 8 * (size_t)kMaxBlocks + 8;
+// 9 Krylov vectors, node-block inverses (n_nodes * ndof^2 <= 4 * n_dofs), partials, result words
+constexpr size_t kScratchDoubles = 9 * kVec + 4 * kVec + 8 * (size_t)kMaxBlocks + 8;
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
@@ -76,10 +76,10 @@ extern "C" gd_status gd_solve_noalloc(int32_t ndof, int64_t n_nodes, const int32
     kc.rowptr = rowptr;
     kc.colidx = colidx;
     kc.fixed = fixed;
-    for (int k = 0; k < 8; ++k) kc.work[k] = base + (size_t)k * n;
+    for (int k = 0; k < 9; ++k) kc.work[k] = base + (size_t)k * n;
     kc.work_x = nullptr;
-    kc.binv = base + 8 * kVec;
-    kc.red = base + 12 * kVec;
+    kc.binv = base + 9 * kVec;
+    kc.red = base + 13 * kVec;
     kc.out = kc.red + 8 * (size_t)kMaxBlocks;
     kc.stream = (cudaStream_t)stream;
     kc.num_sms = num_sms;

@@ -69,53 +69,6 @@ __device__ __forceinline__ double sum_partials(const double *red, int slot, int 
     return res;
 }
 
-// y = A x on free rows, y = x on prescribed rows; warp per node: the ndof rows
-// of a node share one column list, read once; partial dots <a,y> and <b,y>
-// (a or b may be null) are written per block.
-template <int NDOF>
-__global__ void __launch_bounds__(kThreads) spmv_kernel(int64_t n_nodes, const int32_t *__restrict__ rowptr,
-                                                        const int32_t *__restrict__ colidx,
-                                                        const double *__restrict__ vals,
-                                                        const uint8_t *__restrict__ fixed,
-                                                        const double *__restrict__ x, double *__restrict__ y,
-                                                        const double *da, const double *db, double *red, int slot_a,
-                                                        int slot_b, int nb)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
-    double pa = 0.0, pb = 0.0;
-    for (int64_t nd = warp0; nd < n_nodes; nd += nwarps) {
-        const int64_t r0 = nd * NDOF;
-        const int32_t base = rowptr[r0];
-        const int32_t len = rowptr[r0 + 1] - base;
-        double acc[NDOF];
-#pragma unroll
-        for (int i = 0; i < NDOF; ++i) acc[i] = 0.0;
-        for (int j = lane; j < len; j += 32) {
-            const double xv = x[colidx[base + j]];
-#pragma unroll
-            for (int i = 0; i < NDOF; ++i) acc[i] += vals[base + (int64_t)i * len + j] * xv;
-        }
-#pragma unroll
-        for (int i = 0; i < NDOF; ++i) acc[i] = warp_sum(acc[i]);
-        if (lane < NDOF) {
-            double v = 0.0;
-#pragma unroll
-            for (int i = 0; i < NDOF; ++i)
-                if (i == lane) v = acc[i];
-            const int64_t r = r0 + lane;
-            if (fixed[r]) v = x[r];
-            y[r] = v;
-            if (da) pa += da[r] * v;
-            if (db) pb += db[r] * v;
-        }
-    }
-    double v2[2] = {pa, pb};
-    const int sl[2] = {slot_a, slot_b};
-    block_partials<2>(v2, red, sl, nb);
-}
-
 // plain y = A x (free_only: prescribed rows y = x, prescribed columns skipped)
 template <int NDOF>
 __global__ void __launch_bounds__(kThreads) spmv_plain_kernel(int64_t n_nodes, const int32_t *__restrict__ rowptr,
@@ -155,136 +108,9 @@ __global__ void __launch_bounds__(kThreads) spmv_plain_kernel(int64_t n_nodes, c
     }
 }
 
-// BiCGStab scalar slots in scal[]: 0 rho_old, 1 alpha, 2 omega, 3 rho, 4 flag
-// partial slots in red[]: 0 <rh,r>, 1 <rh,v>, 2 <t,s>, 3 <t,t>, 4 <r,r>, 5 <b,b>/misc
-enum { S_RHO = 0, S_RHV = 1, S_TS = 2, S_TT = 3, S_RR = 4, S_MISC = 5 };
+// partial slots in red[] of the vector kernels: 5, 6 norms and residuals
+enum { S_MISC = 5 };
 
-// p = r + beta (p - omega v), y = D^-1 p, beta = (rho/rho_old)(alpha/omega)
-__global__ void __launch_bounds__(kThreads) bicg_p_kernel(int64_t n, const double *__restrict__ r,
-                                                          double *__restrict__ p, const double *__restrict__ v,
-                                                          double *__restrict__ yv, const double *__restrict__ dinv,
-                                                          const double *red, double *scal, int nb, int first)
-{
-    const double rho = sum_partials(red, S_RHO, nb);
-    double beta = 0.0;
-    const double omega = scal[2];
-    // exact convergence or breakdown makes a denominator vanish: take a zero step
-    // and flag it (scal[4]) instead of producing 0/0
-    if (!first && scal[0] != 0.0 && omega != 0.0) beta = (rho / scal[0]) * (scal[1] / omega);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && rho == 0.0) scal[4] = 1.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double pv = first ? r[i] : r[i] + beta * (p[i] - omega * v[i]);
-        p[i] = pv;
-        yv[i] = dinv[i] * pv;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) scal[3] = rho;
-}
-
-// alpha = rho / <rh, v>; s = r - alpha v; z = D^-1 s
-__global__ void __launch_bounds__(kThreads) bicg_s_kernel(int64_t n, const double *__restrict__ r,
-                                                          const double *__restrict__ v, double *__restrict__ s,
-                                                          double *__restrict__ z, const double *__restrict__ dinv,
-                                                          const double *red, double *scal, int nb)
-{
-    const double rhv = sum_partials(red, S_RHV, nb);
-    const double alpha = rhv != 0.0 ? scal[3] / rhv : 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double sv = r[i] - alpha * v[i];
-        s[i] = sv;
-        z[i] = dinv[i] * sv;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) scal[1] = alpha;
-}
-
-// omega = <t,s>/<t,t>; x += alpha y + omega z; r = s - omega t; partials <rh,r>, <r,r>
-__global__ void __launch_bounds__(kThreads) bicg_x_kernel(int64_t n, double *__restrict__ x,
-                                                          const double *__restrict__ yv, const double *__restrict__ z,
-                                                          double *__restrict__ r, const double *__restrict__ s,
-                                                          const double *__restrict__ t, const double *__restrict__ rh,
-                                                          double *red, double *scal, int nb)
-{
-    const double ts = sum_partials(red, S_TS, nb);
-    const double tt = sum_partials(red, S_TT, nb);
-    const double omega = tt != 0.0 ? ts / tt : 0.0;
-    const double alpha = scal[1];
-    double prr = 0.0, prhr = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        x[i] += alpha * yv[i] + omega * z[i];
-        double rv = s[i] - omega * t[i];
-        r[i] = rv;
-        prr += rv * rv;
-        prhr += rh[i] * rv;
-    }
-    __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        scal[2] = omega;
-        scal[0] = scal[3];
-    }
-    double v2[2] = {prhr, prr};
-    const int sl[2] = {S_RHO, S_RR};
-    block_partials<2>(v2, red, sl, nb);
-}
-
-// r = b (free) / 0 (fixed), rh = r, x = 0, p = v = 0; partials <rh,r>, <r,r>
-__global__ void __launch_bounds__(kThreads) bicg_init_kernel(int64_t n, const double *__restrict__ b,
-                                                             const uint8_t *__restrict__ fixed,
-                                                             double *__restrict__ x, double *__restrict__ r,
-                                                             double *__restrict__ rh, double *__restrict__ p,
-                                                             double *__restrict__ v, double *red, double *scal, int nb)
-{
-    double prr = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double bv = fixed[i] ? 0.0 : b[i];
-        x[i] = 0.0;
-        r[i] = bv;
-        rh[i] = bv;
-        p[i] = 0.0;
-        v[i] = 0.0;
-        prr += bv * bv;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        scal[0] = 1.0;
-        scal[1] = 1.0;
-        scal[2] = 1.0;
-        scal[4] = 0.0;
-    }
-    double v2[2] = {prr, prr};
-    const int sl[2] = {S_RHO, S_RR};
-    block_partials<2>(v2, red, sl, nb);
-}
-
-// reduce a slot to scal[idx] (one block)
-__global__ void reduce_slot_kernel(const double *red, int slot, int nb, double *out)
-{
-    double s = sum_partials(red, slot, nb);
-    if (threadIdx.x == 0) *out = s;
-}
-
-// Jacobi: dinv_i = 1 / A_ii on free rows, 1 on prescribed rows
-template <int NDOF>
-__global__ void jacobi_kernel(int64_t n_nodes, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                              const double *__restrict__ vals, const uint8_t *__restrict__ fixed,
-                              double *__restrict__ dinv)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t nd = warp0; nd < n_nodes; nd += nwarps) {
-        const int64_t r0 = nd * NDOF;
-        const int32_t base = rowptr[r0];
-        const int32_t len = rowptr[r0 + 1] - base;
-        for (int j = lane; j < len; j += 32) {
-            const int32_t c = colidx[base + j];
-            if (c >= r0 && c < r0 + NDOF) {
-                const int i = (int)(c - r0);
-                const double d = vals[base + (int64_t)i * len + j];
-                dinv[r0 + i] = fixed[r0 + i] ? 1.0 : (d != 0.0 ? 1.0 / d : 1.0);
-            }
-        }
-    }
-}
-
-// ||v_free||^2 and ||v_fixed||^2 partials
 __global__ void __launch_bounds__(kThreads) norm_free_kernel(int64_t n, const double *__restrict__ v,
                                                              const uint8_t *__restrict__ fixed, double *red, int nb)
 {
@@ -481,19 +307,6 @@ __global__ void axpby_kernel(int64_t n, double *out, const double *x, double b, 
 
 int vec_grid(int64_t n, int nb) { return (int)((n + kThreads - 1) / kThreads < nb ? (n + kThreads - 1) / kThreads : nb); }
 
-cudaError_t spmv(const SolverCtx &c, const double *x, double *y, const double *da, const double *db, int slot_a,
-                 int slot_b)
-{
-    count(c);
-    if (c.ndof == 3)
-        spmv_kernel<3><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals, c.fixed, x, y,
-                                                           da, db, c.red, slot_a, slot_b, c.blocks);
-    else
-        spmv_kernel<4><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals, c.fixed, x, y,
-                                                           da, db, c.red, slot_a, slot_b, c.blocks);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 cudaError_t launch_spmv(const SolverCtx &c, const double *x, double *y, int free_only)
@@ -506,60 +319,6 @@ cudaError_t launch_spmv(const SolverCtx &c, const double *x, double *y, int free
         spmv_plain_kernel<4><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals, c.fixed, x,
                                                                  y, free_only);
     return cudaGetLastError();
-}
-
-cudaError_t launch_jacobi_diag(const SolverCtx &c, double *diag)
-{
-    count(c);
-    if (c.ndof == 3)
-        jacobi_kernel<3><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals, c.fixed, diag);
-    else
-        jacobi_kernel<4><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals, c.fixed, diag);
-    return cudaGetLastError();
-}
-
-// All blocks of the vector kernels use the same grid (c.blocks) so that every
-// partial slot has exactly c.blocks entries.
-int bicgstab(const SolverCtx &c, const double *dinv, const double *b, double *x, double *work[8], double rtol,
-             int max_it, double *final_rel)
-{
-    double *r = work[0], *rh = work[1], *p = work[2], *v = work[3], *s = work[4], *t = work[5], *yv = work[6],
-           *z = work[7];
-    const int nb = c.blocks;
-    bicg_init_kernel<<<nb, kThreads, 0, c.stream>>>(c.n, b, c.fixed, x, r, rh, p, v, c.red, c.scal, nb);
-    reduce_slot_kernel<<<1, kThreads, 0, c.stream>>>(c.red, S_RR, nb, c.scal + 8);
-    count(c, 2);
-    double h[2];
-    if (cudaMemcpyAsync(h, c.scal + 8, sizeof(double), cudaMemcpyDeviceToHost, c.stream) != cudaSuccess) return -1;
-    if (cudaStreamSynchronize(c.stream) != cudaSuccess) return -1;
-    const double bnorm = std::sqrt(h[0]);
-    if (final_rel) *final_rel = 0.0;
-    if (bnorm == 0.0) return 0;
-    const int check = 4;
-    for (int it = 0; it < max_it; ++it) {
-        bicg_p_kernel<<<nb, kThreads, 0, c.stream>>>(c.n, r, p, v, yv, dinv, c.red, c.scal, nb, it == 0);
-        spmv(c, yv, v, rh, nullptr, S_RHV, S_MISC);
-        bicg_s_kernel<<<nb, kThreads, 0, c.stream>>>(c.n, r, v, s, z, dinv, c.red, c.scal, nb);
-        spmv(c, z, t, s, t, S_TS, S_TT);
-        bicg_x_kernel<<<nb, kThreads, 0, c.stream>>>(c.n, x, yv, z, r, s, t, rh, c.red, c.scal, nb);
-        count(c, 3);
-        if ((it + 1) % check == 0 || it + 1 == max_it) {
-            reduce_slot_kernel<<<1, kThreads, 0, c.stream>>>(c.red, S_RR, nb, c.scal + 8);
-            count(c);
-            if (cudaMemcpyAsync(h, c.scal + 8, sizeof(double), cudaMemcpyDeviceToHost, c.stream) != cudaSuccess)
-                return -1;
-            double flag = 0.0;
-            if (cudaMemcpyAsync(&flag, c.scal + 4, sizeof(double), cudaMemcpyDeviceToHost, c.stream) != cudaSuccess)
-                return -1;
-            if (cudaStreamSynchronize(c.stream) != cudaSuccess) return -1;
-            const double rel = std::sqrt(h[0]) / bnorm;
-            if (final_rel) *final_rel = rel;
-            if (!std::isfinite(rel)) return -1;
-            if (rel <= rtol) return it + 1;
-            if (flag != 0.0) return -1;   // rho = 0 with a non-zero residual: breakdown
-        }
-    }
-    return -1;
 }
 
 cudaError_t launch_norm2_free(const SolverCtx &c, const double *v, double *out_dev, double *out_fixed_dev)
