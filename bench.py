@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
                     help="default: fp64 (mixed for the batch workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="FP64 runs only: skip the mixed-precision comparison on the same steps")
     ap.add_argument("--inner", default="auto", choices=["auto", "fp64", "refined"],
                     help="Newton inner-solve policy (gd_options.inner_solve)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
@@ -192,6 +194,42 @@ def run_reference(args):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def mixed_comparison(args, B, torch, prob, batch, stream, flush, reps64, n_qp):
+    """The same warm-up and timed load steps in GD_MIXED: device-timed throughput and
+    Newton-step time, and the reaction-force error against the FP64 run step by step."""
+    import numpy as np
+    opts = B.gd_default_options(precision=B.GD_MIXED, cuda_stream=stream.cuda_stream)
+    h = B.gd_create_batch(prob, opts) if batch else B.gd_create(prob, opts)
+    for _ in range(args.warmup):
+        B.gd_newton_step(h)
+    B.gd_autotune(h)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    reps = []
+    reac = []
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        reps.append(B.gd_newton_step(h))
+        evs[k][1].record(stream)
+        if batch:
+            reac.append(None)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    useful = sum(r.iterations + 1 + 2 * r.step_cuts for r in reps)
+    r32 = np.array([r.reaction for r in reps])
+    r64 = np.array([r.reaction for r in reps64])
+    err = float(np.max(np.abs(r32 - r64)) / max(np.max(np.abs(r64)), 1e-300)) if not batch else None
+    return {"value": n_qp * useful / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "newton_iterations": sum(r.iterations for r in reps),
+            "krylov_iterations": sum(r.krylov_iterations for r in reps),
+            "krylov_fp32_iterations": sum(r.krylov_fp32_iterations for r in reps),
+            "assembly_avg_ms": sum(r.assembly_ms for r in reps) / max(sum(r.assemblies for r in reps), 1),
+            "reaction_rel_err_vs_fp64": err,
+            "note": "same load steps as the FP64 line; reaction error = max over the timed steps of "
+                    "|F_mixed - F_fp64| / max |F_fp64|" if not batch else "batch: per-specimen reactions not compared here"}
 
 
 def run_gd(args):
@@ -388,6 +426,8 @@ def run_gd(args):
         "krylov_fp32_iterations": sum(r.krylov_fp32_iterations for r in reps),
         "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "tuning": tuning,
     }
+    if prec == B.GD_FP64 and not args.no_mixed:
+        line["mixed"] = mixed_comparison(args, B, torch, prob, batch, stream, flush, reps, n_qp)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(max(probs, key=lambda p: p.mesh.n_elems), args.cpu_seconds)
     if dist:

@@ -687,6 +687,8 @@ gd_status newton_batch(gd::Handle &H, gd_newton_report &rep)
     return GD_OK;
 }
 
+gd_status linear_predictor(gd::Handle &H);
+
 // load of specimen s at step coordinate t: piecewise linear through 0 at t = 0
 // and the path values at t = 1..n (held after the last step)
 double path_load(const gd::Handle &H, int s, double t)
@@ -711,7 +713,7 @@ gd_status predict(gd::Handle &H, double t)
         GD_CUDA(&H, gd::launch_predictor(H.n_dofs, H.w_dofs, H.dofs, extrap ? H.dofs_prev : nullptr,
                                          extrap ? (Lt - L1) / dl : 0.0, H.bc_dof, H.bc_scale, H.n_bc, Lt, H.stream));
         H.launches += H.n_bc > 0 ? 2 : 1;
-        return GD_OK;
+        return extrap ? GD_OK : linear_predictor(H);
     }
     std::vector<double> hl((size_t)2 * H.n_spec);
     for (int s = 0; s < H.n_spec; ++s) {
@@ -726,6 +728,33 @@ gd_status predict(gd::Handle &H, double t)
                                            H.stream));
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));     // hl is pageable host memory
     H.launches += H.n_bc > 0 ? 2 : 1;
+    return H.have_prev ? GD_OK : linear_predictor(H);
+}
+
+// First step of a path (no previous increment to extrapolate): the prescribed
+// increment d_bc on the committed state plus the free-dof response of the
+// committed state's tangent, K_ff delta = -K_f. d_bc (one assembly, one loose
+// solve).  Without it the whole increment sits in the first column of elements
+// at the loaded boundary, whose strain at the first Newton iterate is many times
+// the nominal one, and the iteration needs dozens of damped steps and halvings.
+gd_status linear_predictor(gd::Handle &H)
+{
+    double *dbc = H.diag, *y = H.kv[8], *rhs = H.kv[9];
+    GD_CUDA(&H, gd::launch_axpby(H.n_dofs, dbc, H.w_dofs, -1.0, H.dofs, H.stream));
+    ++H.launches;
+    gd_status st = assemble_pass(H, H.dofs, H.kappa, H.R_trial, H.vals, H.kappa_trial2, H.loading2, 1);
+    if (st) return st;
+    H.assembly_ms += elapsed_ms(H);
+    gd::SolverCtx c = solver_ctx(H, H.opt.precision == GD_FP64 ? H.vals : nullptr);
+    if (H.opt.precision != GD_FP64) c.vals32 = (const float *)H.vals;
+    GD_CUDA(&H, gd::launch_spmv(c, dbc, y, 0));      // K d_bc (all rows and columns)
+    GD_CUDA(&H, cudaMemsetAsync(rhs, 0, sizeof(double) * H.n_dofs, H.stream));
+    GD_CUDA(&H, gd::launch_axpy_free(c, rhs, y, -1.0));
+    int kit = 0;
+    double rel = 0.0;
+    // a loose solve is enough for an initial guess; a failed one leaves w as it is
+    if (krylov(H, H.vals, rhs, y, kit, rel, 1e-3, H.opt.precision == GD_MIXED, 0.5) == GD_OK)
+        GD_CUDA(&H, gd::launch_axpy_free(c, H.w_dofs, y, 1.0));
     return GD_OK;
 }
 

@@ -234,6 +234,7 @@ struct SolverCtx {
     const int32_t *rowptr;
     const int32_t *colidx;
     const double *vals;
+    const float *vals32 = nullptr;  // FP32 values (mixed mode); used instead of vals when set
     const uint8_t *fixed;
     cudaStream_t stream;
     double *red;                // [2 * blocks * 4]

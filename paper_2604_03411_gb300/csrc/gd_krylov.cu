@@ -73,28 +73,36 @@ __device__ __forceinline__ void partials(double (&v)[K], double *red, const int 
     __syncthreads();
 }
 
-// every block: sum of the partials of K slots in a fixed order (warp 0 reads and
-// reduces them, the result is broadcast through shared memory)
+// every block: sum of the partials of K slots in a fixed order.  All threads of the
+// block load the partials (one or two each: a single round of L2 latency; a loop
+// over them in one warp waits for nb/32 round trips in turn), then the block
+// reduces them in a fixed pattern, so every block obtains bit-identical totals.
 template <int K>
 __device__ __forceinline__ void totals(const double *red, const int (&slot)[K], double (&out)[K])
 {
-    __shared__ double sh[K];
-    const int nb = gridDim.x;
-    if (threadIdx.x < 32) {
+    __shared__ double sh[K][kThreads / 32];
+    const int nb = gridDim.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double s[K];
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            double s = 0.0;
-            for (int i = threadIdx.x; i < nb; i += 32) s += red[slot[k] * nb + i];
-            s = warp_sum(s);
-            if (threadIdx.x == 0) sh[k] = s;
-        }
+    for (int k = 0; k < K; ++k) s[k] = 0.0;
+    for (int i = threadIdx.x; i < nb; i += kThreads)
+#pragma unroll
+        for (int k = 0; k < K; ++k) s[k] += __ldcg(red + slot[k] * nb + i);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        s[k] = warp_sum(s[k]);
+        if (lane == 0) sh[k][w] = s[k];
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < K; ++k) out[k] = sh[k];
+    for (int k = 0; k < K; ++k) {
+        double t = 0.0;
+#pragma unroll
+        for (int i = 0; i < kThreads / 32; ++i) t += sh[k][i];
+        out[k] = t;
+    }
     __syncthreads();
 }
-
 
 // ---------------------------------------------------------------------------
 // Single system, three grid barriers per iteration.
@@ -549,20 +557,24 @@ __device__ __forceinline__ void bpartials(BShared &S, const gd::BatchKrylov &L, 
     __syncthreads();
 }
 
-// totals of the block's specimens (after a grid barrier) -> S.tot[k][j]
+// totals of the block's specimens (after a grid barrier) -> S.tot[k][j]: one warp
+// per (slot, specimen) pair loads that specimen's block partials in parallel (a
+// large specimen spans many blocks) and reduces them in a fixed pattern
 __device__ __forceinline__ void btotals(BShared &S, const gd::BatchKrylov &L, int fs, int ns, int slot0, int slot1)
 {
-    const int nb = gridDim.x;
-    for (int t = threadIdx.x; t < kBSlots * ns; t += blockDim.x) {
+    const int nb = gridDim.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int t = w; t < kBSlots * ns; t += kWarpsPB) {
         const int k = t / ns, j = t - k * ns;
         const int slot = k == 0 ? slot0 : slot1;
         double s = 0.0;
         if (slot >= 0) {
             const int sp = fs + j;
-            for (int bb = L.spec_b0[sp]; bb <= L.spec_b1[sp]; ++bb)
-                s += L.red[((size_t)slot * nb + bb) * L.J + (sp - L.blk_fs[bb])];
+            const int b0 = L.spec_b0[sp], b1 = L.spec_b1[sp];
+            for (int bb = b0 + lane; bb <= b1; bb += 32)
+                s += __ldcg(L.red + ((size_t)slot * nb + bb) * L.J + (sp - L.blk_fs[bb]));
         }
-        S.tot[k][j] = s;
+        s = warp_sum(s);
+        if (lane == 0) S.tot[k][j] = s;
     }
     __syncthreads();
 }

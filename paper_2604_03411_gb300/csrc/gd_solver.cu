@@ -70,10 +70,10 @@ __device__ __forceinline__ double sum_partials(const double *red, int slot, int 
 }
 
 // plain y = A x (free_only: prescribed rows y = x, prescribed columns skipped)
-template <int NDOF>
+template <int NDOF, class V>
 __global__ void __launch_bounds__(kThreads) spmv_plain_kernel(int64_t n_nodes, const int32_t *__restrict__ rowptr,
                                                               const int32_t *__restrict__ colidx,
-                                                              const double *__restrict__ vals,
+                                                              const V *__restrict__ vals,
                                                               const uint8_t *__restrict__ fixed,
                                                               const double *__restrict__ x, double *__restrict__ y,
                                                               int free_only)
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kThreads) spmv_plain_kernel(int64_t n_nodes, c
             const int32_t c = colidx[base + j];
             const double xv = (free_only && fixed[c]) ? 0.0 : x[c];
 #pragma unroll
-            for (int i = 0; i < NDOF; ++i) acc[i] += vals[base + (int64_t)i * len + j] * xv;
+            for (int i = 0; i < NDOF; ++i) acc[i] += (double)vals[base + (int64_t)i * len + j] * xv;
         }
 #pragma unroll
         for (int i = 0; i < NDOF; ++i) acc[i] = warp_sum(acc[i]);
@@ -313,11 +313,18 @@ cudaError_t launch_spmv(const SolverCtx &c, const double *x, double *y, int free
 {
     count(c);
     if (c.ndof == 3)
-        spmv_plain_kernel<3><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals, c.fixed, x,
-                                                                 y, free_only);
+        if (c.vals32)
+            spmv_plain_kernel<3, float><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals32,
+                                                                            c.fixed, x, y, free_only);
+        else
+            spmv_plain_kernel<3, double><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals,
+                                                                             c.fixed, x, y, free_only);
+    else if (c.vals32)
+        spmv_plain_kernel<4, float><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals32,
+                                                                        c.fixed, x, y, free_only);
     else
-        spmv_plain_kernel<4><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals, c.fixed, x,
-                                                                 y, free_only);
+        spmv_plain_kernel<4, double><<<c.blocks, kThreads, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, c.vals,
+                                                                         c.fixed, x, y, free_only);
     return cudaGetLastError();
 }
 
