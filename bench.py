@@ -278,9 +278,12 @@ def run_gd(args):
         step(k)
     # launch shapes from the library's own timings at the warmed-up state
     tune = B.gd_autotune(h)
+    saved = B.gd_get_state(h)        # the end-to-end leg repeats the timed steps from here
     tuning = {"asm_warps": tune.asm_warps, "krylov_ctas_per_sm": tune.krylov_ctas_per_sm,
               "asm_ms_by_warps": dict(zip(("2", "4", "8"), [round(x, 4) for x in tune.asm_ms])),
-              "krylov_us_by_ctas_per_sm": dict(zip(("1", "2", "3", "4"), [round(x, 3) for x in tune.krylov_us]))}
+              "krylov_us_by_ctas_per_sm": dict(zip(("1", "2", "3", "4"), [round(x, 3) for x in tune.krylov_us])),
+              "krylov_node_groups_per_lane": tune.krylov_up,
+              "krylov_us_by_node_groups": dict(zip(("1", "2", "4"), [round(x, 3) for x in tune.krylov_us_up]))}
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -379,12 +382,12 @@ def run_gd(args):
                 "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "avg_launch_ms": asm_avg,
                 "algorithmic_flops_per_launch": flops / max(asm, 1)}
 
-    # --- end to end through the C ABI with host buffers: each step uploads the
-    # committed state (dofs, the previous step's dofs for the predictor, kappa) from
-    # pinned host memory and reads the new state back ---
-    d_np, dp_np, k_np, nxt = B.gd_get_state(h)
-    if nxt >= n_path - args.steps:
-        nxt = 1
+    # --- end to end through the C ABI with host buffers, over the same load steps as
+    # the device-timed loop: each step uploads the committed state (dofs, the previous
+    # step's dofs for the predictor, kappa) from pinned host memory and reads the new
+    # state back ---
+    d_np, dp_np, k_np, nxt = saved
+    if nxt == 0 or nxt + args.steps > n_path:      # no history to restart from: begin after step 0
         B.gd_set_state(h, np.zeros_like(d_np), np.zeros_like(k_np), 0)
         B.gd_newton_step(h)
         d_np, dp_np, k_np, nxt = B.gd_get_state(h)

@@ -303,6 +303,8 @@ typedef struct gd_tune_report {
                                     not fit in shared memory                                    */
     double krylov_us[4];         /* Krylov iteration time with 1..4 CTAs per SM; -1: not
                                     co-resident                                                 */
+    int32_t krylov_up;           /* node groups per lane in the Krylov products (1, 2 or 4)     */
+    double krylov_us_up[3];      /* iteration time with 1, 2, 4 node groups at the chosen grid  */
 } gd_tune_report;
 
 /* Times the element kernel (one tangent pass at the committed state) for each CTA

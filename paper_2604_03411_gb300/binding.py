@@ -80,7 +80,8 @@ class GdPathReport(ctypes.Structure):
 
 class GdTuneReport(ctypes.Structure):
     _fields_ = [("asm_warps", ctypes.c_int32), ("krylov_ctas_per_sm", ctypes.c_int32),
-                ("asm_ms", ctypes.c_double * 3), ("krylov_us", ctypes.c_double * 4)]
+                ("asm_ms", ctypes.c_double * 3), ("krylov_us", ctypes.c_double * 4),
+                ("krylov_up", ctypes.c_int32), ("krylov_us_up", ctypes.c_double * 3)]
 
 
 _H = ctypes.c_void_p

@@ -240,6 +240,7 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
     kc.stream = H.stream;
     kc.blocks = H.krylov_grid;
     kc.num_sms = H.num_sms;
+    kc.up = H.krylov_up;
     GD_CUDA(&H, cudaEventRecord(H.kv0, H.stream));
     bool fp32_vals = H.opt.precision == GD_MIXED;
     if (inner_fp32 && !fp32_vals) {
@@ -340,6 +341,39 @@ gd_status solve_direction(gd::Handle &H, const double *rhs, double *delta, doubl
 
 gd_status norms_batch(gd::Handle &H, const double *R, std::vector<double> &nf, std::vector<double> &nx);
 
+// FP64 solve whose TRUE relative residual ||b - K x|| / ||b|| (free dofs) reaches
+// rtol: the recursively updated BiCGStab residual drifts from the true one by
+// rounding, so the true residual is formed after each solve and corrected by
+// further solves (at most four).  vals are FP64 values on the handle's pattern.
+gd_status krylov_true(gd::Handle &H, const double *vals, const double *b, double *x, double rtol)
+{
+    gd::SolverCtx c = solver_ctx(H, vals);
+    double *res = H.R_trial, *dx = H.kv[8], *y = H.diag;
+    int kit = 0;
+    double rel = 0.0;
+    gd_status st = krylov(H, vals, b, x, kit, rel, rtol, false, std::max(rtol, 1e-10));
+    if (st) return st;
+    double bn = 0.0;
+    GD_CUDA(&H, gd::launch_norm2_free(c, b, H.scal + 30, nullptr));
+    GD_CUDA(&H, cudaMemcpyAsync(&bn, H.scal + 30, sizeof(double), cudaMemcpyDeviceToHost, H.stream));
+    GD_CUDA(&H, cudaStreamSynchronize(H.stream));
+    if (bn == 0.0) return GD_OK;
+    for (int pass = 0; pass < 4; ++pass) {
+        GD_CUDA(&H, gd::launch_spmv(c, x, y, 1));
+        GD_CUDA(&H, gd::launch_residual(c, b, y, res, H.scal + 31));
+        H.launches += 1;
+        double rn = 0.0;
+        GD_CUDA(&H, cudaMemcpyAsync(&rn, H.scal + 31, sizeof(double), cudaMemcpyDeviceToHost, H.stream));
+        GD_CUDA(&H, cudaStreamSynchronize(H.stream));
+        if (!std::isfinite(rn)) return fail(&H, GD_ERR_NAN, "non-finite residual in a refined solve");
+        if (rn <= std::max(rtol, 1e-15) * bn) return GD_OK;
+        st = krylov(H, vals, res, dx, kit, rel, std::max(rtol * bn / rn, 1e-13), false, 0.5);
+        if (st) return st;
+        GD_CUDA(&H, gd::launch_axpy_free(c, x, dx, 1.0));
+    }
+    return GD_OK;       // best effort: the last correction was applied
+}
+
 // Per-specimen BiCGStab on the batch system: specimen s stops at ||r_s|| <=
 // eta[s] ||b_s||.  iters = the largest count over the specimens.
 gd_status krylov_batch(gd::Handle &H, const std::vector<double> &eta, const double *b, double *x, int &iters,
@@ -360,6 +394,7 @@ gd_status krylov_batch(gd::Handle &H, const std::vector<double> &eta, const doub
     kc.stream = H.stream;
     kc.blocks = H.krylov_grid;
     kc.num_sms = H.num_sms;
+    kc.up = H.krylov_up;
     const int S = H.n_spec;
     GD_CUDA(&H, cudaMemcpyAsync((void *)H.bk.rtol, eta.data(), sizeof(double) * S, cudaMemcpyHostToDevice, H.stream));
     GD_CUDA(&H, cudaEventRecord(H.kv0, H.stream));
@@ -1584,12 +1619,35 @@ gd_status gd_autotune(gd_handle *h, gd_tune_report *rep)
             kpick = cap;
         }
     }
-    std::swap(H.vals, H.vals_trial);
-    H.opt.krylov_max = keep_max;
     H.krylov_cpsm = kpick;
     H.krylov_grid = gd::krylov_blocks(H.ndof, H.opt.precision == GD_MIXED, H.num_sms, kpick);
     if (H.krylov_grid < 1) H.krylov_grid = keep_grid;
     r.krylov_ctas_per_sm = kpick;
+    // node groups per product round at the chosen grid
+    const int ups[3] = {1, 2, 4};
+    double ubest = 1e300;
+    int upick = H.krylov_up;
+    for (int ui = 0; ui < 3 && st == GD_OK; ++ui) {
+        H.krylov_up = ups[ui];
+        double tmin = 1e300;
+        for (int rep_i = 0; rep_i < 2; ++rep_i) {
+            int kit = 0;
+            double rel = 0.0;
+            const double k0 = H.krylov_ms;
+            st = krylov(H, H.vals, H.kv[9], H.kv[8], kit, rel, 1e-300, fp32, 1e300);
+            if (st) break;
+            if (rep_i > 0 && kit > 0) tmin = std::min(tmin, (H.krylov_ms - k0) * 1e3 / kit);
+        }
+        r.krylov_us_up[ui] = st ? -1.0 : tmin;
+        if (!st && tmin < ubest) {
+            ubest = tmin;
+            upick = ups[ui];
+        }
+    }
+    H.krylov_up = upick;
+    r.krylov_up = upick ? upick : (fp32 ? 4 : 2);
+    std::swap(H.vals, H.vals_trial);
+    H.opt.krylov_max = keep_max;
     if (st) return st;
     if (H.n_spec > 1 && (st = build_batch_krylov(H))) return st;
     if (rep) *rep = r;
@@ -1835,12 +1893,8 @@ gd_status gd_backward(gd_handle *h, const double *dL_dreaction, double *dL_dthet
             gd::SolverCtx cT = solver_ctx(H, H.vals_T);
             if (fbar != 0.0) GD_CUDA(&H, gd::launch_spmv(cT, er, y, 0));
             GD_CUDA(&H, gd::launch_adj_rhs(H.n_dofs, S, fbar != 0.0 ? y : nullptr, fbar, H.fixed, rhs, H.stream));
-            // K^T lambda = rhs on the free dofs (FP64)
-            int kit = 0;
-            double rel = 0.0;
-            if ((st = krylov(H, H.vals_T, rhs, lam, kit, rel, H.opt.krylov_rtol, false,
-                             std::max(H.opt.krylov_rtol, 1e-10))))
-                break;
+            // K^T lambda = rhs on the free dofs (FP64, refined against the true residual)
+            if ((st = krylov_true(H, H.vals_T, rhs, lam, H.opt.krylov_rtol))) break;
             GD_CUDA(&H, gd::launch_axpby(H.n_dofs, w, lam, fbar, er, H.stream));
             A.mode = 1;
             A.w = w;

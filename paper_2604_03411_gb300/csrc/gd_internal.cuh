@@ -191,6 +191,7 @@ struct Handle {
     // launch shapes (gd_autotune)
     AsmTune asm_tune;
     int krylov_cpsm = 2;
+    int krylov_up = 0;                                   // 0: the precision's default
     // timing
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, kv0 = nullptr, kv1 = nullptr;
     double assembly_ms = 0.0, krylov_ms = 0.0;
@@ -289,6 +290,7 @@ struct KrylovCtx {
     cudaStream_t stream;
     int blocks;                 // cooperative grid size (all blocks co-resident)
     int num_sms;
+    int up = 0;                 // node groups per product round: 1, 2 or 4 (0: 2 for FP64, 4 for FP32)
 };
 cudaError_t krylov_solve_batch(const KrylovCtx &c, const BatchKrylov &L, const void *vals, bool fp32_vals,
                                const double *b, double *x, int max_it, bool fp32_vectors);

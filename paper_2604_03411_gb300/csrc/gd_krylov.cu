@@ -104,6 +104,36 @@ __device__ __forceinline__ void totals(const double *red, const int (&slot)[K], 
     __syncthreads();
 }
 
+// Per-thread dot-product accumulator.  FP64 vectors: a plain FP64 sum.  FP32
+// vectors: each product is split exactly into its rounded value and rounding
+// error (a fused multiply-add gives the error), and both are added with a
+// compensated (two-sum) FP32 accumulation; the thread's sum is widened to FP64
+// once, and every sum across threads and blocks is FP64.  On this part FP64
+// arithmetic and conversions issue at a small fraction of the FP32 rate, and a
+// per-row FP64 product with two widenings made the FP32 solve FP64-bound.
+template <class T>
+struct DotAcc {
+    double s = 0.0;
+    __device__ __forceinline__ void add(T x, T y) { s += (double)x * (double)y; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x, float y)
+    {
+        // _rn intrinsics: the compiler must not fuse these into multiply-adds
+        const float p = __fmul_rn(x, y);
+        const float e = fmaf(x, y, -p);        // x y = p + e exactly
+        const float t = __fadd_rn(s, p);       // two-sum of s and p
+        const float bp = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // ---------------------------------------------------------------------------
 // Single system, three grid barriers per iteration.
 //
@@ -203,12 +233,12 @@ __device__ __forceinline__ T node_apply(const T *binv, int64_t nd, bool node_ok,
     return fixed ? T(0) : out;
 }
 
-template <int NDOF, int G, class V, class T>
+template <int NDOF, int G, int UP, class V, class T>
 __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
 {
     using M = RowMap<NDOF, G, T>;
     constexpr int LPN = M::LPN, NPW = M::NPW;
-    constexpr int UP = std::is_same<T, double>::value ? 2 : 4;   // node groups per product round
+    // UP: node groups per product round (a launch-shape choice of the autotuner)
     cg::grid_group grid = cg::this_grid();
     const int lane = threadIdx.x & 31;
     const int slot = lane / LPN, sub = lane - slot * LPN, nbase = slot * LPN;
@@ -228,7 +258,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
 
     // init: r = b (free), rh = r, p = r, v = q = x~ = 0, y = M^-1 r; <r, r>
     {
-        double rr = 0.0;
+        DotAcc<T> rr;
         for (int64_t ps = 0; ps < passes; ++ps) {
             const int64_t nd = (gw + ps * nw) * NPW + slot;
             const bool node_ok = slot < NPW && nd < n_nodes;
@@ -245,10 +275,10 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                 q[row] = T(0);
                 xt[row] = T(0);
                 wv[row] = yv;
-                rr += (double)bv * (double)bv;
+                rr.add(bv, bv);
             }
         }
-        double pv[2] = {rr, rr};
+        double pv[2] = {rr.value(), rr.value()};
         const int sl[2] = {S_RHO, S_RR};
         partials<2>(pv, A.red, sl);
     }
@@ -285,7 +315,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
         for (it = 0; it < A.max_it; ++it) {
             // phase 1
             {
-                double s1 = 0.0;
+                DotAcc<T> s1;
                 const T tb = (T)beta, tbo = (T)(beta * omega);
                 for (int64_t ps = 0; ps < passes; ++ps) {
                     const int64_t nd = (gw + ps * nw) * NPW + slot;
@@ -300,12 +330,12 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                         p[row] = r[row] + tb * p[row] - tbo * vo;
                         vn = u[row] + tb * vo - tbo * q[row];
                         v[row] = vn;
-                        s1 += (double)rh[row] * (double)vn;
+                        s1.add(rh[row], vn);
                     }
                     const T yv = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, vn, fx);
                     if (own) y[row] = yv;
                 }
-                double pv[1] = {s1};
+                double pv[1] = {s1.value()};
                 const int sl[1] = {S_SIG};
                 partials<1>(pv, A.red, sl);
             }
@@ -318,7 +348,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
             }
             // phase 2
             {
-                double ts = 0.0, tt = 0.0;
+                DotAcc<T> ts, tt;
                 const T ta = (T)alpha;
                 for (int64_t ps0 = 0; ps0 < passes; ps0 += UP) {
                     int64_t ndu[UP];
@@ -340,11 +370,11 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                             const T tv = u[row] - ta * qn;
                             r[row] = sv;
                             t[row] = tv;
-                            ts += (double)tv * (double)sv;
-                            tt += (double)tv * (double)tv;
+                            ts.add(tv, sv);
+                            tt.add(tv, tv);
                         }
                 }
-                double pv[2] = {ts, tt};
+                double pv[2] = {ts.value(), tt.value()};
                 const int sl[2] = {S_TS, S_TT};
                 partials<2>(pv, A.red, sl);
             }
@@ -357,7 +387,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
             }
             // phase 3
             {
-                double prr = 0.0, prhr = 0.0;
+                DotAcc<T> prr, prhr;
                 const T ta = (T)alpha, to = (T)omega;
                 for (int64_t ps = 0; ps < passes; ++ps) {
                     const int64_t nd = (gw + ps * nw) * NPW + slot;
@@ -372,13 +402,13 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                         xt[row] += ta * p[row] + to * sv;
                         rn = sv - to * t[row];
                         r[row] = rn;
-                        prhr += (double)rh[row] * (double)rn;
-                        prr += (double)rn * (double)rn;
+                        prhr.add(rh[row], rn);
+                        prr.add(rn, rn);
                     }
                     const T wn = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, rn, fx);
                     if (own) wv[row] = wn;
                 }
-                double pv[2] = {prhr, prr};
+                double pv[2] = {prhr.value(), prr.value()};
                 const int sl[2] = {S_RHO, S_RR};
                 partials<2>(pv, A.red, sl);
             }
@@ -481,29 +511,33 @@ struct BShared {
     int cnt;
 };
 
-// running per-specimen sums of one warp (j = block-local specimen, -1 = none)
+// running per-specimen sums of one warp (j = block-local specimen, -1 = none);
+// the increments of slot k are products x[k] y[k], accumulated as DotAcc<T>
+template <class T>
 struct WarpAcc {
-    double v[kBSlots];
-    int j;
+    DotAcc<T> v[kBSlots];
+    int j = -1;
 };
 
-__device__ __forceinline__ void wacc_flush(WarpAcc &a, BShared &S, int w, int lane)
+template <class T>
+__device__ __forceinline__ void wacc_flush(WarpAcc<T> &a, BShared &S, int w, int lane)
 {
     if (a.j >= 0) {
 #pragma unroll
         for (int k = 0; k < kBSlots; ++k) {
-            const double s = warp_sum(a.v[k]);
+            const double s = warp_sum(a.v[k].value());
             if (lane == 0) S.acc[w][k][a.j] += s;
         }
     }
     a.j = -1;
 #pragma unroll
-    for (int k = 0; k < kBSlots; ++k) a.v[k] = 0.0;
+    for (int k = 0; k < kBSlots; ++k) a.v[k] = DotAcc<T>();
 }
 
-// every lane of the warp calls this once per group (valid = the lane holds a value)
-__device__ __forceinline__ void wacc_add(WarpAcc &a, BShared &S, int w, int lane, bool valid, int j,
-                                         const double (&val)[kBSlots])
+// every lane of the warp calls this once per group (valid = the lane holds a row)
+template <class T>
+__device__ __forceinline__ void wacc_add(WarpAcc<T> &a, BShared &S, int w, int lane, bool valid, int j,
+                                         const T (&x)[kBSlots], const T (&y)[kBSlots])
 {
     const unsigned vm = __ballot_sync(0xffffffffu, valid);
     if (vm == 0u) return;
@@ -512,7 +546,7 @@ __device__ __forceinline__ void wacc_add(WarpAcc &a, BShared &S, int w, int lane
     if (uniform && j0 == a.j) {
         if (valid)
 #pragma unroll
-            for (int k = 0; k < kBSlots; ++k) a.v[k] += val[k];
+            for (int k = 0; k < kBSlots; ++k) a.v[k].add(x[k], y[k]);
         return;
     }
     wacc_flush(a, S, w, lane);
@@ -520,10 +554,11 @@ __device__ __forceinline__ void wacc_add(WarpAcc &a, BShared &S, int w, int lane
         a.j = j0;
         if (valid)
 #pragma unroll
-            for (int k = 0; k < kBSlots; ++k) a.v[k] = val[k];
+            for (int k = 0; k < kBSlots; ++k) a.v[k].add(x[k], y[k]);
         return;
     }
-    // the group straddles specimens: reduce each one separately
+    // the group straddles specimens: reduce each one separately (at most once per
+    // specimen boundary)
     int jmin = valid ? j : 1 << 30, jmax = valid ? j : -1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -533,7 +568,7 @@ __device__ __forceinline__ void wacc_add(WarpAcc &a, BShared &S, int w, int lane
     for (int jj = jmin; jj <= jmax; ++jj) {
 #pragma unroll
         for (int k = 0; k < kBSlots; ++k) {
-            const double s = warp_sum((valid && j == jj) ? val[k] : 0.0);
+            const double s = warp_sum((valid && j == jj) ? (double)x[k] * (double)y[k] : 0.0);
             if (lane == 0) S.acc[w][k][jj] += s;
         }
     }
@@ -582,12 +617,12 @@ __device__ __forceinline__ void btotals(BShared &S, const gd::BatchKrylov &L, in
 // The batch kernel: the three-barrier iteration of bicgstab3_kernel with every
 // scalar per specimen.  Block b owns nodes [n0, n1) = [b chunk, (b+1) chunk); its
 // warps take node groups of that range in the row mapping of RowMap.
-template <int NDOF, int G, class V, class T>
+template <int NDOF, int G, int UP, class V, class T>
 __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A, gd::BatchKrylov L)
 {
     using M = RowMap<NDOF, G, T>;
     constexpr int LPN = M::LPN, NPW = M::NPW;
-    constexpr int UP = std::is_same<T, double>::value ? 2 : 4;   // node groups per product round
+    // UP: node groups per product round (a launch-shape choice of the autotuner)
     cg::grid_group grid = cg::this_grid();
     __shared__ BShared S;
     const int b = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -620,9 +655,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
     };
     // init: r = b (free), rh = p = r, v = q = x~ = 0, y = M^-1 r; per-specimen ||b||^2
     {
-        WarpAcc acc;
-        acc.j = -1;
-        acc.v[0] = acc.v[1] = 0.0;
+        WarpAcc<T> acc;
         for (int64_t ps = 0; ps < passes; ++ps) {
             int64_t nd;
             bool node_ok;
@@ -633,7 +666,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
             const bool fx = own ? A.fixed[row] != 0 : true;
             const T bv = (own && !fx) ? (T)A.b[row] : T(0);
             const T yv = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, bv, fx);
-            double val[kBSlots] = {0.0, 0.0};
+            const T xa[kBSlots] = {bv, bv};
             if (own) {
                 r[row] = bv;
                 rh[row] = bv;
@@ -643,9 +676,8 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
                 // x~ may be the output itself (FP64): a skipped specimen keeps its x
                 if (L.rtol[fs + j] >= 0.0) xt[row] = T(0);
                 wv[row] = yv;
-                val[0] = val[1] = (double)bv * (double)bv;
             }
-            wacc_add(acc, S, w, lane, own, j, val);
+            wacc_add(acc, S, w, lane, own, j, xa, xa);
         }
         wacc_flush(acc, S, w, lane);
         bpartials(S, L, ns, BS_RHO, BS_RR);
@@ -687,9 +719,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
     for (it = 0; it < A.max_it; ++it) {
         // phase 1: p, v, y = M^-1 v, <rh, v>
         {
-            WarpAcc acc;
-            acc.j = -1;
-            acc.v[0] = acc.v[1] = 0.0;
+            WarpAcc<T> acc;
             for (int64_t ps = 0; ps < passes; ++ps) {
                 int64_t nd;
                 bool node_ok;
@@ -700,7 +730,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
                 const int64_t row = nd * NDOF + sub;
                 T vn = T(0);
                 bool fx = true;
-                double val[kBSlots] = {0.0, 0.0};
+                T xa[kBSlots] = {T(0), T(0)}, ya[kBSlots] = {T(0), T(0)};
                 if (own) {
                     const T tb = (T)S.rho_old[j], tbo = (T)(S.rho_old[j] * S.omega[j]);
                     fx = A.fixed[row] != 0;
@@ -708,11 +738,12 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
                     p[row] = r[row] + tb * p[row] - tbo * vo;
                     vn = u[row] + tb * vo - tbo * q[row];
                     v[row] = vn;
-                    val[0] = (double)rh[row] * (double)vn;
+                    xa[0] = rh[row];
+                    ya[0] = vn;
                 }
                 const T yv = node_apply<NDOF, T>(A.binv, nd, on, sub, nbase, vn, fx);
                 if (own) y[row] = yv;
-                wacc_add(acc, S, w, lane, own, j, val);
+                wacc_add(acc, S, w, lane, own, j, xa, ya);
             }
             wacc_flush(acc, S, w, lane);
             bpartials(S, L, ns, BS_RHV, -1);
@@ -729,9 +760,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
         __syncthreads();
         // phase 2: q = A y, s = r - alpha v, t = u - alpha q, <t, s>, <t, t>
         {
-            WarpAcc acc;
-            acc.j = -1;
-            acc.v[0] = acc.v[1] = 0.0;
+            WarpAcc<T> acc;
             for (int64_t ps0 = 0; ps0 < passes; ps0 += UP) {
                 int64_t ndu[UP];
                 bool oku[UP];
@@ -748,7 +777,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
                 for (int k = 0; k < UP; ++k) {
                     const bool own = oku[k] && sub < NDOF;
                     const int j = ju[k];
-                    double val[kBSlots] = {0.0, 0.0};
+                    T xa[kBSlots] = {T(0), T(0)}, ya[kBSlots] = {T(0), T(0)};
                     if (own) {
                         const int64_t row = ndu[k] * NDOF + sub;
                         const T ta = (T)S.alpha[j];
@@ -758,10 +787,12 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
                         const T tv = u[row] - ta * qn;
                         r[row] = sv;
                         t[row] = tv;
-                        val[0] = (double)tv * (double)sv;
-                        val[1] = (double)tv * (double)tv;
+                        xa[0] = tv;
+                        ya[0] = sv;
+                        xa[1] = tv;
+                        ya[1] = tv;
                     }
-                    wacc_add(acc, S, w, lane, own, j, val);
+                    wacc_add(acc, S, w, lane, own, j, xa, ya);
                 }
             }
             wacc_flush(acc, S, w, lane);
@@ -774,9 +805,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
         __syncthreads();
         // phase 3: x~ += alpha p + omega s, r = s - omega t, y = M^-1 r, <rh, r>, <r, r>
         {
-            WarpAcc acc;
-            acc.j = -1;
-            acc.v[0] = acc.v[1] = 0.0;
+            WarpAcc<T> acc;
             for (int64_t ps = 0; ps < passes; ++ps) {
                 int64_t nd;
                 bool node_ok;
@@ -787,7 +816,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
                 const int64_t row = nd * NDOF + sub;
                 T rn = T(0);
                 bool fx = true;
-                double val[kBSlots] = {0.0, 0.0};
+                T xa[kBSlots] = {T(0), T(0)}, ya[kBSlots] = {T(0), T(0)};
                 if (own) {
                     const T ta = (T)S.alpha[j], to = (T)S.omega[j];
                     fx = A.fixed[row] != 0;
@@ -795,12 +824,14 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
                     xt[row] += ta * p[row] + to * sv;
                     rn = sv - to * t[row];
                     r[row] = rn;
-                    val[0] = (double)rh[row] * (double)rn;
-                    val[1] = (double)rn * (double)rn;
+                    xa[0] = rh[row];
+                    ya[0] = rn;
+                    xa[1] = rn;
+                    ya[1] = rn;
                 }
                 const T wn = node_apply<NDOF, T>(A.binv, nd, on, sub, nbase, rn, fx);
                 if (own) wv[row] = wn;
-                wacc_add(acc, S, w, lane, own, j, val);
+                wacc_add(acc, S, w, lane, own, j, xa, ya);
             }
             wacc_flush(acc, S, w, lane);
             bpartials(S, L, ns, BS_RHO, BS_RR);
@@ -991,8 +1022,11 @@ cudaError_t solve_t(const KrylovCtx &c, const V *vals, const double *b, double *
     A.rtol = rtol;
     A.max_it = max_it;
     void *args[] = {&A};
-    return cudaLaunchCooperativeKernel((void *)bicgstab3_kernel<NDOF, G, V, T>, dim3(c.blocks), dim3(kThreads), args,
-                                       0, c.stream);
+    const int up = c.up ? c.up : (std::is_same<T, double>::value ? 2 : 4);
+    const void *fn = up == 1   ? (const void *)bicgstab3_kernel<NDOF, G, 1, V, T>
+                     : up == 4 ? (const void *)bicgstab3_kernel<NDOF, G, 4, V, T>
+                               : (const void *)bicgstab3_kernel<NDOF, G, 2, V, T>;
+    return cudaLaunchCooperativeKernel(fn, dim3(c.blocks), dim3(kThreads), args, 0, c.stream);
 }
 
 template <int NDOF, class V, class T>
@@ -1035,23 +1069,32 @@ cudaError_t solve_batch_t(const KrylovCtx &c, const gd::BatchKrylov &L, const V 
     A.max_it = max_it;
     gd::BatchKrylov Lc = L;
     void *args[] = {&A, &Lc};
-    return cudaLaunchCooperativeKernel((void *)bicgstab3_batch_kernel<NDOF, G, V, T>, dim3(c.blocks), dim3(kThreads),
+    const int up = c.up ? c.up : (std::is_same<T, double>::value ? 2 : 4);
+    const void *fn = up == 1   ? (const void *)bicgstab3_batch_kernel<NDOF, G, 1, V, T>
+                     : up == 4 ? (const void *)bicgstab3_batch_kernel<NDOF, G, 4, V, T>
+                               : (const void *)bicgstab3_batch_kernel<NDOF, G, 2, V, T>;
+    return cudaLaunchCooperativeKernel(fn, dim3(c.blocks), dim3(kThreads),
                                        args, 0, c.stream);
 }
 
 // co-resident CTAs per SM of the solve kernels of one variant
+// co-resident CTAs per SM of the solve kernels of one variant (every UP)
 template <int NDOF, class V, class T>
 int coop_per_sm()
 {
     constexpr int G = NDOF == 3 ? 8 : 32;
-    int per_sm = 0, per_sm_b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bicgstab3_kernel<NDOF, G, V, T>, kThreads, 0) !=
-        cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, bicgstab3_batch_kernel<NDOF, G, V, T>, kThreads, 0) !=
-        cudaSuccess)
-        return 0;
-    return per_sm_b < per_sm ? per_sm_b : per_sm;
+    const void *fns[6] = {(const void *)bicgstab3_kernel<NDOF, G, 1, V, T>, (const void *)bicgstab3_kernel<NDOF, G, 2, V, T>,
+                          (const void *)bicgstab3_kernel<NDOF, G, 4, V, T>,
+                          (const void *)bicgstab3_batch_kernel<NDOF, G, 1, V, T>,
+                          (const void *)bicgstab3_batch_kernel<NDOF, G, 2, V, T>,
+                          (const void *)bicgstab3_batch_kernel<NDOF, G, 4, V, T>};
+    int best = 1 << 30;
+    for (const void *f : fns) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kThreads, 0) != cudaSuccess) return 0;
+        if (per_sm < best) best = per_sm;
+    }
+    return best;
 }
 
 __global__ void narrow_kernel(const double *in, float *out, int64_t n)

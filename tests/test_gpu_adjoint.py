@@ -71,10 +71,7 @@ def test_adjoint_vs_central_differences(env, energy):
     idx = np.concatenate([rng.choice(n_psi, 12, replace=False), n_psi + rng.choice(theta0.size - n_psi, 8, replace=False)])
     fd = []
     for i in idx:
-        # a small step keeps both evaluations on the same side of any point where a
-        # quadrature point switches between loading and unloading (the path is only
-        # piecewise smooth in theta)
-        step = 2e-5 * max(abs(theta0[i]), 1e-1)
+        step = 1e-4 * max(abs(theta0[i]), 1e-1)
         tp = theta0.copy(); tp[i] += step
         tm = theta0.copy(); tm[i] -= step
         Lp = gpu_loss(B, prob, tp, target)[0]
