@@ -1645,7 +1645,7 @@ gd_status gd_autotune(gd_handle *h, gd_tune_report *rep)
         }
     }
     H.krylov_up = upick;
-    r.krylov_up = upick ? upick : (fp32 ? 4 : 2);
+    r.krylov_up = upick ? upick : 1;
     std::swap(H.vals, H.vals_trial);
     H.opt.krylov_max = keep_max;
     if (st) return st;

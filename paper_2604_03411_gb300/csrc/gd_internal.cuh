@@ -290,7 +290,7 @@ struct KrylovCtx {
     cudaStream_t stream;
     int blocks;                 // cooperative grid size (all blocks co-resident)
     int num_sms;
-    int up = 0;                 // node groups per product round: 1, 2 or 4 (0: 2 for FP64, 4 for FP32)
+    int up = 0;                 // node groups per product round: 1, 2 or 4 (0: 1)
 };
 cudaError_t krylov_solve_batch(const KrylovCtx &c, const BatchKrylov &L, const void *vals, bool fp32_vals,
                                const double *b, double *x, int max_it, bool fp32_vectors);

@@ -168,7 +168,7 @@ struct RowMap {
 // dependent loads (row pointer, column index, x) instead of U of them in turn.
 // The product phases are bound by that latency, not by bandwidth or arithmetic.
 template <int NDOF, int LPN, int U, class V, class T>
-__device__ __forceinline__ void row_products(const KArgs<V, T> &A, const int64_t (&nd)[U], const bool (&ok)[U],
+__device__ __forceinline__ void row_products(const KArgs<V, T> &A, const int32_t (&nd)[U], const bool (&ok)[U],
                                              int sub, const T *x, T (&out)[U])
 {
     int32_t base[U], len[U];
@@ -187,7 +187,7 @@ __device__ __forceinline__ void row_products(const KArgs<V, T> &A, const int64_t
 #pragma unroll
             for (int u = 0; u < U; ++u)
                 if (j < len[u])
-                    out[u] += (T)A.vals[base[u] + (int64_t)sub * len[u] + j] * x[A.colidx[base[u] + j]];
+                    out[u] += (T)A.vals[base[u] + sub * len[u] + j] * x[A.colidx[base[u] + j]];
         }
     } else {
         T acc[U][NDOF];
@@ -202,7 +202,7 @@ __device__ __forceinline__ void row_products(const KArgs<V, T> &A, const int64_t
                 if (j < len[u]) {
                     const T xv = x[A.colidx[base[u] + j]];
 #pragma unroll
-                    for (int i = 0; i < NDOF; ++i) acc[u][i] += (T)A.vals[base[u] + (int64_t)i * len[u] + j] * xv;
+                    for (int i = 0; i < NDOF; ++i) acc[u][i] += (T)A.vals[base[u] + i * len[u] + j] * xv;
                 }
         }
 #pragma unroll
@@ -222,13 +222,13 @@ __device__ __forceinline__ void row_products(const KArgs<V, T> &A, const int64_t
 
 // row sub of M^-1 w for the node whose NDOF row values sit in lanes base..base+NDOF-1
 template <int NDOF, class T>
-__device__ __forceinline__ T node_apply(const T *binv, int64_t nd, bool node_ok, int sub, int base, T w, bool fixed)
+__device__ __forceinline__ T node_apply(const T *binv, int64_t nd_wide, bool node_ok, int sub, int base, T w, bool fixed)
 {
     T out = T(0);
 #pragma unroll
     for (int k = 0; k < NDOF; ++k) {
         const T wk = __shfl_sync(0xffffffffu, w, base + k);
-        if (node_ok && sub < NDOF) out += binv[(nd * NDOF + sub) * NDOF + k] * wk;
+        if (node_ok && sub < NDOF) out += binv[(nd_wide * NDOF + sub) * NDOF + k] * wk;
     }
     return fixed ? T(0) : out;
 }
@@ -242,10 +242,10 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
     cg::grid_group grid = cg::this_grid();
     const int lane = threadIdx.x & 31;
     const int slot = lane / LPN, sub = lane - slot * LPN, nbase = slot * LPN;
-    const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * kThreads) >> 5;
-    const int64_t n_nodes = A.n_nodes;
-    const int64_t passes = (n_nodes + nw * NPW - 1) / (nw * NPW);   // warp-uniform
+    const int32_t gw = (blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int32_t nw = (gridDim.x * kThreads) >> 5;
+    const int32_t n_nodes = (int32_t)A.n_nodes;
+    const int32_t passes = (n_nodes + nw * NPW - 1) / (nw * NPW);   // warp-uniform
     // vector roles: r (also s), rh, p, v, q, t, y = M^-1 v (read by phase 2's product),
     // w = M^-1 r (read by phase 4's product), u.  y and w must differ: phase 1 of the
     // next iteration writes y with no barrier after phase 4, whose product still reads
@@ -259,11 +259,11 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
     // init: r = b (free), rh = r, p = r, v = q = x~ = 0, y = M^-1 r; <r, r>
     {
         DotAcc<T> rr;
-        for (int64_t ps = 0; ps < passes; ++ps) {
-            const int64_t nd = (gw + ps * nw) * NPW + slot;
+        for (int32_t ps = 0; ps < passes; ++ps) {
+            const int32_t nd = (gw + ps * nw) * NPW + slot;
             const bool node_ok = slot < NPW && nd < n_nodes;
             const bool own = node_ok && sub < NDOF;
-            const int64_t row = nd * NDOF + sub;
+            const int32_t row = nd * NDOF + sub;
             const bool fx = own ? A.fixed[row] != 0 : true;
             const T bv = (own && !fx) ? (T)A.b[row] : T(0);
             const T yv = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, bv, fx);
@@ -295,8 +295,8 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
         if (!(bnorm == 0.0)) status = 2;
     } else {
         // u = A w
-        for (int64_t ps0 = 0; ps0 < passes; ps0 += UP) {
-            int64_t ndu[UP];
+        for (int32_t ps0 = 0; ps0 < passes; ps0 += UP) {
+            int32_t ndu[UP];
             bool oku[UP];
             T au[UP];
 #pragma unroll
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
 #pragma unroll
             for (int k = 0; k < UP; ++k)
                 if (oku[k] && sub < NDOF) {
-                    const int64_t row = ndu[k] * NDOF + sub;
+                    const int32_t row = ndu[k] * NDOF + sub;
                     u[row] = A.fixed[row] ? T(0) : au[k];
                 }
         }
@@ -317,11 +317,11 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
             {
                 DotAcc<T> s1;
                 const T tb = (T)beta, tbo = (T)(beta * omega);
-                for (int64_t ps = 0; ps < passes; ++ps) {
-                    const int64_t nd = (gw + ps * nw) * NPW + slot;
+                for (int32_t ps = 0; ps < passes; ++ps) {
+                    const int32_t nd = (gw + ps * nw) * NPW + slot;
                     const bool node_ok = slot < NPW && nd < n_nodes;
                     const bool own = node_ok && sub < NDOF;
-                    const int64_t row = nd * NDOF + sub;
+                    const int32_t row = nd * NDOF + sub;
                     T vn = T(0);
                     bool fx = true;
                     if (own) {
@@ -350,8 +350,8 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
             {
                 DotAcc<T> ts, tt;
                 const T ta = (T)alpha;
-                for (int64_t ps0 = 0; ps0 < passes; ps0 += UP) {
-                    int64_t ndu[UP];
+                for (int32_t ps0 = 0; ps0 < passes; ps0 += UP) {
+                    int32_t ndu[UP];
                     bool oku[UP];
                     T au[UP];
 #pragma unroll
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
 #pragma unroll
                     for (int k = 0; k < UP; ++k)
                         if (oku[k] && sub < NDOF) {
-                            const int64_t row = ndu[k] * NDOF + sub;
+                            const int32_t row = ndu[k] * NDOF + sub;
                             const T qn = A.fixed[row] ? T(0) : au[k];
                             q[row] = qn;
                             const T sv = r[row] - ta * v[row];
@@ -389,11 +389,11 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
             {
                 DotAcc<T> prr, prhr;
                 const T ta = (T)alpha, to = (T)omega;
-                for (int64_t ps = 0; ps < passes; ++ps) {
-                    const int64_t nd = (gw + ps * nw) * NPW + slot;
+                for (int32_t ps = 0; ps < passes; ++ps) {
+                    const int32_t nd = (gw + ps * nw) * NPW + slot;
                     const bool node_ok = slot < NPW && nd < n_nodes;
                     const bool own = node_ok && sub < NDOF;
-                    const int64_t row = nd * NDOF + sub;
+                    const int32_t row = nd * NDOF + sub;
                     T rn = T(0);
                     bool fx = true;
                     if (own) {
@@ -444,8 +444,8 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                 rho = t3[0];
             }
             // phase 4: u = A w (and rh = r on a restart)
-            for (int64_t ps0 = 0; ps0 < passes; ps0 += UP) {
-                int64_t ndu[UP];
+            for (int32_t ps0 = 0; ps0 < passes; ps0 += UP) {
+                int32_t ndu[UP];
                 bool oku[UP];
                 T au[UP];
 #pragma unroll
@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
 #pragma unroll
                 for (int k = 0; k < UP; ++k)
                     if (oku[k] && sub < NDOF) {
-                        const int64_t row = ndu[k] * NDOF + sub;
+                        const int32_t row = ndu[k] * NDOF + sub;
                         u[row] = A.fixed[row] ? T(0) : au[k];
                         if (restart) rh[row] = r[row];
                     }
@@ -466,11 +466,11 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
         if (it >= A.max_it && rel > A.rtol && status == 0) status = 3;
     }
     // x = M^-1 x~ (in place when x~ is the FP64 output)
-    for (int64_t ps = 0; ps < passes; ++ps) {
-        const int64_t nd = (gw + ps * nw) * NPW + slot;
+    for (int32_t ps = 0; ps < passes; ++ps) {
+        const int32_t nd = (gw + ps * nw) * NPW + slot;
         const bool node_ok = slot < NPW && nd < n_nodes;
         const bool own = node_ok && sub < NDOF;
-        const int64_t row = nd * NDOF + sub;
+        const int32_t row = nd * NDOF + sub;
         const bool fx = own ? A.fixed[row] != 0 : true;
         const T xv = own ? xt[row] : T(0);
         const T xo = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, xv, fx);
@@ -627,11 +627,11 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
     __shared__ BShared S;
     const int b = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int slot = lane / LPN, sub = lane - slot * LPN, nbase = slot * LPN;
-    const int64_t n0 = (int64_t)b * L.chunk;
-    const int64_t n1 = n0 + L.chunk < A.n_nodes ? n0 + L.chunk : A.n_nodes;
+    const int32_t n0 = b * (int32_t)L.chunk;
+    const int32_t n1 = n0 + (int32_t)L.chunk < (int32_t)A.n_nodes ? n0 + (int32_t)L.chunk : (int32_t)A.n_nodes;
     const int fs = n0 < n1 ? L.blk_fs[b] : 0;
     const int ns = n0 < n1 ? L.blk_ns[b] : 0;
-    const int64_t passes = (L.chunk + (int64_t)kWarpsPB * NPW - 1) / ((int64_t)kWarpsPB * NPW);   // grid-uniform
+    const int32_t passes = ((int32_t)L.chunk + kWarpsPB * NPW - 1) / (kWarpsPB * NPW);   // grid-uniform
     // y = M^-1 v and w = M^-1 r are separate for the reason given at bicgstab3_kernel
     T *r = A.r, *rh = A.rh, *p = A.p, *v = A.v, *q = A.s, *t = A.t, *y = A.y, *wv = A.w, *u = A.z, *xt = A.x;
     for (int i = threadIdx.x; i < kWarpsPB * kBSlots * kMaxSpecPerBlock; i += blockDim.x) (&S.acc[0][0][0])[i] = 0.0;
@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
     }
     __syncthreads();
     // node of this lane in pass ps, its block-local specimen (-1: none) and row ownership
-    auto node_of = [&](int64_t ps, int64_t &nd, bool &node_ok, int &j) {
+    auto node_of = [&](int32_t ps, int32_t &nd, bool &node_ok, int &j) {
         nd = n0 + (w + ps * kWarpsPB) * NPW + slot;
         node_ok = slot < NPW && nd < n1;
         j = node_ok ? L.node_spec[nd] - fs : -1;
@@ -656,13 +656,13 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
     // init: r = b (free), rh = p = r, v = q = x~ = 0, y = M^-1 r; per-specimen ||b||^2
     {
         WarpAcc<T> acc;
-        for (int64_t ps = 0; ps < passes; ++ps) {
-            int64_t nd;
+        for (int32_t ps = 0; ps < passes; ++ps) {
+            int32_t nd;
             bool node_ok;
             int j;
             node_of(ps, nd, node_ok, j);
             const bool own = node_ok && sub < NDOF;
-            const int64_t row = nd * NDOF + sub;
+            const int32_t row = nd * NDOF + sub;
             const bool fx = own ? A.fixed[row] != 0 : true;
             const T bv = (own && !fx) ? (T)A.b[row] : T(0);
             const T yv = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, bv, fx);
@@ -696,8 +696,8 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
     }
     __syncthreads();
     // u = A w
-    for (int64_t ps0 = 0; ps0 < passes; ps0 += UP) {
-        int64_t ndu[UP];
+    for (int32_t ps0 = 0; ps0 < passes; ps0 += UP) {
+        int32_t ndu[UP];
         bool oku[UP];
         T au[UP];
 #pragma unroll
@@ -711,7 +711,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
 #pragma unroll
         for (int k = 0; k < UP; ++k)
             if (oku[k] && sub < NDOF) {
-                const int64_t row = ndu[k] * NDOF + sub;
+                const int32_t row = ndu[k] * NDOF + sub;
                 u[row] = A.fixed[row] ? T(0) : au[k];
             }
     }
@@ -720,14 +720,14 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
         // phase 1: p, v, y = M^-1 v, <rh, v>
         {
             WarpAcc<T> acc;
-            for (int64_t ps = 0; ps < passes; ++ps) {
-                int64_t nd;
+            for (int32_t ps = 0; ps < passes; ++ps) {
+                int32_t nd;
                 bool node_ok;
                 int j;
                 node_of(ps, nd, node_ok, j);
                 const bool on = node_ok && S.act[j];
                 const bool own = on && sub < NDOF;
-                const int64_t row = nd * NDOF + sub;
+                const int32_t row = nd * NDOF + sub;
                 T vn = T(0);
                 bool fx = true;
                 T xa[kBSlots] = {T(0), T(0)}, ya[kBSlots] = {T(0), T(0)};
@@ -761,8 +761,8 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
         // phase 2: q = A y, s = r - alpha v, t = u - alpha q, <t, s>, <t, t>
         {
             WarpAcc<T> acc;
-            for (int64_t ps0 = 0; ps0 < passes; ps0 += UP) {
-                int64_t ndu[UP];
+            for (int32_t ps0 = 0; ps0 < passes; ps0 += UP) {
+                int32_t ndu[UP];
                 bool oku[UP];
                 int ju[UP];
                 T au[UP];
@@ -779,7 +779,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
                     const int j = ju[k];
                     T xa[kBSlots] = {T(0), T(0)}, ya[kBSlots] = {T(0), T(0)};
                     if (own) {
-                        const int64_t row = ndu[k] * NDOF + sub;
+                        const int32_t row = ndu[k] * NDOF + sub;
                         const T ta = (T)S.alpha[j];
                         const T qn = A.fixed[row] ? T(0) : au[k];
                         q[row] = qn;
@@ -806,14 +806,14 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
         // phase 3: x~ += alpha p + omega s, r = s - omega t, y = M^-1 r, <rh, r>, <r, r>
         {
             WarpAcc<T> acc;
-            for (int64_t ps = 0; ps < passes; ++ps) {
-                int64_t nd;
+            for (int32_t ps = 0; ps < passes; ++ps) {
+                int32_t nd;
                 bool node_ok;
                 int j;
                 node_of(ps, nd, node_ok, j);
                 const bool on = node_ok && S.act[j];
                 const bool own = on && sub < NDOF;
-                const int64_t row = nd * NDOF + sub;
+                const int32_t row = nd * NDOF + sub;
                 T rn = T(0);
                 bool fx = true;
                 T xa[kBSlots] = {T(0), T(0)}, ya[kBSlots] = {T(0), T(0)};
@@ -869,8 +869,8 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
         }
         __syncthreads();
         // phase 4: u = A w (and rh = r on a restart)
-        for (int64_t ps0 = 0; ps0 < passes; ps0 += UP) {
-            int64_t ndu[UP];
+        for (int32_t ps0 = 0; ps0 < passes; ps0 += UP) {
+            int32_t ndu[UP];
             bool oku[UP];
             int ju[UP];
             T au[UP];
@@ -884,7 +884,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
 #pragma unroll
             for (int k = 0; k < UP; ++k)
                 if (oku[k] && sub < NDOF) {
-                    const int64_t row = ndu[k] * NDOF + sub;
+                    const int32_t row = ndu[k] * NDOF + sub;
                     u[row] = A.fixed[row] ? T(0) : au[k];
                     if (S.st[ju[k]] == 4) rh[row] = r[row];
                 }
@@ -895,14 +895,14 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
         __syncthreads();
     }
     // x = M^-1 x~ (not for skipped specimens)
-    for (int64_t ps = 0; ps < passes; ++ps) {
-        int64_t nd;
+    for (int32_t ps = 0; ps < passes; ++ps) {
+        int32_t nd;
         bool node_ok;
         int j;
         node_of(ps, nd, node_ok, j);
         if (node_ok && S.keep[j]) node_ok = false;     // warp-uniform use below only through node_ok
         const bool own = node_ok && sub < NDOF;
-        const int64_t row = nd * NDOF + sub;
+        const int32_t row = nd * NDOF + sub;
         const bool fx = own ? A.fixed[row] != 0 : true;
         const T xv = own ? xt[row] : T(0);
         const T xo = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, xv, fx);
@@ -1022,7 +1022,7 @@ cudaError_t solve_t(const KrylovCtx &c, const V *vals, const double *b, double *
     A.rtol = rtol;
     A.max_it = max_it;
     void *args[] = {&A};
-    const int up = c.up ? c.up : (std::is_same<T, double>::value ? 2 : 4);
+    const int up = c.up ? c.up : 1;
     const void *fn = up == 1   ? (const void *)bicgstab3_kernel<NDOF, G, 1, V, T>
                      : up == 4 ? (const void *)bicgstab3_kernel<NDOF, G, 4, V, T>
                                : (const void *)bicgstab3_kernel<NDOF, G, 2, V, T>;
@@ -1069,7 +1069,7 @@ cudaError_t solve_batch_t(const KrylovCtx &c, const gd::BatchKrylov &L, const V 
     A.max_it = max_it;
     gd::BatchKrylov Lc = L;
     void *args[] = {&A, &Lc};
-    const int up = c.up ? c.up : (std::is_same<T, double>::value ? 2 : 4);
+    const int up = c.up ? c.up : 1;
     const void *fn = up == 1   ? (const void *)bicgstab3_batch_kernel<NDOF, G, 1, V, T>
                      : up == 4 ? (const void *)bicgstab3_batch_kernel<NDOF, G, 4, V, T>
                                : (const void *)bicgstab3_batch_kernel<NDOF, G, 2, V, T>;
