@@ -492,6 +492,32 @@ gd_status mixed_noise(gd::Handle &H, const double *R32, std::vector<double> &noi
     return norms_batch(H, diff, noise, nx);
 }
 
+// GD_MIXED noise level for the Newton test.  The FP32 rounding noise of the
+// residual scales with the force level, so it is measured by the FP64 pass of
+// mixed_noise on the first Newton solve (and after every restart of the state) and
+// every kNoiseEvery solves, and in between taken as the measured ratio to the
+// specimen's force scale ||R_fixed|| (||R|| at the first iterate when nothing is
+// prescribed).  The FP64 pass costs as much as several FP32 passes.
+constexpr int kNoiseEvery = 8;
+
+gd_status noise_estimate(gd::Handle &H, const double *R, const std::vector<double> &scale,
+                         std::vector<double> &noise)
+{
+    const int S = H.n_spec;
+    if (H.noise_age <= 0 || (int)H.noise_ratio.size() != S) {
+        gd_status st = mixed_noise(H, R, noise);
+        if (st) return st;
+        H.noise_ratio.assign(S, 0.0);
+        for (int s = 0; s < S; ++s) H.noise_ratio[s] = scale[s] > 0.0 ? noise[s] / scale[s] : 0.0;
+        H.noise_age = kNoiseEvery;
+        return GD_OK;
+    }
+    noise.assign(S, 0.0);
+    for (int s = 0; s < S; ++s) noise[s] = H.noise_ratio[s] * scale[s];
+    --H.noise_age;
+    return GD_OK;
+}
+
 // Newton iteration for one load value starting from H.w_dofs (already predicted,
 // prescribed dofs set).  On return H.w_dofs/H.R/H.kappa_trial hold the last iterate.
 gd_status newton(gd::Handle &H, gd_newton_report &rep)
@@ -509,7 +535,8 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
     double noise = 0.0;
     if (H.opt.precision == GD_MIXED) {
         std::vector<double> nz;
-        if ((st = mixed_noise(H, H.R, nz))) return st;
+        const std::vector<double> sc(1, nr.fixed_ > 0.0 ? nr.fixed_ : r0);
+        if ((st = noise_estimate(H, H.R, sc, nz))) return st;
         noise = nz[0];
     }
     const double ntol = std::max(std::max(H.opt.newton_rtol * r0, H.opt.newton_atol), 2.0 * noise);
@@ -628,7 +655,11 @@ gd_status newton_batch(gd::Handle &H, gd_newton_report &rep)
         return std::sqrt(t);
     };
     std::vector<double> noise(S, 0.0);
-    if (H.opt.precision == GD_MIXED && (st = mixed_noise(H, H.R, noise))) return st;
+    if (H.opt.precision == GD_MIXED) {
+        std::vector<double> sc(S);
+        for (int s = 0; s < S; ++s) sc[s] = nx[s] > 0.0 ? nx[s] : nf[s];
+        if ((st = noise_estimate(H, H.R, sc, noise))) return st;
+    }
     for (int s = 0; s < S; ++s) {
         r0[s] = std::max(nf[s], nx[s]);
         ntol[s] = std::max(std::max(H.opt.newton_rtol * r0[s], H.opt.newton_atol), 2.0 * noise[s]);
@@ -1565,6 +1596,7 @@ gd_status gd_autotune(gd_handle *h, gd_tune_report *rep)
     for (int wi = 0; wi < 3; ++wi) {
         H.asm_tune.warps = widths[wi];
         H.asm_tune.cta_per_sm = 0;
+        H.asm_tune.exact = true;
         double tmin = 1e300;
         bool ok = true;
         for (int rep_i = 0; rep_i < 3 && ok; ++rep_i) {
@@ -1583,6 +1615,7 @@ gd_status gd_autotune(gd_handle *h, gd_tune_report *rep)
             pick = H.asm_tune;
         }
     }
+    pick.exact = false;
     H.asm_tune = pick;
     r.asm_warps = pick.warps;
     // Krylov: a fixed number of iterations on that tangent per grid size
@@ -1752,6 +1785,7 @@ gd_status gd_set_state(gd_handle *h, const double *dofs, const double *dofs_prev
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));
     H.next_step = next_step;
     H.rec_on = false;
+    H.noise_age = 0;
     H.have_prev = dofs_prev != nullptr;
     H.load_prev = (double)next_step;
     H.load_prevprev = dofs_prev ? (double)(next_step - 1) : H.load_prev;

@@ -589,14 +589,26 @@ cudaError_t launch_kw(const AsmArgs &a, int num_sms, int cta_per_sm, cudaStream_
     return cudaGetLastError();
 }
 
+// the requested CTA width, or the widest narrower one whose shared memory fits (a
+// width tuned for one kernel may not fit another: the FP64 kernel needs twice the
+// FP32 kernel's scratch)
 template <int DIM>
 cudaError_t launch_dim(const AsmArgs &a, int num_sms, const AsmTune &t, cudaStream_t s)
 {
-    switch (t.warps) {
-    case 2: return launch_kw<DIM, 2>(a, num_sms, t.cta_per_sm, s);
-    case 8: return launch_kw<DIM, 8>(a, num_sms, t.cta_per_sm, s);
-    default: return launch_kw<DIM, 4>(a, num_sms, t.cta_per_sm, s);
+    if (t.exact) {
+        switch (t.warps) {
+        case 1: return launch_kw<DIM, 1>(a, num_sms, t.cta_per_sm, s);
+        case 2: return launch_kw<DIM, 2>(a, num_sms, t.cta_per_sm, s);
+        case 8: return launch_kw<DIM, 8>(a, num_sms, t.cta_per_sm, s);
+        default: return launch_kw<DIM, 4>(a, num_sms, t.cta_per_sm, s);
+        }
     }
+    cudaError_t e = cudaErrorInvalidConfiguration;
+    if (t.warps >= 8) e = launch_kw<DIM, 8>(a, num_sms, t.cta_per_sm, s);
+    if (e == cudaErrorInvalidConfiguration && t.warps >= 4) e = launch_kw<DIM, 4>(a, num_sms, t.cta_per_sm, s);
+    if (e == cudaErrorInvalidConfiguration && t.warps >= 2) e = launch_kw<DIM, 2>(a, num_sms, t.cta_per_sm, s);
+    if (e == cudaErrorInvalidConfiguration) e = launch_kw<DIM, 1>(a, num_sms, t.cta_per_sm, s);
+    return e;
 }
 
 }  // namespace

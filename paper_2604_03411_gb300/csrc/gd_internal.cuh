@@ -98,6 +98,7 @@ struct Checkpoint {
 struct AsmTune {
     int warps = 4;
     int cta_per_sm = 0;
+    bool exact = false;      // true: fail instead of falling back to a narrower CTA that fits
 };
 // Batched specimens: the Krylov grid's blocks take contiguous node chunks and
 // every specimen runs its own BiCGStab recurrences (own scalars, own stopping
@@ -191,6 +192,10 @@ struct Handle {
     // launch shapes (gd_autotune)
     AsmTune asm_tune;
     int krylov_cpsm = 2;
+    // GD_MIXED: measured FP32 residual noise per unit force scale, and load steps until
+    // it is measured again
+    std::vector<double> noise_ratio;
+    int noise_age = 0;
     int krylov_up = 0;                                   // 0: the precision's default
     // timing
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, kv0 = nullptr, kv1 = nullptr;
