@@ -241,6 +241,7 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
     kc.blocks = H.krylov_grid;
     kc.num_sms = H.num_sms;
     kc.up = H.krylov_up;
+    kc.lmax = 0;
     GD_CUDA(&H, cudaEventRecord(H.kv0, H.stream));
     bool fp32_vals = H.opt.precision == GD_MIXED;
     if (inner_fp32 && !fp32_vals) {
@@ -395,6 +396,7 @@ gd_status krylov_batch(gd::Handle &H, const std::vector<double> &eta, const doub
     kc.blocks = H.krylov_grid;
     kc.num_sms = H.num_sms;
     kc.up = H.krylov_up;
+    kc.lmax = 0;
     const int S = H.n_spec;
     GD_CUDA(&H, cudaMemcpyAsync((void *)H.bk.rtol, eta.data(), sizeof(double) * S, cudaMemcpyHostToDevice, H.stream));
     GD_CUDA(&H, cudaEventRecord(H.kv0, H.stream));
@@ -1299,6 +1301,8 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
     gd::Handle &H = hh->h;
     H.h_rowptr.swap(P.rowptr);
     H.h_colidx.swap(P.colidx);
+    for (size_t r = 0; r + 1 < H.h_rowptr.size(); ++r)
+        H.krylov_lmax = std::max(H.krylov_lmax, H.h_rowptr[r + 1] - H.h_rowptr[r]);
     H.dim = dim;
     H.nen = nen;
     H.nq = nen;

@@ -197,6 +197,7 @@ struct Handle {
     std::vector<double> noise_ratio;
     int noise_age = 0;
     int krylov_up = 0;                                   // 0: the precision's default
+    int krylov_lmax = 0;                                 // longest CSR row
     // timing
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, kv0 = nullptr, kv1 = nullptr;
     double assembly_ms = 0.0, krylov_ms = 0.0;
@@ -296,6 +297,7 @@ struct KrylovCtx {
     int blocks;                 // cooperative grid size (all blocks co-resident)
     int num_sms;
     int up = 0;                 // node groups per product round: 1, 2 or 4 (0: 1)
+    int lmax = 0;               // longest row (0: rows are not copied to shared memory)
 };
 cudaError_t krylov_solve_batch(const KrylovCtx &c, const BatchKrylov &L, const void *vals, bool fp32_vals,
                                const double *b, double *x, int max_it, bool fp32_vectors);

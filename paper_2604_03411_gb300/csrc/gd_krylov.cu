@@ -41,6 +41,10 @@ struct KArgs {
     double *out;              // [0] iterations, [1] final relative residual, [2] status
     double rtol;
     int max_it;
+    // shared-memory copy of the block's rows for the products (single-system kernel):
+    // 0 none, 1 column lists, 2 column lists and values; lmax = longest row
+    int cache;
+    int lmax;
 };
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -50,9 +54,19 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// block sum of K values -> red[slot_k * gridDim.x + blockIdx.x]
+// Grid-wide sums of the single-system kernel.  Each block reduces its threads'
+// values and adds the block sum into a global FP64 accumulator with one atomic
+// add; after the grid barrier every block reads the finished total, one load per
+// slot.  (Summing every block's partial in every block costs a round trip per
+// partial line and was measured at 3.6-5.6 us per reduction.)  All blocks read
+// the same total, so they take the same decisions; the order of the atomic adds,
+// and with it the last bits of a total, can differ from run to run.  Two
+// accumulators per slot alternate between iterations: block 0 clears the other
+// one when it reads the current one, which is safe because every block read the
+// other one two barriers earlier and the next adds into it come two barriers
+// later.  acc[2 slot + parity]; the launcher clears all of them before the launch.
 template <int K>
-__device__ __forceinline__ void partials(double (&v)[K], double *red, const int (&slot)[K])
+__device__ __forceinline__ void acc_add(double (&v)[K], double *acc, const int (&slot)[K], int par)
 {
     __shared__ double sh[K][kThreads / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -67,40 +81,26 @@ __device__ __forceinline__ void partials(double (&v)[K], double *red, const int 
         for (int k = 0; k < K; ++k) {
             double s = lane < kThreads / 32 ? sh[k][lane] : 0.0;
             s = warp_sum(s);
-            if (lane == 0) red[slot[k] * gridDim.x + blockIdx.x] = s;
+            if (lane == 0) atomicAdd(acc + 2 * slot[k] + par, s);
         }
     }
     __syncthreads();
 }
 
-// every block: sum of the partials of K slots in a fixed order.  All threads of the
-// block load the partials (one or two each: a single round of L2 latency; a loop
-// over them in one warp waits for nb/32 round trips in turn), then the block
-// reduces them in a fixed pattern, so every block obtains bit-identical totals.
 template <int K>
-__device__ __forceinline__ void totals(const double *red, const int (&slot)[K], double (&out)[K])
+__device__ __forceinline__ void acc_read(double *acc, const int (&slot)[K], int par, double (&out)[K])
 {
-    __shared__ double sh[K][kThreads / 32];
-    const int nb = gridDim.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double s[K];
+    __shared__ double sh[K];
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) s[k] = 0.0;
-    for (int i = threadIdx.x; i < nb; i += kThreads)
-#pragma unroll
-        for (int k = 0; k < K; ++k) s[k] += __ldcg(red + slot[k] * nb + i);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        s[k] = warp_sum(s[k]);
-        if (lane == 0) sh[k][w] = s[k];
+        for (int k = 0; k < K; ++k) {
+            sh[k] = __ldcg(acc + 2 * slot[k] + par);
+            if (blockIdx.x == 0) acc[2 * slot[k] + (par ^ 1)] = 0.0;
+        }
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double t = 0.0;
-#pragma unroll
-        for (int i = 0; i < kThreads / 32; ++i) t += sh[k][i];
-        out[k] = t;
-    }
+    for (int k = 0; k < K; ++k) out[k] = sh[k];
     __syncthreads();
 }
 
@@ -167,16 +167,25 @@ struct RowMap {
 // loads of the U rows are issued together, so a lane waits for one chain of
 // dependent loads (row pointer, column index, x) instead of U of them in turn.
 // The product phases are bound by that latency, not by bandwidth or arithmetic.
+// cs[u] (may be null): the node's shared-memory record, its row length then its
+// column indices; cv[u] (may be null): its values, row i at cv[u] + i lmax.  Without
+// them the row is read from the CSR arrays in global memory.
 template <int NDOF, int LPN, int U, class V, class T>
 __device__ __forceinline__ void row_products(const KArgs<V, T> &A, const int32_t (&nd)[U], const bool (&ok)[U],
-                                             int sub, const T *x, T (&out)[U])
+                                             int sub, const T *x, T (&out)[U], const int32_t *const (&cs)[U],
+                                             const V *const (&cv)[U])
 {
     int32_t base[U], len[U];
     int lmax = 0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        base[u] = ok[u] ? A.rowptr[nd[u] * NDOF] : 0;
-        len[u] = ok[u] ? A.rowptr[nd[u] * NDOF + 1] - base[u] : 0;
+        if (cs[u]) {
+            base[u] = (ok[u] && !cv[u]) ? A.rowptr[nd[u] * NDOF] : 0;
+            len[u] = ok[u] ? cs[u][0] : 0;
+        } else {
+            base[u] = ok[u] ? A.rowptr[nd[u] * NDOF] : 0;
+            len[u] = ok[u] ? A.rowptr[nd[u] * NDOF + 1] - base[u] : 0;
+        }
         lmax = len[u] > lmax ? len[u] : lmax;
     }
     if constexpr (LPN == NDOF) {
@@ -186,8 +195,11 @@ __device__ __forceinline__ void row_products(const KArgs<V, T> &A, const int32_t
         for (int j = 0; j < lmax; ++j) {
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (j < len[u])
-                    out[u] += (T)A.vals[base[u] + sub * len[u] + j] * x[A.colidx[base[u] + j]];
+                if (j < len[u]) {
+                    const int32_t col = cs[u] ? cs[u][1 + j] : A.colidx[base[u] + j];
+                    const V a = cv[u] ? cv[u][sub * A.lmax + j] : A.vals[base[u] + sub * len[u] + j];
+                    out[u] += (T)a * x[col];
+                }
         }
     } else {
         T acc[U][NDOF];
@@ -200,9 +212,10 @@ __device__ __forceinline__ void row_products(const KArgs<V, T> &A, const int32_t
 #pragma unroll
             for (int u = 0; u < U; ++u)
                 if (j < len[u]) {
-                    const T xv = x[A.colidx[base[u] + j]];
+                    const T xv = x[cs[u] ? cs[u][1 + j] : A.colidx[base[u] + j]];
 #pragma unroll
-                    for (int i = 0; i < NDOF; ++i) acc[u][i] += (T)A.vals[base[u] + i * len[u] + j] * xv;
+                    for (int i = 0; i < NDOF; ++i)
+                        acc[u][i] += (T)(cv[u] ? cv[u][i * A.lmax + j] : A.vals[base[u] + i * len[u] + j]) * xv;
                 }
         }
 #pragma unroll
@@ -251,9 +264,37 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
     // next iteration writes y with no barrier after phase 4, whose product still reads
     // other lanes' w
     T *r = A.r, *rh = A.rh, *p = A.p, *v = A.v, *q = A.s, *t = A.t, *y = A.y, *wv = A.w, *u = A.z, *xt = A.x;
-    // partial-sum slots: consecutive phases use different slots, so that a block
-    // writing the next phase's partials never overwrites ones another block is
-    // still summing after the barrier
+    // shared-memory rows (A.cache > 0): one record per (pass, warp of the block, node
+    // slot): [row length, column indices ...] with stride lmax + 1, then the values,
+    // NDOF x lmax per record; the launcher sizes the dynamic shared memory for
+    // passes x warps x NPW records
+    extern __shared__ __align__(16) unsigned char kdyn[];
+    const int wib = threadIdx.x >> 5;
+    const int32_t n_rec = passes * (kThreads / 32) * NPW;
+    int32_t *scol = reinterpret_cast<int32_t *>(kdyn);
+    V *sval = reinterpret_cast<V *>(kdyn + ((((size_t)n_rec * (A.lmax + 1) * sizeof(int32_t)) + 15) & ~(size_t)15));
+    auto rec_of = [&](int32_t ps) { return (ps * (kThreads / 32) + wib) * NPW + slot; };
+    if (A.cache > 0) {
+        for (int32_t ps = 0; ps < passes; ++ps) {
+            const int32_t nd = (gw + ps * nw) * NPW + slot;
+            if (slot < NPW && nd < n_nodes) {
+                const int32_t rec = rec_of(ps);
+                const int32_t base = A.rowptr[nd * NDOF];
+                const int32_t len = A.rowptr[nd * NDOF + 1] - base;
+                int32_t *cs = scol + (size_t)rec * (A.lmax + 1);
+                if (sub == 0) cs[0] = len;
+                for (int32_t j = sub; j < len; j += LPN) cs[1 + j] = A.colidx[base + j];
+                if (A.cache == 2) {
+                    V *cv = sval + (size_t)rec * NDOF * A.lmax;
+                    for (int i = 0; i < NDOF; ++i)
+                        for (int32_t j = sub; j < len; j += LPN) cv[i * A.lmax + j] = A.vals[base + i * len + j];
+                }
+            }
+        }
+        __syncwarp();       // each warp reads only its own records
+    }
+    // accumulator slots (two parities each, see acc_add); the initial <r, r> uses
+    // parity 1 of the slots that iteration 0's phase 3 fills in parity 0
     enum { S_RHO = 0, S_RR = 1, S_SIG = 2, S_TS = 3, S_TT = 4 };
 
     // init: r = b (free), rh = r, p = r, v = q = x~ = 0, y = M^-1 r; <r, r>
@@ -280,13 +321,13 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
         }
         double pv[2] = {rr.value(), rr.value()};
         const int sl[2] = {S_RHO, S_RR};
-        partials<2>(pv, A.red, sl);
+        acc_add<2>(pv, A.red, sl, 1);
     }
     grid.sync();
     double tot[2];
     {
         const int sl[2] = {S_RHO, S_RR};
-        totals<2>(A.red, sl, tot);
+        acc_read<2>(A.red, sl, 1, tot);
     }
     const double bnorm = sqrt(tot[1]);
     double rho = tot[0], alpha = 0.0, omega = 1.0, beta = 0.0, rel = 0.0;
@@ -304,7 +345,13 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                 ndu[k] = (gw + (ps0 + k) * nw) * NPW + slot;
                 oku[k] = ps0 + k < passes && slot < NPW && ndu[k] < n_nodes;
             }
-            row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, wv, au);
+            const int32_t *csu[UP];
+#pragma unroll
+            for (int k = 0; k < UP; ++k) csu[k] = A.cache > 0 ? scol + (size_t)rec_of(ps0 + k) * (A.lmax + 1) : nullptr;
+            const V *cvu[UP];
+#pragma unroll
+            for (int k = 0; k < UP; ++k) cvu[k] = A.cache == 2 ? sval + (size_t)rec_of(ps0 + k) * NDOF * A.lmax : nullptr;
+            row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, wv, au, csu, cvu);
 #pragma unroll
             for (int k = 0; k < UP; ++k)
                 if (oku[k] && sub < NDOF) {
@@ -337,13 +384,13 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                 }
                 double pv[1] = {s1.value()};
                 const int sl[1] = {S_SIG};
-                partials<1>(pv, A.red, sl);
+                acc_add<1>(pv, A.red, sl, it & 1);
             }
             grid.sync();
             {
                 double t1[1];
                 const int sl[1] = {S_SIG};
-                totals<1>(A.red, sl, t1);
+                acc_read<1>(A.red, sl, it & 1, t1);
                 alpha = t1[0] != 0.0 ? rho / t1[0] : 0.0;
             }
             // phase 2
@@ -359,7 +406,13 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                         ndu[k] = (gw + (ps0 + k) * nw) * NPW + slot;
                         oku[k] = ps0 + k < passes && slot < NPW && ndu[k] < n_nodes;
                     }
-                    row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, y, au);
+                    const int32_t *csu[UP];
+#pragma unroll
+            for (int k = 0; k < UP; ++k) csu[k] = A.cache > 0 ? scol + (size_t)rec_of(ps0 + k) * (A.lmax + 1) : nullptr;
+            const V *cvu[UP];
+#pragma unroll
+            for (int k = 0; k < UP; ++k) cvu[k] = A.cache == 2 ? sval + (size_t)rec_of(ps0 + k) * NDOF * A.lmax : nullptr;
+            row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, y, au, csu, cvu);
 #pragma unroll
                     for (int k = 0; k < UP; ++k)
                         if (oku[k] && sub < NDOF) {
@@ -376,13 +429,13 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                 }
                 double pv[2] = {ts.value(), tt.value()};
                 const int sl[2] = {S_TS, S_TT};
-                partials<2>(pv, A.red, sl);
+                acc_add<2>(pv, A.red, sl, it & 1);
             }
             grid.sync();
             {
                 double t2[2];
                 const int sl[2] = {S_TS, S_TT};
-                totals<2>(A.red, sl, t2);
+                acc_read<2>(A.red, sl, it & 1, t2);
                 omega = t2[1] != 0.0 ? t2[0] / t2[1] : 0.0;
             }
             // phase 3
@@ -410,13 +463,13 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                 }
                 double pv[2] = {prhr.value(), prr.value()};
                 const int sl[2] = {S_RHO, S_RR};
-                partials<2>(pv, A.red, sl);
+                acc_add<2>(pv, A.red, sl, it & 1);
             }
             grid.sync();
             double t3[2];
             {
                 const int sl[2] = {S_RHO, S_RR};
-                totals<2>(A.red, sl, t3);
+                acc_read<2>(A.red, sl, it & 1, t3);
             }
             rel = sqrt(t3[1]) / bnorm;
             if (!(rel == rel)) {
@@ -453,7 +506,13 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                     ndu[k] = (gw + (ps0 + k) * nw) * NPW + slot;
                     oku[k] = ps0 + k < passes && slot < NPW && ndu[k] < n_nodes;
                 }
-                row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, wv, au);
+                const int32_t *csu[UP];
+#pragma unroll
+            for (int k = 0; k < UP; ++k) csu[k] = A.cache > 0 ? scol + (size_t)rec_of(ps0 + k) * (A.lmax + 1) : nullptr;
+            const V *cvu[UP];
+#pragma unroll
+            for (int k = 0; k < UP; ++k) cvu[k] = A.cache == 2 ? sval + (size_t)rec_of(ps0 + k) * NDOF * A.lmax : nullptr;
+            row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, wv, au, csu, cvu);
 #pragma unroll
                 for (int k = 0; k < UP; ++k)
                     if (oku[k] && sub < NDOF) {
@@ -707,7 +766,11 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
             node_of(ps0 + k, ndu[k], nok, jk);
             oku[k] = ps0 + k < passes && nok && S.act[jk];
         }
-        row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, wv, au);
+        {
+            const int32_t *csu[UP] = {};
+            const V *cvu[UP] = {};
+            row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, wv, au, csu, cvu);
+        }
 #pragma unroll
         for (int k = 0; k < UP; ++k)
             if (oku[k] && sub < NDOF) {
@@ -772,7 +835,11 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
                     node_of(ps0 + k, ndu[k], nok, ju[k]);
                     oku[k] = ps0 + k < passes && nok && S.act[ju[k]];
                 }
-                row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, y, au);
+                {
+                    const int32_t *csu[UP] = {};
+                    const V *cvu[UP] = {};
+                    row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, y, au, csu, cvu);
+                }
 #pragma unroll
                 for (int k = 0; k < UP; ++k) {
                     const bool own = oku[k] && sub < NDOF;
@@ -880,7 +947,11 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_batch_kernel(KArgs<V, T> A
                 node_of(ps0 + k, ndu[k], nok, ju[k]);
                 oku[k] = ps0 + k < passes && nok && S.act[ju[k]];
             }
-            row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, wv, au);
+            {
+            const int32_t *csu[UP] = {};
+            const V *cvu[UP] = {};
+            row_products<NDOF, LPN, UP, V, T>(A, ndu, oku, sub, wv, au, csu, cvu);
+        }
 #pragma unroll
             for (int k = 0; k < UP; ++k)
                 if (oku[k] && sub < NDOF) {
@@ -1021,12 +1092,49 @@ cudaError_t solve_t(const KrylovCtx &c, const V *vals, const double *b, double *
     A.out = c.out;
     A.rtol = rtol;
     A.max_it = max_it;
+    A.cache = 0;
+    A.lmax = 0;
+    // the grid-wide accumulators (2 parities x 5 slots) start at zero
+    e = cudaMemsetAsync(c.red, 0, 10 * sizeof(double), c.stream);
+    if (e != cudaSuccess) return e;
     void *args[] = {&A};
     const int up = c.up ? c.up : 1;
     const void *fn = up == 1   ? (const void *)bicgstab3_kernel<NDOF, G, 1, V, T>
                      : up == 4 ? (const void *)bicgstab3_kernel<NDOF, G, 4, V, T>
                                : (const void *)bicgstab3_kernel<NDOF, G, 2, V, T>;
-    return cudaLaunchCooperativeKernel(fn, dim3(c.blocks), dim3(kThreads), args, 0, c.stream);
+    // Shared-memory copy of each block's rows: column lists and, when they fit,
+    // values, for as long as the grid stays co-resident with that shared memory.
+    // The products then wait on the gathered x alone instead of the chain
+    // row pointer -> column index -> x.
+    size_t smem = 0;
+    if (c.lmax > 0) {
+        using M = RowMap<NDOF, G, T>;
+        const int64_t nw = (int64_t)c.blocks * (kThreads / 32);
+        const int64_t passes = (c.n_nodes + nw * M::NPW - 1) / (nw * M::NPW);
+        const int64_t n_rec = passes * (kThreads / 32) * M::NPW;
+        const size_t colb = ((size_t)n_rec * (c.lmax + 1) * sizeof(int32_t) + 15) & ~(size_t)15;
+        const size_t valb = (size_t)n_rec * NDOF * c.lmax * sizeof(V);
+        const int need = (c.blocks + c.num_sms - 1) / c.num_sms;      // CTAs per SM of this grid
+        for (int mode = 2; mode >= 1 && A.cache == 0; --mode) {
+            const size_t sm = colb + (mode == 2 ? valb : 0);
+            if (sm > 200 * 1024) continue;
+            if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, sm) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            if (per_sm >= need) {
+                A.cache = mode;
+                A.lmax = c.lmax;
+                smem = sm;
+            }
+        }
+    }
+    return cudaLaunchCooperativeKernel(fn, dim3(c.blocks), dim3(kThreads), args, smem, c.stream);
 }
 
 template <int NDOF, class V, class T>
@@ -1067,6 +1175,8 @@ cudaError_t solve_batch_t(const KrylovCtx &c, const gd::BatchKrylov &L, const V 
     A.out = nullptr;
     A.rtol = 0.0;
     A.max_it = max_it;
+    A.cache = 0;
+    A.lmax = 0;
     gd::BatchKrylov Lc = L;
     void *args[] = {&A, &Lc};
     const int up = c.up ? c.up : 1;
