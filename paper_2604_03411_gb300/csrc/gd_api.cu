@@ -241,7 +241,7 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
     kc.blocks = H.krylov_grid;
     kc.num_sms = H.num_sms;
     kc.up = H.krylov_up;
-    kc.lmax = 0;
+    kc.lmax = H.krylov_lmax;
     GD_CUDA(&H, cudaEventRecord(H.kv0, H.stream));
     bool fp32_vals = H.opt.precision == GD_MIXED;
     if (inner_fp32 && !fp32_vals) {
@@ -396,7 +396,7 @@ gd_status krylov_batch(gd::Handle &H, const std::vector<double> &eta, const doub
     kc.blocks = H.krylov_grid;
     kc.num_sms = H.num_sms;
     kc.up = H.krylov_up;
-    kc.lmax = 0;
+    kc.lmax = H.krylov_lmax;
     const int S = H.n_spec;
     GD_CUDA(&H, cudaMemcpyAsync((void *)H.bk.rtol, eta.data(), sizeof(double) * S, cudaMemcpyHostToDevice, H.stream));
     GD_CUDA(&H, cudaEventRecord(H.kv0, H.stream));
