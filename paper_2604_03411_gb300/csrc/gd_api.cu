@@ -499,14 +499,19 @@ gd_status mixed_noise(gd::Handle &H, const double *R32, std::vector<double> &noi
 // mixed_noise on the first Newton solve (and after every restart of the state) and
 // every kNoiseEvery solves, and in between taken as the measured ratio to the
 // specimen's force scale ||R_fixed|| (||R|| at the first iterate when nothing is
-// prescribed).  The FP64 pass costs as much as several FP32 passes.
+// prescribed).  The FP64 pass costs as much as several FP32 passes.  The ratio
+// drifts once damage lowers the reaction while the element forces that cancel in
+// the residual stay large, so a Newton solve whose line search stalls on an
+// estimate it did not measure itself measures it again (force = true).
 constexpr int kNoiseEvery = 8;
 
 gd_status noise_estimate(gd::Handle &H, const double *R, const std::vector<double> &scale,
-                         std::vector<double> &noise)
+                         std::vector<double> &noise, bool &measured, bool force = false)
 {
     const int S = H.n_spec;
-    if (H.noise_age <= 0 || (int)H.noise_ratio.size() != S) {
+    measured = false;
+    if (force || H.noise_age <= 0 || (int)H.noise_ratio.size() != S) {
+        measured = true;
         gd_status st = mixed_noise(H, R, noise);
         if (st) return st;
         H.noise_ratio.assign(S, 0.0);
@@ -535,13 +540,14 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
     double nrm = nr.free_;
     const double r0 = std::max(nr.free_, nr.fixed_);
     double noise = 0.0;
+    bool fresh = false;     // noise measured at an iterate of this solve
+    const std::vector<double> sc(1, nr.fixed_ > 0.0 ? nr.fixed_ : r0);
     if (H.opt.precision == GD_MIXED) {
         std::vector<double> nz;
-        const std::vector<double> sc(1, nr.fixed_ > 0.0 ? nr.fixed_ : r0);
-        if ((st = noise_estimate(H, H.R, sc, nz))) return st;
+        if ((st = noise_estimate(H, H.R, sc, nz, fresh))) return st;
         noise = nz[0];
     }
-    const double ntol = std::max(std::max(H.opt.newton_rtol * r0, H.opt.newton_atol), 2.0 * noise);
+    double ntol = std::max(std::max(H.opt.newton_rtol * r0, H.opt.newton_atol), 2.0 * noise);
     rep.residual0 = nrm;
     rep.local_failures = hc[0];
     rep.loading_points = hc[1];
@@ -567,9 +573,18 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
         // two halvings, a decrease below the noise cannot be measured)
         double alpha = 1.0, nt = 0.0;
         bool decreased = false;
-        const int ls_max = (H.opt.precision == GD_MIXED && nrm <= 8.0 * noise) ? std::min(2, H.opt.line_search_max)
-                                                                               : H.opt.line_search_max;
+        int ls_max = (H.opt.precision == GD_MIXED && nrm <= 8.0 * noise) ? std::min(2, H.opt.line_search_max)
+                                                                         : H.opt.line_search_max;
         for (int ls = 0; ls <= ls_max; ++ls) {
+            if (ls == 1 && H.opt.precision == GD_MIXED && !fresh) {
+                // the full step did not lower ||R_free||: measure the noise at this
+                // iterate before halving (the pass overwrites R_trial, recomputed below)
+                std::vector<double> nz;
+                if ((st = noise_estimate(H, H.R, sc, nz, fresh, true))) return st;
+                noise = nz[0];
+                ntol = std::max(ntol, 2.0 * noise);
+                if (nrm <= 8.0 * noise) ls_max = std::max(1, std::min(2, H.opt.line_search_max));
+            }
             GD_CUDA(&H, cudaMemcpyAsync(H.w_trial, H.w_dofs, sizeof(double) * H.n_dofs, cudaMemcpyDeviceToDevice,
                                         H.stream));
             GD_CUDA(&H, gd::launch_axpy_free(c, H.w_trial, delta, alpha));
@@ -656,12 +671,11 @@ gd_status newton_batch(gd::Handle &H, gd_newton_report &rep)
         for (double x : v) t += x * x;
         return std::sqrt(t);
     };
-    std::vector<double> noise(S, 0.0);
-    if (H.opt.precision == GD_MIXED) {
-        std::vector<double> sc(S);
-        for (int s = 0; s < S; ++s) sc[s] = nx[s] > 0.0 ? nx[s] : nf[s];
-        if ((st = noise_estimate(H, H.R, sc, noise))) return st;
-    }
+    std::vector<double> noise(S, 0.0), sc(S);
+    bool fresh = false;     // noise measured at an iterate of this solve
+    for (int s = 0; s < S; ++s) sc[s] = nx[s] > 0.0 ? nx[s] : nf[s];
+    if (H.opt.precision == GD_MIXED)
+        if ((st = noise_estimate(H, H.R, sc, noise, fresh))) return st;
     for (int s = 0; s < S; ++s) {
         r0[s] = std::max(nf[s], nx[s]);
         ntol[s] = std::max(std::max(H.opt.newton_rtol * r0[s], H.opt.newton_atol), 2.0 * noise[s]);
@@ -712,8 +726,20 @@ gd_status newton_batch(gd::Handle &H, gd_newton_report &rep)
             accepted[s] = done[s];
             if (!done[s] && nf[s] > 8.0 * noise[s]) near_floor = false;
         }
-        const int ls_max = near_floor ? std::min(2, H.opt.line_search_max) : H.opt.line_search_max;
+        int ls_max = near_floor ? std::min(2, H.opt.line_search_max) : H.opt.line_search_max;
         for (int ls = 0; ls <= ls_max; ++ls) {
+            if (ls == 1 && H.opt.precision == GD_MIXED && !fresh) {
+                // a full step lowered no ||R_free|| of some specimen: measure the noise
+                // at this iterate before halving (the pass overwrites R_trial and the
+                // right-hand side, both recomputed before they are read again)
+                if ((st = noise_estimate(H, H.R, sc, noise, fresh, true))) return st;
+                near_floor = true;
+                for (int s = 0; s < S; ++s) {
+                    ntol[s] = std::max(ntol[s], 2.0 * noise[s]);
+                    if (!accepted[s] && nf[s] > 8.0 * noise[s]) near_floor = false;
+                }
+                if (near_floor) ls_max = std::max(1, std::min(2, H.opt.line_search_max));
+            }
             if ((st = set_coef(H, alpha))) return st;
             GD_CUDA(&H, cudaMemcpyAsync(H.w_trial, H.w_dofs, sizeof(double) * H.n_dofs, cudaMemcpyDeviceToDevice,
                                         H.stream));
