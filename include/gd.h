@@ -138,6 +138,13 @@ typedef struct gd_options {
                                   BiCGStab always.  GD_INNER_REFINED: FP32 BiCGStab cycles
                                   refined by FP64 residuals b - K x until the FP64 tolerance
                                   is met.  A failed FP32 solve falls back to FP64.          */
+    int32_t coarse;            /* single-specimen handles: target number of coarse unknowns of
+                                  the two-level preconditioner M^-1 = D^-1 + P (P^T K P)^-1 P^T
+                                  (D the node-block diagonal, P constants and rigid rotations
+                                  on aggregates of the node graph); default 1536, at most
+                                  3072, 0 = node-block Jacobi only.  The preconditioner
+                                  changes the iteration count, not the solution.  Batches
+                                  ignore it.                                                */
 } gd_options;
 
 typedef struct gd_newton_report {
@@ -173,7 +180,7 @@ typedef struct gd_handle gd_handle;
 /* Fills *opt with the defaults: FP64, newton_rtol 1e-10, newton_atol 1e-12,
  * newton_max 25, line_search_max 12, BiCGStab with krylov_rtol 1e-12 and
  * krylov_max 20000, local_max 100, checkpoint_every 5, max_step_cuts 4,
- * default stream. */
+ * default stream, coarse 1536. */
 void gd_default_options(gd_options *opt);
 
 /* Creates a problem (Sec. 3.1 kernel inputs, Sec. 3.2 load path): copies and
@@ -266,6 +273,19 @@ gd_status gd_spmv(gd_handle *h, const double *x, double *y, int32_t free_only);
  * Errors: GD_ERR_KRYLOV when the tolerance is not reached. */
 gd_status gd_solve(gd_handle *h, const void *csr_vals, const double *b, double *x, int32_t *iterations,
                    double *rel_residual);
+
+/* Coarse space of the handle's two-level preconditioner (see gd_options.coarse):
+ * number of aggregates and of coarse unknowns (0 and 0 when it is off).  Host
+ * only.  Errors: GD_ERR_ARG. */
+gd_status gd_coarse_info(gd_handle *h, int32_t *n_aggregates, int32_t *n_coarse);
+
+/* The aggregates the two-level preconditioner would build for `mesh` (host only,
+ * no device needed): greedy breadth-first aggregates of about target_nodes
+ * connected nodes over the node graph of gd_build_pattern's pattern, those below
+ * a quarter of the target joined to their smallest neighbour.  agg (host,
+ * [n_nodes]) receives every node's aggregate in [0, *n_aggregates).
+ * Errors: GD_ERR_ARG, GD_ERR_MESH (as gd_build_pattern). */
+gd_status gd_coarse_aggregates(const gd_mesh *mesh, int32_t target_nodes, int32_t *agg, int32_t *n_aggregates);
 
 /* Largest system (n_nodes * ndof) that gd_solve_noalloc accepts. */
 #define GD_NOALLOC_MAX_DOFS 131072

@@ -58,7 +58,8 @@ class GdOptions(ctypes.Structure):
                 ("newton_max", ctypes.c_int32), ("line_search_max", ctypes.c_int32), ("krylov", ctypes.c_int32),
                 ("krylov_rtol", ctypes.c_double), ("krylov_max", ctypes.c_int32), ("gmres_m", ctypes.c_int32),
                 ("local_max", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
-                ("max_step_cuts", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p), ("inner_solve", ctypes.c_int32)]
+                ("max_step_cuts", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p), ("inner_solve", ctypes.c_int32),
+                ("coarse", ctypes.c_int32)]
 
 
 class GdNewtonReport(ctypes.Structure):
@@ -100,6 +101,9 @@ PROTOTYPES = {
     "gd_set_params": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p]),
     "gd_csr_pattern": (ctypes.c_int, [_H, _i64p, _i64p, _i32p, _i32p]),
     "gd_build_pattern": (ctypes.c_int, [ctypes.POINTER(GdMesh), _i64p, _i64p, _i32p, _i32p, _i32p]),
+    "gd_coarse_info": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "gd_coarse_aggregates": (ctypes.c_int, [ctypes.POINTER(GdMesh), ctypes.c_int32, _i32p,
+                                            ctypes.POINTER(ctypes.c_int32)]),
     "gd_assemble": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "gd_spmv": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
@@ -215,6 +219,23 @@ def gd_build_pattern(m):
     _check(lib().gd_build_pattern(ctypes.byref(mesh), None, None, _hp(rowptr, _i32p), _hp(colidx, _i32p),
                                   _hp(slot, _i32p)), None)
     return rowptr, colidx, slot.reshape(-1, nen, nen)
+
+
+def gd_coarse_aggregates(m, target_nodes: int):
+    """Host-only: (agg [n_nodes], n_aggregates) of the two-level preconditioner's aggregation."""
+    mesh, keep = _mesh_struct(m)
+    agg = np.zeros(m.n_nodes, np.int32)
+    na = ctypes.c_int32()
+    _check(lib().gd_coarse_aggregates(ctypes.byref(mesh), int(target_nodes), _hp(agg, _i32p), ctypes.byref(na)), None)
+    return agg, na.value
+
+
+def gd_coarse_info(h: Handle):
+    """(aggregates, coarse unknowns) of the handle's two-level preconditioner ((0, 0): off)."""
+    na = ctypes.c_int32()
+    nc = ctypes.c_int32()
+    _check(lib().gd_coarse_info(h.ptr, ctypes.byref(na), ctypes.byref(nc)), h.ptr)
+    return na.value, nc.value
 
 
 def gd_create(problem, options: Optional[GdOptions] = None) -> Handle:

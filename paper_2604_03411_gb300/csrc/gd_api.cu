@@ -22,6 +22,10 @@ namespace {
 
 thread_local std::string g_create_error;
 
+// most coarse unknowns of the two-level preconditioner: the inversion kernel keeps a
+// panel of 16 coarse rows in shared memory (192 KB at 3072)
+constexpr int kCoarseMax = 3072;
+
 gd_status fail(gd::Handle *H, gd_status st, const std::string &msg)
 {
     if (H) H->err = msg;
@@ -116,6 +120,11 @@ void free_handle(gd::Handle &H)
     dfree(H.bk_cnt);
     dfree(H.psi_tab);
     dfree(H.yld_tab);
+    {
+        gd::CoarseSpace &c = H.coarse;
+        void *cp[] = {c.agg, c.coff, c.P, c.Ac, c.X32, c.X64, c.rc, c.cc, c.status};
+        for (void *p : cp) dfree(p);
+    }
     for (gd::DevNet &n : H.h_psi_tab) {
         dfree(n.p); dfree(n.W2T); dfree(n.pf); dfree(n.W2Tf);
     }
@@ -242,6 +251,7 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
     kc.num_sms = H.num_sms;
     kc.up = H.krylov_up;
     kc.lmax = H.krylov_lmax;
+    kc.coarse = H.coarse.nc > 0 ? &H.coarse : nullptr;
     GD_CUDA(&H, cudaEventRecord(H.kv0, H.stream));
     bool fp32_vals = H.opt.precision == GD_MIXED;
     if (inner_fp32 && !fp32_vals) {
@@ -251,7 +261,7 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
         fp32_vals = true;
     }
     GD_CUDA(&H, gd::krylov_solve(kc, vals, fp32_vals, b, x, rtol, H.opt.krylov_max, inner_fp32));
-    H.launches += 2;
+    H.launches += kc.coarse ? 4 : 2;
     GD_CUDA(&H, cudaEventRecord(H.kv1, H.stream));
     double kout[3];
     GD_CUDA(&H, cudaMemcpyAsync(kout, H.scal + 24, 3 * sizeof(double), cudaMemcpyDeviceToHost, H.stream));
@@ -1112,6 +1122,7 @@ void gd_default_options(gd_options *o)
     o->checkpoint_every = 5;
     o->max_step_cuts = 4;
     o->cuda_stream = nullptr;
+    o->coarse = 1536;
 }
 
 const char *gd_last_error(const gd_handle *h) { return h ? h->h.err.c_str() : g_create_error.c_str(); }
@@ -1311,6 +1322,7 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
         return fail(nullptr, GD_ERR_ARG, "iteration caps");
     if (o.inner_solve < GD_INNER_AUTO || o.inner_solve > GD_INNER_REFINED)
         return fail(nullptr, GD_ERR_ARG, "inner_solve");
+    if (o.coarse < 0 || o.coarse > kCoarseMax) return fail(nullptr, GD_ERR_ARG, "coarse must be in [0, 3072]");
 
     const int dim = mesh->dim, nen = dim == 2 ? 4 : 8, ndof = dim + 1;
     const int64_t NN = mesh->n_nodes, NE = mesh->n_elems;
@@ -1481,6 +1493,42 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
     if (n_spec > 1) {
         gd_status sb = build_batch_krylov(H);
         if (sb) return bail(sb);
+    } else if (o.coarse > 0) {
+        // two-level preconditioner: aggregates sized so the coarse unknowns come near
+        // the target (larger aggregates when the kept modes exceed the cap)
+        gd::CoarseSpace &C = H.coarse;
+        C.nm = gd::coarse_modes(dim);
+        std::vector<int32_t> agg, coff;
+        std::vector<float> Pc;
+        int target = (int)std::max<int64_t>(4, (NN * C.nm + o.coarse - 1) / o.coarse);
+        int32_t na = 0;
+        for (int tries = 0; tries < 8; ++tries) {
+            na = gd::coarse_aggregate(NN, ndof, H.h_rowptr, H.h_colidx, target, agg);
+            gd::coarse_basis(dim, NN, mesh->coords, fixed.data(), agg, na, Pc, coff);
+            if (coff[na] <= kCoarseMax) break;
+            target = target * 3 / 2 + 1;
+        }
+        if (coff[na] > kCoarseMax) {
+            H.err = "coarse space larger than 3072 unknowns";
+            return bail(GD_ERR_ARG);
+        }
+        C.n_agg = na;
+        C.nc = coff[na];
+        if (C.nc > 0) {
+            const size_t nc = (size_t)C.nc;
+            GD_CREATE_CUDA(dalloc(&C.agg, agg.size()));
+            GD_CREATE_CUDA(dalloc(&C.coff, coff.size()));
+            GD_CREATE_CUDA(dalloc(&C.P, Pc.size()));
+            GD_CREATE_CUDA(dalloc(&C.Ac, nc * nc));
+            GD_CREATE_CUDA(dalloc(&C.X32, nc * nc));
+            GD_CREATE_CUDA(dalloc(&C.X64, nc * nc));
+            GD_CREATE_CUDA(dalloc(&C.rc, 2 * nc));
+            GD_CREATE_CUDA(dalloc(&C.cc, nc));
+            GD_CREATE_CUDA(dalloc(&C.status, 1));
+            GD_CREATE_CUDA(cudaMemcpy(C.agg, agg.data(), sizeof(int32_t) * agg.size(), cudaMemcpyHostToDevice));
+            GD_CREATE_CUDA(cudaMemcpy(C.coff, coff.data(), sizeof(int32_t) * coff.size(), cudaMemcpyHostToDevice));
+            GD_CREATE_CUDA(cudaMemcpy(C.P, Pc.data(), sizeof(float) * Pc.size(), cudaMemcpyHostToDevice));
+        }
     }
     H.red_blocks = 4 * H.num_sms;                    // room for Krylov grids up to 4 CTAs per SM
     GD_CREATE_CUDA(dalloc(&H.red, (size_t)8 * H.red_blocks));
@@ -1566,6 +1614,27 @@ gd_status gd_csr_pattern(gd_handle *h, int64_t *n_rows, int64_t *nnz, int32_t *r
     if (nnz) *nnz = H.nnz;
     if (rowptr) std::memcpy(rowptr, H.h_rowptr.data(), sizeof(int32_t) * H.h_rowptr.size());
     if (colidx) std::memcpy(colidx, H.h_colidx.data(), sizeof(int32_t) * H.h_colidx.size());
+    return GD_OK;
+}
+
+gd_status gd_coarse_info(gd_handle *h, int32_t *n_aggregates, int32_t *n_coarse)
+{
+    if (!h) return fail(nullptr, GD_ERR_ARG, "handle is null");
+    if (n_aggregates) *n_aggregates = h->h.coarse.nc > 0 ? h->h.coarse.n_agg : 0;
+    if (n_coarse) *n_coarse = h->h.coarse.nc;
+    return GD_OK;
+}
+
+gd_status gd_coarse_aggregates(const gd_mesh *mesh, int32_t target_nodes, int32_t *agg, int32_t *n_aggregates)
+{
+    if (!agg || !n_aggregates) return fail(nullptr, GD_ERR_ARG, "output arrays are null");
+    if (target_nodes < 1) return fail(nullptr, GD_ERR_ARG, "target_nodes must be positive");
+    Pattern P;
+    gd_status st = build_pattern(mesh, P);
+    if (st) return st;
+    std::vector<int32_t> a;
+    *n_aggregates = gd::coarse_aggregate(mesh->n_nodes, mesh->dim + 1, P.rowptr, P.colidx, target_nodes, a);
+    std::memcpy(agg, a.data(), sizeof(int32_t) * a.size());
     return GD_OK;
 }
 
@@ -1686,11 +1755,12 @@ gd_status gd_autotune(gd_handle *h, gd_tune_report *rep)
     H.krylov_grid = gd::krylov_blocks(H.ndof, H.opt.precision == GD_MIXED, H.num_sms, kpick);
     if (H.krylov_grid < 1) H.krylov_grid = keep_grid;
     r.krylov_ctas_per_sm = kpick;
-    // node groups per product round at the chosen grid
+    // node groups per product round at the chosen grid (the two-level kernel has one)
     const int ups[3] = {1, 2, 4};
     double ubest = 1e300;
     int upick = H.krylov_up;
-    for (int ui = 0; ui < 3 && st == GD_OK; ++ui) {
+    for (double &v : r.krylov_us_up) v = -1.0;
+    for (int ui = 0; ui < 3 && st == GD_OK && H.coarse.nc == 0; ++ui) {
         H.krylov_up = ups[ui];
         double tmin = 1e300;
         for (int rep_i = 0; rep_i < 2; ++rep_i) {

@@ -118,6 +118,22 @@ struct BatchKrylov {
     int J = 0;                            // max specimens per block
     int n_spec = 0;
 };
+// Two-level preconditioner (gd_coarse.cu): aggregation coarse space of the node
+// graph, M^-1 = D^-1 + P Ac^-1 P^T with Ac = P^T A P.
+struct CoarseSpace {
+    int nm = 0;                   // basis slots per aggregate: ndof constants + rotations (4 in 2D, 7 in 3D)
+    int n_agg = 0;
+    int nc = 0;                   // coarse unknowns (the kept basis columns of all aggregates)
+    int32_t *agg = nullptr;       // [n_nodes] aggregate of every node
+    int32_t *coff = nullptr;      // [n_agg + 1] first coarse unknown of every aggregate
+    float *P = nullptr;           // [n_nodes][ndof][nm] basis values (zero beyond the kept columns)
+    double *Ac = nullptr;         // [nc][nc] Galerkin matrix
+    float *X32 = nullptr;         // [nc][nc] its inverse
+    double *X64 = nullptr;        // [nc][nc] the same values in FP64
+    double *rc = nullptr;         // [2][nc] restriction sums (FP32 solves use them as float storage)
+    double *cc = nullptr;         // [nc] coarse solution (likewise)
+    int *status = nullptr;        // device: 0 when X holds the inverse
+};
 struct Handle {
     // sizes
     int dim = 0, nen = 0, nq = 0, ndof = 0;
@@ -198,6 +214,7 @@ struct Handle {
     int noise_age = 0;
     int krylov_up = 0;                                   // 0: the precision's default
     int krylov_lmax = 0;                                 // longest CSR row
+    CoarseSpace coarse;                                  // two-level preconditioner (nc = 0: off)
     // timing
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, kv0 = nullptr, kv1 = nullptr;
     double assembly_ms = 0.0, krylov_ms = 0.0;
@@ -282,6 +299,21 @@ cudaError_t launch_axpby(int64_t n, double *out, const double *x, double b, cons
 cudaError_t launch_damage_max(const double *kappa, int64_t n, double eta_d, double kappa_d, double *out,
                               cudaStream_t s);
 
+int coarse_modes(int dim);
+// greedy breadth-first aggregates of about `target` nodes over the node graph of
+// the node-block CSR pattern; aggregates below target/4 join their smallest
+// neighbour.  Returns the number of aggregates, agg[i] in [0, n).
+int32_t coarse_aggregate(int64_t n_nodes, int ndof, const std::vector<int32_t> &rowptr,
+                         const std::vector<int32_t> &colidx, int target, std::vector<int32_t> &agg);
+// orthonormal basis per aggregate (constants per nodal unknown, rigid rotations of
+// the displacement; zero on prescribed dofs); P [n_nodes][ndof][nm], coff [n_agg + 1]
+void coarse_basis(int dim, int64_t n_nodes, const double *coords, const uint8_t *fixed,
+                  const std::vector<int32_t> &agg, int32_t n_agg, std::vector<float> &P, std::vector<int32_t> &coff);
+// Ac = P^T A P for the tangent values vals, X32 = Ac^-1 (and X64 when want_x64)
+cudaError_t coarse_setup(const CoarseSpace &cs, int ndof, int64_t n_nodes, const int32_t *rowptr,
+                         const int32_t *colidx, const void *vals, bool fp32_vals, bool want_x64, int num_sms,
+                         cudaStream_t s);
+
 // persistent cooperative Krylov solve (gd_krylov.cu)
 struct KrylovCtx {
     int64_t n_nodes;
@@ -298,6 +330,7 @@ struct KrylovCtx {
     int num_sms;
     int up = 0;                 // node groups per product round: 1, 2 or 4 (0: 1)
     int lmax = 0;               // longest row (0: rows are not copied to shared memory)
+    const CoarseSpace *coarse = nullptr;   // two-level preconditioner (single systems; null: Jacobi only)
 };
 cudaError_t krylov_solve_batch(const KrylovCtx &c, const BatchKrylov &L, const void *vals, bool fp32_vals,
                                const double *b, double *x, int max_it, bool fp32_vectors);

@@ -4,11 +4,12 @@
 // The paper solves each Newton system with a direct LU factorisation (Sec. 3.2);
 // on the device an iterative solve is used instead.  All blocks of a
 // cooperative launch are co-resident, so phases are separated by grid-wide
-// barriers instead of kernel launches.  Dot products are written as per-block
-// partials; after a barrier every block sums all partials in the same fixed
-// order, so every block holds bit-identical scalars and takes the same branch
-// (deterministic, no atomics, no host round trip).  The loop ends on the device
-// when ||r|| <= rtol ||b||, on breakdown, or after max_it iterations.
+// barriers instead of kernel launches.  Every grid-wide sum ends in one global
+// accumulator that all blocks read after the barrier, so every block holds the
+// same scalars and takes the same branch (no host round trip).  The loop ends
+// on the device when ||r|| <= rtol ||b||, on breakdown, or after max_it
+// iterations.  Single systems may add a second, coarse level to the
+// preconditioner (gd_coarse.cu): three more phases per application.
 //
 // Prescribed dofs: Krylov vectors are zero there and the operator is the
 // identity there (the eliminated Newton system).
@@ -45,7 +46,83 @@ struct KArgs {
     // 0 none, 1 column lists, 2 column lists and values; lmax = longest row
     int cache;
     int lmax;
+    // coarse level (single-system kernel with CO): P [n_nodes][NDOF][nm], aggregate of
+    // every node, first coarse unknown of every aggregate, the inverse coarse matrix
+    // (FP32 for FP32 vectors, FP64 otherwise), restriction sums [2][nc] and coarse
+    // solution [nc] in the vector type, status word of the inversion
+    int c_nc;
+    const float *c_P;
+    const int32_t *c_agg, *c_off;
+    const float *c_X32;
+    const double *c_X64;
+    T *c_rc, *c_cc;
+    const int *c_status;
 };
+
+template <int NDOF>
+struct CoarseModes {
+    static constexpr int NM = NDOF == 3 ? 4 : 7;     // ndof constants + rigid rotations (2D: 1, 3D: 3)
+};
+
+template <class T>
+__device__ __forceinline__ T warp_sum_t(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// restriction P^T w of the node whose NDOF values sit in lanes base..base+NDOF-1:
+// the node's lanes split its nm coarse components and add them to rc (atomics).
+// Called by every lane of the warp.
+template <int NDOF, int LPN, class V, class T>
+__device__ __forceinline__ void coarse_restrict(const KArgs<V, T> &A, int32_t nd, bool node_ok, int sub, int base,
+                                                T w, T *rc)
+{
+    constexpr int NM = CoarseModes<NDOF>::NM;
+    T wk[NDOF];
+#pragma unroll
+    for (int k = 0; k < NDOF; ++k) wk[k] = __shfl_sync(0xffffffffu, w, base + k);
+    if (!node_ok) return;
+    const int32_t a = A.c_agg[nd], o = A.c_off[a], n = A.c_off[a + 1] - o;
+    for (int m = sub; m < n; m += LPN) {
+        T sum = T(0);
+#pragma unroll
+        for (int k = 0; k < NDOF; ++k) sum += (T)A.c_P[(nd * NDOF + k) * NM + m] * wk[k];
+        atomicAdd(rc + o + m, sum);
+    }
+}
+
+// cc = Ac^-1 rc: one warp per coarse row, lanes along the row
+template <class V, class T>
+__device__ __forceinline__ void coarse_solve(const KArgs<V, T> &A, const T *rc, T *cc, int32_t gw, int32_t nw,
+                                             int lane)
+{
+    const int32_t nc = A.c_nc;
+    for (int32_t k = gw; k < nc; k += nw) {
+        T s = T(0);
+        if constexpr (std::is_same<T, double>::value) {
+            const double *xr = A.c_X64 + (int64_t)k * nc;
+            for (int32_t j = lane; j < nc; j += 32) s += xr[j] * rc[j];
+        } else {
+            const float *xr = A.c_X32 + (int64_t)k * nc;
+            for (int32_t j = lane; j < nc; j += 32) s += xr[j] * rc[j];
+        }
+        s = warp_sum_t(s);
+        if (lane == 0) cc[k] = s;
+    }
+}
+
+// row sub of P cc for node nd
+template <int NDOF, class V, class T>
+__device__ __forceinline__ T coarse_prolong(const KArgs<V, T> &A, int32_t nd, int sub, const T *cc)
+{
+    constexpr int NM = CoarseModes<NDOF>::NM;
+    const int32_t a = A.c_agg[nd], o = A.c_off[a], n = A.c_off[a + 1] - o;
+    T s = T(0);
+    for (int m = 0; m < n; ++m) s += (T)A.c_P[(nd * NDOF + sub) * NM + m] * cc[o + m];
+    return s;
+}
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -246,7 +323,7 @@ __device__ __forceinline__ T node_apply(const T *binv, int64_t nd_wide, bool nod
     return fixed ? T(0) : out;
 }
 
-template <int NDOF, int G, int UP, class V, class T>
+template <int NDOF, int G, int UP, class V, class T, bool CO = false>
 __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
 {
     using M = RowMap<NDOF, G, T>;
@@ -259,6 +336,29 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
     const int32_t nw = (gridDim.x * kThreads) >> 5;
     const int32_t n_nodes = (int32_t)A.n_nodes;
     const int32_t passes = (n_nodes + nw * NPW - 1) / (nw * NPW);   // warp-uniform
+    // CO: two-level preconditioner M^-1 = D^-1 + P Ac^-1 P^T.  The node-block part is
+    // applied where the vector is formed, together with the restriction P^T (atomic
+    // sums into rc); after the phase's barrier, Ac^-1 rc (one warp per coarse row),
+    // a barrier, the prolongation P added to the owned rows, and a barrier before
+    // the product reads them.  Skipped when the inversion reported a zero pivot.
+    bool co = false;
+    if constexpr (CO) co = __ldcg(A.c_status) == 0;
+    T *rc0 = nullptr, *rc1 = nullptr, *cc = nullptr;
+    if constexpr (CO) {
+        rc0 = A.c_rc;
+        rc1 = A.c_rc + A.c_nc;
+        cc = A.c_cc;
+    }
+    auto coarse_apply = [&](T *rc, T *dst) {
+        coarse_solve<V, T>(A, rc, cc, gw, nw, lane);
+        grid.sync();
+        for (int32_t ps = 0; ps < passes; ++ps) {
+            const int32_t nd = (gw + ps * nw) * NPW + slot;
+            if (slot < NPW && nd < n_nodes && sub < NDOF) dst[nd * NDOF + sub] += coarse_prolong<NDOF, V, T>(A, nd, sub, cc);
+        }
+        for (int32_t k = blockIdx.x * kThreads + threadIdx.x; k < A.c_nc; k += gridDim.x * kThreads) rc[k] = T(0);
+        grid.sync();
+    };
     // vector roles: r (also s), rh, p, v, q, t, y = M^-1 v (read by phase 2's product),
     // w = M^-1 r (read by phase 4's product), u.  y and w must differ: phase 1 of the
     // next iteration writes y with no barrier after phase 4, whose product still reads
@@ -308,6 +408,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
             const bool fx = own ? A.fixed[row] != 0 : true;
             const T bv = (own && !fx) ? (T)A.b[row] : T(0);
             const T yv = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, bv, fx);
+            if (co) coarse_restrict<NDOF, LPN, V, T>(A, nd, node_ok, sub, nbase, bv, rc0);
             if (own) {
                 r[row] = bv;
                 rh[row] = bv;
@@ -335,6 +436,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
     if (!(bnorm > 0.0)) {
         if (!(bnorm == 0.0)) status = 2;
     } else {
+        if (co) coarse_apply(rc0, wv);
         // u = A w
         for (int32_t ps0 = 0; ps0 < passes; ps0 += UP) {
             int32_t ndu[UP];
@@ -380,6 +482,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                         s1.add(rh[row], vn);
                     }
                     const T yv = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, vn, fx);
+                    if (co) coarse_restrict<NDOF, LPN, V, T>(A, nd, node_ok, sub, nbase, vn, rc0);
                     if (own) y[row] = yv;
                 }
                 double pv[1] = {s1.value()};
@@ -393,6 +496,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                 acc_read<1>(A.red, sl, it & 1, t1);
                 alpha = t1[0] != 0.0 ? rho / t1[0] : 0.0;
             }
+            if (co) coarse_apply(rc0, y);
             // phase 2
             {
                 DotAcc<T> ts, tt;
@@ -459,6 +563,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                         prr.add(rn, rn);
                     }
                     const T wn = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, rn, fx);
+                    if (co) coarse_restrict<NDOF, LPN, V, T>(A, nd, node_ok, sub, nbase, rn, rc1);
                     if (own) wv[row] = wn;
                 }
                 double pv[2] = {prhr.value(), prr.value()};
@@ -496,6 +601,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                 beta = (t3[0] / rho) * (alpha / omega);
                 rho = t3[0];
             }
+            if (co) coarse_apply(rc1, wv);
             // phase 4: u = A w (and rh = r on a restart)
             for (int32_t ps0 = 0; ps0 < passes; ps0 += UP) {
                 int32_t ndu[UP];
@@ -533,7 +639,18 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
         const bool fx = own ? A.fixed[row] != 0 : true;
         const T xv = own ? xt[row] : T(0);
         const T xo = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, xv, fx);
+        if (co) coarse_restrict<NDOF, LPN, V, T>(A, nd, node_ok, sub, nbase, xv, rc0);
         if (own) A.x_out[row] = (double)xo;
+    }
+    if (co) {
+        grid.sync();
+        coarse_solve<V, T>(A, rc0, cc, gw, nw, lane);
+        grid.sync();
+        for (int32_t ps = 0; ps < passes; ++ps) {
+            const int32_t nd = (gw + ps * nw) * NPW + slot;
+            if (slot < NPW && nd < n_nodes && sub < NDOF)
+                A.x_out[nd * NDOF + sub] += (double)coarse_prolong<NDOF, V, T>(A, nd, sub, cc);
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         A.out[0] = it;
@@ -1066,7 +1183,7 @@ cudaError_t solve_t(const KrylovCtx &c, const V *vals, const double *b, double *
                                                                           c.fixed, binv);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    KArgs<V, T> A;
+    KArgs<V, T> A{};
     A.n_nodes = c.n_nodes;
     A.rowptr = c.rowptr;
     A.colidx = c.colidx;
@@ -1094,12 +1211,39 @@ cudaError_t solve_t(const KrylovCtx &c, const V *vals, const double *b, double *
     A.max_it = max_it;
     A.cache = 0;
     A.lmax = 0;
+    A.c_nc = 0;
+    A.c_P = nullptr;
+    A.c_agg = A.c_off = nullptr;
+    A.c_X32 = nullptr;
+    A.c_X64 = nullptr;
+    A.c_rc = A.c_cc = nullptr;
+    A.c_status = nullptr;
+    const bool co = c.coarse && c.coarse->nc > 0;
+    if (co) {
+        const CoarseSpace &cs = *c.coarse;
+        e = coarse_setup(cs, NDOF, c.n_nodes, c.rowptr, c.colidx, vals, std::is_same<V, float>::value,
+                         std::is_same<T, double>::value, c.num_sms, c.stream);
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(cs.rc, 0, sizeof(T) * 2 * (size_t)cs.nc, c.stream);
+        if (e != cudaSuccess) return e;
+        A.c_nc = cs.nc;
+        A.c_P = cs.P;
+        A.c_agg = cs.agg;
+        A.c_off = cs.coff;
+        A.c_X32 = cs.X32;
+        A.c_X64 = cs.X64;
+        A.c_rc = (T *)cs.rc;
+        A.c_cc = (T *)cs.cc;
+        A.c_status = cs.status;
+    }
     // the grid-wide accumulators (2 parities x 5 slots) start at zero
     e = cudaMemsetAsync(c.red, 0, 10 * sizeof(double), c.stream);
     if (e != cudaSuccess) return e;
     void *args[] = {&A};
     const int up = c.up ? c.up : 1;
-    const void *fn = up == 1   ? (const void *)bicgstab3_kernel<NDOF, G, 1, V, T>
+    // the two-level variant interleaves one node group per lane
+    const void *fn = co        ? (const void *)bicgstab3_kernel<NDOF, G, 1, V, T, true>
+                     : up == 1 ? (const void *)bicgstab3_kernel<NDOF, G, 1, V, T>
                      : up == 4 ? (const void *)bicgstab3_kernel<NDOF, G, 4, V, T>
                                : (const void *)bicgstab3_kernel<NDOF, G, 2, V, T>;
     // Shared-memory copy of each block's rows: column lists and, when they fit,
@@ -1149,7 +1293,7 @@ cudaError_t solve_batch_t(const KrylovCtx &c, const gd::BatchKrylov &L, const V 
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(L.active_cnt, 0, 2 * sizeof(int), c.stream);
     if (e != cudaSuccess) return e;
-    KArgs<V, T> A;
+    KArgs<V, T> A{};
     A.n_nodes = c.n_nodes;
     A.rowptr = c.rowptr;
     A.colidx = c.colidx;
@@ -1187,14 +1331,14 @@ cudaError_t solve_batch_t(const KrylovCtx &c, const gd::BatchKrylov &L, const V 
                                        args, 0, c.stream);
 }
 
-// co-resident CTAs per SM of the solve kernels of one variant
 // co-resident CTAs per SM of the solve kernels of one variant (every UP)
 template <int NDOF, class V, class T>
 int coop_per_sm()
 {
     constexpr int G = NDOF == 3 ? 8 : 32;
-    const void *fns[6] = {(const void *)bicgstab3_kernel<NDOF, G, 1, V, T>, (const void *)bicgstab3_kernel<NDOF, G, 2, V, T>,
+    const void *fns[7] = {(const void *)bicgstab3_kernel<NDOF, G, 1, V, T>, (const void *)bicgstab3_kernel<NDOF, G, 2, V, T>,
                           (const void *)bicgstab3_kernel<NDOF, G, 4, V, T>,
+                          (const void *)bicgstab3_kernel<NDOF, G, 1, V, T, true>,
                           (const void *)bicgstab3_batch_kernel<NDOF, G, 1, V, T>,
                           (const void *)bicgstab3_batch_kernel<NDOF, G, 2, V, T>,
                           (const void *)bicgstab3_batch_kernel<NDOF, G, 4, V, T>};

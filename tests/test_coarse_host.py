@@ -1,0 +1,86 @@
+"""Host logic of the two-level preconditioner's coarse space (no GPU): the
+breadth-first aggregation of the node graph covers every node once, keeps every
+aggregate connected, sizes the aggregates near the target, and reduces to the
+trivial partitions at the extremes; checked against an independent graph built
+from the element connectivity."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.csgraph as csg
+
+from paper_2604_03411_gb300 import inputs as I
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2604_03411_gb300 import build as build_mod
+    build_mod.build()
+    import paper_2604_03411_gb300.binding as binding
+    binding.lib()
+    return binding
+
+
+def node_graph(mesh):
+    """Node adjacency (nodes sharing an element), from the connectivity alone."""
+    conn = np.asarray(mesh.conn, np.int64)
+    e = np.repeat(np.arange(conn.shape[0]), conn.shape[1])
+    Ne = sp.csr_matrix((np.ones(conn.size), (e, conn.ravel())), shape=(conn.shape[0], mesh.n_nodes))
+    return (Ne.T @ Ne).tocsr()
+
+
+def check_partition(mesh, agg, n_agg):
+    assert agg.shape == (mesh.n_nodes,)
+    assert agg.min() == 0 and agg.max() == n_agg - 1
+    assert np.unique(agg).size == n_agg
+    G = node_graph(mesh)
+    for a in range(n_agg):
+        idx = np.nonzero(agg == a)[0]
+        sub = G[idx][:, idx]
+        ncomp, _ = csg.connected_components(sub, directed=False)
+        assert ncomp == 1, f"aggregate {a} is not connected"
+    return np.bincount(agg)
+
+
+@pytest.mark.parametrize("target", [9, 25, 80])
+def test_notched_plate_aggregates(B, target):
+    mesh = I.uniaxial_bc_2d(I.notched_plate_q4(60, 24))
+    agg, n_agg = B.gd_coarse_aggregates(mesh, target)
+    sizes = check_partition(mesh, agg, n_agg)
+    assert sizes.max() <= target + target // 4 * 8      # a full aggregate plus a few merged remnants
+    assert sizes.min() >= 1
+    # the greedy search fills most aggregates to the target
+    assert np.median(sizes) >= 0.5 * target
+    again, n2 = B.gd_coarse_aggregates(mesh, target)
+    assert n2 == n_agg and np.array_equal(again, agg)
+
+
+def test_hex8_aggregates(B):
+    mesh = I.biaxial_bc_3d(I.structured_hex8(7, 6, 5))
+    agg, n_agg = B.gd_coarse_aggregates(mesh, 27)
+    sizes = check_partition(mesh, agg, n_agg)
+    assert sizes.sum() == mesh.n_nodes
+    assert np.median(sizes) >= 13
+
+
+def test_extremes(B):
+    mesh = I.uniaxial_bc_2d(I.structured_q4(5, 4))
+    agg, n_agg = B.gd_coarse_aggregates(mesh, 1)
+    assert n_agg == mesh.n_nodes and np.array_equal(np.sort(agg), np.arange(mesh.n_nodes))
+    agg, n_agg = B.gd_coarse_aggregates(mesh, 10 * mesh.n_nodes)
+    assert n_agg == 1 and np.all(agg == 0)
+
+
+def test_small_remnants_are_merged(B):
+    """Brute force on a 1 x n strip of Q4 elements (a path-like node graph): every
+    aggregate ends with at least a quarter of the target nodes."""
+    mesh = I.uniaxial_bc_2d(I.structured_q4(13, 1))
+    for target in (3, 4, 6, 8):
+        agg, n_agg = B.gd_coarse_aggregates(mesh, target)
+        sizes = check_partition(mesh, agg, n_agg)
+        assert sizes.min() >= max(1, target // 4)
+
+
+def test_bad_arguments(B):
+    mesh = I.uniaxial_bc_2d(I.structured_q4(3, 3))
+    with pytest.raises(B.GDError):
+        B.gd_coarse_aggregates(mesh, 0)

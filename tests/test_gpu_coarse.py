@@ -1,0 +1,129 @@
+"""Two-level preconditioner (gd_options.coarse): the iterative solve with the
+coarse level reaches the same solution as the node-block Jacobi solve and as a
+direct sparse LU of the same system, in fewer iterations; Newton paths with and
+without it agree to the Newton tolerance (FP64 2D and 3D, mixed precision), and
+with the oracle."""
+import numpy as np
+import pytest
+
+from gpu_common import rel_err
+from paper_2604_03411_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_03411_gb300 import build as build_mod
+    build_mod.build()
+    import oracle
+    import paper_2604_03411_gb300.binding as B
+    return torch, B, oracle
+
+
+def tight(B, **kw):
+    o = dict(newton_rtol=1e-12, newton_atol=1e-14, krylov_rtol=1e-13, krylov_max=50000)
+    o.update(kw)
+    return B.gd_default_options(**o)
+
+
+def test_coarse_space_is_built(env):
+    torch, B, oracle = env
+    prob = I.config2(n_long=60, n_wide=24)
+    na, nc = B.gd_coarse_info(B.gd_create(prob, B.gd_default_options()))
+    assert na > 0 and na <= nc <= 4 * na and nc <= 1536 * 2
+    assert B.gd_coarse_info(B.gd_create(prob, B.gd_default_options(coarse=0))) == (0, 0)
+    na2, nc2 = B.gd_coarse_info(B.gd_create(prob, B.gd_default_options(coarse=200)))
+    assert 0 < nc2 < nc
+    with pytest.raises(B.GDError):
+        B.gd_create(prob, B.gd_default_options(coarse=5000))
+
+
+def test_two_level_solve_matches_jacobi_and_lu(env):
+    """gd_solve on a damaged notched-plate tangent: with and without the coarse
+    level, against SuperLU; the coarse level needs fewer iterations."""
+    torch, B, oracle = env
+    import scipy.sparse.linalg as spla
+    from gpu_common import gpu_assemble
+    prob = I.config2(n_long=120, n_wide=48)
+    prob.load = prob.load[:6]
+    h2 = B.gd_create(prob, B.gd_default_options(krylov_rtol=1e-12, krylov_max=40000))
+    h1 = B.gd_create(prob, B.gd_default_options(krylov_rtol=1e-12, krylov_max=40000, coarse=0))
+    for _ in range(4):
+        B.gd_newton_step(h2)
+    dofs, kappa = B.gd_get_fields(h2)
+    R, K, _, _ = gpu_assemble(B, torch, h2, dofs, kappa)
+    n = R.size
+    bidx = prob.mesh.bc_node.astype(np.int64) * 3 + prob.mesh.bc_comp
+    free = np.ones(n, bool)
+    free[bidx] = False
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal(n)
+    b[~free] = 0.0
+    vals = torch.tensor(K.data, dtype=torch.float64, device="cuda")
+    bt = torch.tensor(b, device="cuda")
+    Kff = K[free][:, free].tocsc()
+    xr = spla.spsolve(Kff, b[free])
+    out = {}
+    for name, h in (("two-level", h2), ("jacobi", h1)):
+        xt = torch.zeros_like(bt)
+        it, rel = B.gd_solve(h, bt, xt, vals)
+        x = xt.cpu().numpy()
+        assert rel <= 1e-12 and it > 0
+        assert np.all(x[~free] == 0.0)
+        true_rel = np.linalg.norm(Kff @ x[free] - b[free]) / np.linalg.norm(b[free])
+        assert true_rel < 1e-10, (name, true_rel)
+        assert rel_err(x[free], xr) < 1e-6, name
+        out[name] = (it, x)
+    assert out["two-level"][0] < 0.6 * out["jacobi"][0], (out["two-level"][0], out["jacobi"][0])
+    assert rel_err(out["two-level"][1], out["jacobi"][1]) < 1e-6
+
+
+def test_newton_path_with_and_without_coarse_level(env):
+    """FP64 notched plate: the reaction curve and the fields do not depend on the
+    preconditioner beyond the Newton tolerance; both match the oracle."""
+    torch, B, oracle = env
+    prob = I.config2(n_long=40, n_wide=16)
+    prob.load = prob.load[:5]
+    r = {}
+    f = {}
+    for c in (0, 1536, 64):
+        h = B.gd_create(prob, tight(B, coarse=c))
+        r[c], _ = B.gd_run_load_path(h)
+        f[c] = B.gd_get_fields(h)
+    for c in (1536, 64):
+        assert rel_err(r[c], r[0]) < 1e-9, (c, r[c], r[0])
+        assert rel_err(f[c][0], f[0][0]) < 1e-8
+    m = oracle.Model.from_problem(prob)
+    ro = oracle.run_load_path(m, prob.mesh, prob.load, rtol=1e-12, atol=1e-14)
+    assert rel_err(r[1536], ro["reaction"]) < 1e-9
+
+
+def test_hex8_two_level(env):
+    """3D (ndof 4, seven basis columns per aggregate): biaxial HEX8 path with and
+    without the coarse level."""
+    torch, B, oracle = env
+    prob = I.config3(n=6, n_steps=30, precision="fp64")
+    prob.load = prob.load[:3]
+    ra, _ = B.gd_run_load_path(B.gd_create(prob, tight(B)))
+    rb, _ = B.gd_run_load_path(B.gd_create(prob, tight(B, coarse=0)))
+    rc, _ = B.gd_run_load_path(B.gd_create(prob, tight(B, coarse=40)))
+    assert rel_err(ra, rb) < 1e-9 and rel_err(rc, rb) < 1e-9
+
+
+def test_mixed_precision_two_level(env):
+    """GD_MIXED (FP32 inner solves carry the coarse level in FP32) against FP64."""
+    torch, B, oracle = env
+    prob = I.config2(n_long=60, n_wide=24)
+    prob.load = prob.load[:4]
+    r64, _ = B.gd_run_load_path(B.gd_create(prob, tight(B, coarse=0)))
+    h = B.gd_create(prob, B.gd_default_options(precision=B.GD_MIXED))
+    r32, rep = B.gd_run_load_path(h)
+    assert rel_err(r32, r64) < 1e-4
+    h0 = B.gd_create(prob, B.gd_default_options(precision=B.GD_MIXED, coarse=0))
+    r32b, rep0 = B.gd_run_load_path(h0)
+    assert rel_err(r32b, r64) < 1e-4
+    assert rep.total_krylov < rep0.total_krylov
