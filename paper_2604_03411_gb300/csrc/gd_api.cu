@@ -22,10 +22,6 @@ namespace {
 
 thread_local std::string g_create_error;
 
-// most coarse unknowns of the two-level preconditioner: the inversion kernel keeps a
-// panel of 16 coarse rows in shared memory (192 KB at 3072)
-constexpr int kCoarseMax = 3072;
-
 gd_status fail(gd::Handle *H, gd_status st, const std::string &msg)
 {
     if (H) H->err = msg;
@@ -122,7 +118,7 @@ void free_handle(gd::Handle &H)
     dfree(H.yld_tab);
     {
         gd::CoarseSpace &c = H.coarse;
-        void *cp[] = {c.agg, c.coff, c.P, c.Ac, c.X32, c.X64, c.rc, c.cc, c.status};
+        void *cp[] = {c.agg, c.coff, c.node_co, c.P, c.Ac, c.X32, c.X64, c.rc, c.cc, c.status};
         for (void *p : cp) dfree(p);
     }
     for (gd::DevNet &n : H.h_psi_tab) {
@@ -231,8 +227,17 @@ gd_status norms(gd::Handle &H, const double *R, NormPair &out)
 // accept: a solve that stops at its iteration cap or on a breakdown is still
 // returned as GD_OK when its relative residual is at most `accept` (default: rtol,
 // i.e. strict); a non-finite residual is always an error.
+// The coarse inverse of the two-level preconditioner is kept for the next solves of
+// the same kind of matrix (the Newton tangent changes little from one solve to the
+// next, and a slightly stale coarse level is still a good one): it is recomputed
+// after kCoarseReuse solves, for another kind of matrix, and as soon as a solve
+// converges at under 0.7 times the rate (log reduction per iteration) of the solve
+// that computed it.  kind: 0 the Newton tangent, 1 its transpose (adjoint), 2 a
+// caller's matrix (always recomputed, and not kept).
+constexpr int kCoarseReuse = 4;
+
 gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, int &iters, double &rel,
-                 double rtol, bool inner_fp32 = false, double accept = -1.0)
+                 double rtol, bool inner_fp32 = false, double accept = -1.0, int kind = 0)
 {
     gd::KrylovCtx kc;
     kc.n_nodes = H.n_nodes;
@@ -252,6 +257,8 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
     kc.up = H.krylov_up;
     kc.lmax = H.krylov_lmax;
     kc.coarse = H.coarse.nc > 0 ? &H.coarse : nullptr;
+    const bool refresh = kind == 2 || H.coarse_age < 0 || H.coarse_kind != kind || H.coarse_age >= kCoarseReuse;
+    kc.coarse_refresh = refresh;
     GD_CUDA(&H, cudaEventRecord(H.kv0, H.stream));
     bool fp32_vals = H.opt.precision == GD_MIXED;
     if (inner_fp32 && !fp32_vals) {
@@ -271,6 +278,19 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
     H.krylov_ms += kms;
     iters = (int)kout[0];
     rel = kout[1];
+    if (kc.coarse) {
+        const double rate = (iters > 0 && rel > 0.0 && std::isfinite(rel)) ? -std::log(rel) / iters : 0.0;
+        if (kind == 2) {
+            H.coarse_age = -1;
+        } else if (refresh) {
+            H.coarse_age = 1;
+            H.coarse_kind = kind;
+            H.coarse_rate = rate;
+        } else {
+            ++H.coarse_age;
+            if (rate < 0.7 * H.coarse_rate) H.coarse_age = -1;
+        }
+    }
     if (kout[2] != 0.0 && !(kout[2] != 2.0 && std::isfinite(rel) && rel <= std::max(accept, rtol)))
         return fail(&H, GD_ERR_KRYLOV, "BiCGStab stopped (status " + std::to_string((int)kout[2]) +
                                            ", relative residual " + std::to_string(rel) + ")");
@@ -362,7 +382,8 @@ gd_status krylov_true(gd::Handle &H, const double *vals, const double *b, double
     double *res = H.R_trial, *dx = H.kv[8], *y = H.diag;
     int kit = 0;
     double rel = 0.0;
-    gd_status st = krylov(H, vals, b, x, kit, rel, rtol, false, std::max(rtol, 1e-10));
+    const int kind = vals == H.vals_T ? 1 : 0;
+    gd_status st = krylov(H, vals, b, x, kit, rel, rtol, false, std::max(rtol, 1e-10), kind);
     if (st) return st;
     double bn = 0.0;
     GD_CUDA(&H, gd::launch_norm2_free(c, b, H.scal + 30, nullptr));
@@ -378,7 +399,7 @@ gd_status krylov_true(gd::Handle &H, const double *vals, const double *b, double
         GD_CUDA(&H, cudaStreamSynchronize(H.stream));
         if (!std::isfinite(rn)) return fail(&H, GD_ERR_NAN, "non-finite residual in a refined solve");
         if (rn <= std::max(rtol, 1e-15) * bn) return GD_OK;
-        st = krylov(H, vals, res, dx, kit, rel, std::max(rtol * bn / rn, 1e-13), false, 0.5);
+        st = krylov(H, vals, res, dx, kit, rel, std::max(rtol * bn / rn, 1e-13), false, 0.5, kind);
         if (st) return st;
         GD_CUDA(&H, gd::launch_axpy_free(c, x, dx, 1.0));
     }
@@ -1322,7 +1343,7 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
         return fail(nullptr, GD_ERR_ARG, "iteration caps");
     if (o.inner_solve < GD_INNER_AUTO || o.inner_solve > GD_INNER_REFINED)
         return fail(nullptr, GD_ERR_ARG, "inner_solve");
-    if (o.coarse < 0 || o.coarse > kCoarseMax) return fail(nullptr, GD_ERR_ARG, "coarse must be in [0, 3072]");
+    if (o.coarse < 0 || o.coarse > gd::kCoarseMax) return fail(nullptr, GD_ERR_ARG, "coarse must be in [0, 3072]");
 
     const int dim = mesh->dim, nen = dim == 2 ? 4 : 8, ndof = dim + 1;
     const int64_t NN = mesh->n_nodes, NE = mesh->n_elems;
@@ -1505,10 +1526,10 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
         for (int tries = 0; tries < 8; ++tries) {
             na = gd::coarse_aggregate(NN, ndof, H.h_rowptr, H.h_colidx, target, agg);
             gd::coarse_basis(dim, NN, mesh->coords, fixed.data(), agg, na, Pc, coff);
-            if (coff[na] <= kCoarseMax) break;
+            if (coff[na] <= gd::kCoarseMax) break;
             target = target * 3 / 2 + 1;
         }
-        if (coff[na] > kCoarseMax) {
+        if (coff[na] > gd::kCoarseMax) {
             H.err = "coarse space larger than 3072 unknowns";
             return bail(GD_ERR_ARG);
         }
@@ -1518,6 +1539,7 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
             const size_t nc = (size_t)C.nc;
             GD_CREATE_CUDA(dalloc(&C.agg, agg.size()));
             GD_CREATE_CUDA(dalloc(&C.coff, coff.size()));
+            GD_CREATE_CUDA(dalloc(&C.node_co, agg.size()));
             GD_CREATE_CUDA(dalloc(&C.P, Pc.size()));
             GD_CREATE_CUDA(dalloc(&C.Ac, nc * nc));
             GD_CREATE_CUDA(dalloc(&C.X32, nc * nc));
@@ -1527,6 +1549,9 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
             GD_CREATE_CUDA(dalloc(&C.status, 1));
             GD_CREATE_CUDA(cudaMemcpy(C.agg, agg.data(), sizeof(int32_t) * agg.size(), cudaMemcpyHostToDevice));
             GD_CREATE_CUDA(cudaMemcpy(C.coff, coff.data(), sizeof(int32_t) * coff.size(), cudaMemcpyHostToDevice));
+            std::vector<int32_t> nco(agg.size());
+            for (size_t i = 0; i < agg.size(); ++i) nco[i] = coff[agg[i]] * 8 + (coff[agg[i] + 1] - coff[agg[i]]);
+            GD_CREATE_CUDA(cudaMemcpy(C.node_co, nco.data(), sizeof(int32_t) * nco.size(), cudaMemcpyHostToDevice));
             GD_CREATE_CUDA(cudaMemcpy(C.P, Pc.data(), sizeof(float) * Pc.size(), cudaMemcpyHostToDevice));
         }
     }
@@ -1603,6 +1628,7 @@ gd_status gd_set_params(gd_handle *h, const double *theta_psi, const double *the
     }
     GD_CUDA(&H, gd::launch_prep_nets(H.psi, H.yld, H.mat.energy, H.netc, H.stream));
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));
+    H.coarse_age = -1;                       // new networks, new tangents
     return GD_OK;
 }
 
@@ -1674,7 +1700,8 @@ gd_status gd_solve(gd_handle *h, const void *csr_vals, const double *b, double *
     if (!b || !x) return fail(&H, GD_ERR_ARG, "null vector");
     int it = 0;
     double rel = 0.0;
-    gd_status st = krylov(H, csr_vals ? csr_vals : H.vals, b, x, it, rel, H.opt.krylov_rtol);
+    gd_status st = krylov(H, csr_vals ? csr_vals : H.vals, b, x, it, rel, H.opt.krylov_rtol, false, -1.0,
+                          csr_vals ? 2 : 0);
     if (iterations) *iterations = it;
     if (rel_residual) *rel_residual = rel;
     return st;
@@ -1886,6 +1913,7 @@ gd_status gd_set_state(gd_handle *h, const double *dofs, const double *dofs_prev
     H.next_step = next_step;
     H.rec_on = false;
     H.noise_age = 0;
+    H.coarse_age = -1;
     H.have_prev = dofs_prev != nullptr;
     H.load_prev = (double)next_step;
     H.load_prevprev = dofs_prev ? (double)(next_step - 1) : H.load_prev;

@@ -267,87 +267,128 @@ __global__ void __launch_bounds__(256) coarse_assemble_kernel(int64_t n_nodes, c
     }
 }
 
-constexpr int kGjWarps = 16;   // warps per CTA = rows per panel
+constexpr int kGjRows = 16;      // rows per panel
+constexpr int kGjThreads = 512;  // threads per CTA; C columns per thread (nc <= C kGjThreads)
 
 // X = Ac^-1 by blocked in-place Gauss-Jordan elimination with diagonal pivots.
-// Panels of kGjWarps consecutive rows go to the CTAs in turn (panel K to CTA
-// K mod grid), one row per warp.  For panel K its CTA first eliminates the
-// panel's own pivot columns among the panel rows in shared memory (the rows
-// become D^-1 [panel rows], D the panel's diagonal block, with D^-1 in the pivot
-// columns); after a grid barrier every CTA copies the panel to shared memory
-// and updates each of its other rows i by x_i -= x_i[panel columns] * panel,
-// the panel columns of x_i starting from zero.  That is the unblocked in-place
-// elimination reordered by panels (one grid barrier per panel instead of per
-// pivot).
-__global__ void __launch_bounds__(kGjWarps * 32) coarse_invert_kernel(const double *Ac, float *X, double *X64,
-                                                                        int nc, int *status)
+// Panels of kGjRows consecutive rows go to the CTAs in turn (panel K to CTA K
+// mod grid).  For panel K, its CTA first eliminates the panel's own pivot
+// columns among the panel rows: every thread holds the panel rows' values of
+// its columns in registers, and for each pivot the thread holding the pivot
+// column publishes that column through shared memory (the rows become D^-1
+// [panel rows], D the panel's diagonal block, with D^-1 in the pivot columns).
+// After a grid barrier every CTA copies the panel to shared memory and updates
+// each of its own rows i by x_i -= x_i[panel columns] * panel, the panel columns
+// of x_i starting from zero (thread per column, all of the CTA's rows at once,
+// so each panel value read from shared memory serves kGjRows rows).  That is the
+// unblocked in-place elimination reordered by panels, one grid barrier per panel.
+template <int C>
+__global__ void __launch_bounds__(kGjThreads) coarse_invert_kernel(const double *Ac, float *X, double *X64, int nc,
+                                                                   int *status)
 {
     cg::grid_group grid = cg::this_grid();
-    extern __shared__ __align__(16) float pp[];     // [kGjWarps][nc]
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    extern __shared__ __align__(16) float gsh[];
+    float *pp = gsh;                                 // [kGjRows][nc] panel rows
+    float *fc = gsh + kGjRows * nc;                  // [kGjRows] pivot column of the panel rows
+    float *Fs = fc + kGjRows;                        // [kGjRows][kGjRows] panel columns of the CTA's rows
+    const int tid = threadIdx.x;
     const int nb = gridDim.x, b = blockIdx.x;
-    const int64_t tid = (int64_t)b * blockDim.x + threadIdx.x, nt = (int64_t)nb * blockDim.x;
+    const int64_t gtid = (int64_t)b * kGjThreads + tid, nt = (int64_t)nb * kGjThreads;
     const int64_t n2 = (int64_t)nc * nc;
-    for (int64_t k = tid; k < n2; k += nt) X[k] = (float)Ac[k];
+    for (int64_t k = gtid; k < n2; k += nt) X[k] = (float)Ac[k];
     int bad = 0;
-    const int np = (nc + kGjWarps - 1) / kGjWarps;
+    const int np = (nc + kGjRows - 1) / kGjRows;
     grid.sync();
     for (int K = 0; K < np; ++K) {
-        const int r0 = K * kGjWarps, pr = min(kGjWarps, nc - r0);
+        const int r0 = K * kGjRows, pr = min(kGjRows, nc - r0);
         if (K % nb == b) {
-            if (w < pr)
-                for (int j = lane; j < nc; j += 32) pp[w * nc + j] = X[(int64_t)(r0 + w) * nc + j];
-            __syncthreads();
-            for (int t = 0; t < pr; ++t) {
+            float v[C][kGjRows];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int j = tid + c * kGjThreads;
+#pragma unroll
+                for (int w = 0; w < kGjRows; ++w) v[c][w] = (j < nc && w < pr) ? X[(int64_t)(r0 + w) * nc + j] : 0.0f;
+            }
+#pragma unroll
+            for (int t = 0; t < kGjRows; ++t) {
+                if (t >= pr) break;
                 const int col = r0 + t;
-                float piv = pp[t * nc + col];
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    if (tid + c * kGjThreads == col)
+#pragma unroll
+                        for (int w = 0; w < kGjRows; ++w) fc[w] = v[c][w];
+                __syncthreads();
+                float piv = fc[t];
                 if (!(fabsf(piv) > 0.0f) || !isfinite(piv)) {
                     bad = 1;
                     piv = 1.0f;
                 }
                 const float inv = 1.0f / piv;
-                __syncthreads();                     // every thread has read the pivot
-                if (w == t)
-                    for (int j = lane; j < nc; j += 32) pp[t * nc + j] = j == col ? inv : pp[t * nc + j] * inv;
-                __syncthreads();
-                if (w != t && w < pr) {
-                    const float f = pp[w * nc + col];
-                    __syncwarp();                    // the warp read f before its lanes rewrite the row
-                    for (int j = lane; j < nc; j += 32)
-                        pp[w * nc + j] = j == col ? -f * inv : pp[w * nc + j] - f * pp[t * nc + j];
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const int j = tid + c * kGjThreads;
+                    if (j == col) {
+#pragma unroll
+                        for (int w = 0; w < kGjRows; ++w) v[c][w] = w == t ? inv : -fc[w] * inv;
+                    } else {
+                        const float pt = v[c][t] * inv;
+#pragma unroll
+                        for (int w = 0; w < kGjRows; ++w) v[c][w] = w == t ? pt : v[c][w] - fc[w] * pt;
+                    }
                 }
-                __syncthreads();
+                __syncthreads();                     // fc is rewritten by the next pivot
             }
-            if (w < pr)
-                for (int j = lane; j < nc; j += 32) X[(int64_t)(r0 + w) * nc + j] = pp[w * nc + j];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int j = tid + c * kGjThreads;
+                if (j < nc)
+#pragma unroll
+                    for (int w = 0; w < kGjRows; ++w)
+                        if (w < pr) X[(int64_t)(r0 + w) * nc + j] = v[c][w];
+            }
         }
         grid.sync();
-        if (K % nb != b) {
-            for (int t = w; t < pr; t += kGjWarps)
-                for (int j = lane; j < nc; j += 32) pp[t * nc + j] = X[(int64_t)(r0 + t) * nc + j];
-        }
-        __syncthreads();
-        for (int K2 = b; K2 < np; K2 += nb) {
-            const int i = K2 * kGjWarps + w;
-            if (K2 == K || i >= nc) continue;
-            float f[kGjWarps];
+        // this CTA's rows: panels K2 = b, b + grid, ... other than K
+        const bool any = b < np && !(b == K && b + nb >= np);
+        if (any) {
+            for (int64_t k = tid; k < (int64_t)pr * nc; k += kGjThreads) pp[k] = X[(int64_t)r0 * nc + k];
+            for (int K2 = b; K2 < np; K2 += nb) {
+                if (K2 == K) continue;
+                const int i0 = K2 * kGjRows, ri = min(kGjRows, nc - i0);
+                if (tid < kGjRows * kGjRows) {
+                    const int r = tid / kGjRows, t = tid % kGjRows;
+                    Fs[tid] = (r < ri && t < pr) ? X[(int64_t)(i0 + r) * nc + r0 + t] : 0.0f;
+                }
+                __syncthreads();
+                for (int c = 0; c < C; ++c) {
+                    const int j = tid + c * kGjThreads;
+                    if (j >= nc) break;
+                    const bool in_panel = j >= r0 && j < r0 + pr;
+                    float pt[kGjRows];
 #pragma unroll
-            for (int t = 0; t < kGjWarps; ++t) f[t] = t < pr ? X[(int64_t)i * nc + r0 + t] : 0.0f;
-            __syncwarp();
-            for (int j = lane; j < nc; j += 32) {
-                float x = (j >= r0 && j < r0 + pr) ? 0.0f : X[(int64_t)i * nc + j];
+                    for (int t = 0; t < kGjRows; ++t) pt[t] = t < pr ? pp[t * nc + j] : 0.0f;
 #pragma unroll
-                for (int t = 0; t < kGjWarps; ++t)
-                    if (t < pr) x -= f[t] * pp[t * nc + j];
-                X[(int64_t)i * nc + j] = x;
+                    for (int r = 0; r < kGjRows; ++r) {
+                        if (r >= ri) break;
+                        float x = in_panel ? 0.0f : X[(int64_t)(i0 + r) * nc + j];
+                        const float4 *F4 = reinterpret_cast<const float4 *>(Fs + r * kGjRows);
+#pragma unroll
+                        for (int q = 0; q < kGjRows / 4; ++q) {
+                            const float4 f = F4[q];
+                            x -= f.x * pt[4 * q] + f.y * pt[4 * q + 1] + f.z * pt[4 * q + 2] + f.w * pt[4 * q + 3];
+                        }
+                        X[(int64_t)(i0 + r) * nc + j] = x;
+                    }
+                }
+                __syncthreads();                     // Fs (and then pp) are rewritten
             }
         }
-        __syncthreads();                             // pp is rewritten by the next panel
     }
     if (bad) atomicOr(status, 1);
     if (X64) {
         grid.sync();
-        for (int64_t k = tid; k < n2; k += nt) X64[k] = (double)X[k];
+        for (int64_t k = gtid; k < n2; k += nt) X64[k] = (double)X[k];
     }
 }
 
@@ -380,11 +421,19 @@ cudaError_t coarse_setup(const CoarseSpace &cs, int ndof, int64_t n_nodes, const
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = sizeof(float) * (size_t)kGjWarps * nc;
-    e = cudaFuncSetAttribute((const void *)coarse_invert_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int C = (nc + kGjThreads - 1) / kGjThreads;
+    const void *fn = C <= 1 ? (const void *)coarse_invert_kernel<1>
+                     : C == 2 ? (const void *)coarse_invert_kernel<2>
+                     : C == 3 ? (const void *)coarse_invert_kernel<3>
+                     : C == 4 ? (const void *)coarse_invert_kernel<4>
+                     : C == 5 ? (const void *)coarse_invert_kernel<5>
+                              : (const void *)coarse_invert_kernel<6>;
+    if (C > 6) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(float) * ((size_t)kGjRows * nc + kGjRows + kGjRows * kGjRows);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)coarse_invert_kernel, kGjWarps * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kGjThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const double *Ac = cs.Ac;
@@ -393,8 +442,7 @@ cudaError_t coarse_setup(const CoarseSpace &cs, int ndof, int64_t n_nodes, const
     int ncv = nc;
     int *st = cs.status;
     void *args[] = {(void *)&Ac, (void *)&X, (void *)&X64, (void *)&ncv, (void *)&st};
-    return cudaLaunchCooperativeKernel((const void *)coarse_invert_kernel, dim3(num_sms), dim3(kGjWarps * 32), args,
-                                       smem, s);
+    return cudaLaunchCooperativeKernel(fn, dim3(num_sms), dim3(kGjThreads), args, smem, s);
 }
 
 }  // namespace gd

@@ -120,12 +120,14 @@ struct BatchKrylov {
 };
 // Two-level preconditioner (gd_coarse.cu): aggregation coarse space of the node
 // graph, M^-1 = D^-1 + P Ac^-1 P^T with Ac = P^T A P.
+constexpr int kCoarseMax = 3072;     // most coarse unknowns (the inversion keeps 16 rows of them in shared memory)
 struct CoarseSpace {
     int nm = 0;                   // basis slots per aggregate: ndof constants + rotations (4 in 2D, 7 in 3D)
     int n_agg = 0;
     int nc = 0;                   // coarse unknowns (the kept basis columns of all aggregates)
     int32_t *agg = nullptr;       // [n_nodes] aggregate of every node
     int32_t *coff = nullptr;      // [n_agg + 1] first coarse unknown of every aggregate
+    int32_t *node_co = nullptr;   // [n_nodes] 8 x first coarse unknown + count of the node's aggregate
     float *P = nullptr;           // [n_nodes][ndof][nm] basis values (zero beyond the kept columns)
     double *Ac = nullptr;         // [nc][nc] Galerkin matrix
     float *X32 = nullptr;         // [nc][nc] its inverse
@@ -215,6 +217,10 @@ struct Handle {
     int krylov_up = 0;                                   // 0: the precision's default
     int krylov_lmax = 0;                                 // longest CSR row
     CoarseSpace coarse;                                  // two-level preconditioner (nc = 0: off)
+    // reuse of the coarse inverse across solves: solves since it was computed (-1: none
+    // valid), the kind of matrix it belongs to, and the convergence rate of that solve
+    int coarse_age = -1, coarse_kind = -1;
+    double coarse_rate = 0.0;
     // timing
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, kv0 = nullptr, kv1 = nullptr;
     double assembly_ms = 0.0, krylov_ms = 0.0;
@@ -331,6 +337,7 @@ struct KrylovCtx {
     int up = 0;                 // node groups per product round: 1, 2 or 4 (0: 1)
     int lmax = 0;               // longest row (0: rows are not copied to shared memory)
     const CoarseSpace *coarse = nullptr;   // two-level preconditioner (single systems; null: Jacobi only)
+    bool coarse_refresh = true;            // recompute P^T A P and its inverse before the solve
 };
 cudaError_t krylov_solve_batch(const KrylovCtx &c, const BatchKrylov &L, const void *vals, bool fp32_vals,
                                const double *b, double *x, int max_it, bool fp32_vectors);

@@ -46,17 +46,18 @@ struct KArgs {
     // 0 none, 1 column lists, 2 column lists and values; lmax = longest row
     int cache;
     int lmax;
-    // coarse level (single-system kernel with CO): P [n_nodes][NDOF][nm], aggregate of
-    // every node, first coarse unknown of every aggregate, the inverse coarse matrix
+    // coarse level (single-system kernel with CO): P [n_nodes][NDOF][nm], the coarse
+    // unknowns of every node's aggregate, the inverse coarse matrix
     // (FP32 for FP32 vectors, FP64 otherwise), restriction sums [2][nc] and coarse
     // solution [nc] in the vector type, status word of the inversion
     int c_nc;
     const float *c_P;
-    const int32_t *c_agg, *c_off;
+    const int32_t *c_node;    // 8 x first coarse unknown + count, per node
     const float *c_X32;
     const double *c_X64;
     T *c_rc, *c_cc;
     const int *c_status;
+    int c_xs;                 // 1: each CTA keeps its rows of the inverse in shared memory
 };
 
 template <int NDOF>
@@ -74,53 +75,91 @@ __device__ __forceinline__ T warp_sum_t(T v)
 
 // restriction P^T w of the node whose NDOF values sit in lanes base..base+NDOF-1:
 // the node's lanes split its nm coarse components and add them to rc (atomics).
-// Called by every lane of the warp.
-template <int NDOF, int LPN, class V, class T>
-__device__ __forceinline__ void coarse_restrict(const KArgs<V, T> &A, int32_t nd, bool node_ok, int sub, int base,
-                                                T w, T *rc)
+// co: the node's packed coarse unknowns (8 x first + count), pP: its basis values
+// [NDOF][nm] (shared-memory record or global).  Called by every lane of the warp.
+template <int NDOF, int LPN, class T>
+__device__ __forceinline__ void coarse_restrict(bool node_ok, int sub, int base, T w, T *rc, int32_t co,
+                                                const float *pP)
 {
     constexpr int NM = CoarseModes<NDOF>::NM;
     T wk[NDOF];
 #pragma unroll
     for (int k = 0; k < NDOF; ++k) wk[k] = __shfl_sync(0xffffffffu, w, base + k);
     if (!node_ok) return;
-    const int32_t a = A.c_agg[nd], o = A.c_off[a], n = A.c_off[a + 1] - o;
+    const int32_t o = co >> 3, n = co & 7;
     for (int m = sub; m < n; m += LPN) {
         T sum = T(0);
 #pragma unroll
-        for (int k = 0; k < NDOF; ++k) sum += (T)A.c_P[(nd * NDOF + k) * NM + m] * wk[k];
+        for (int k = 0; k < NDOF; ++k) sum += (T)pP[k * NM + m] * wk[k];
         atomicAdd(rc + o + m, sum);
     }
 }
 
-// cc = Ac^-1 rc: one warp per coarse row, lanes along the row
+// cc = Ac^-1 rc: the coarse rows go to the CTAs in turn (rows b, b + grid, ...),
+// up to eight rows of a CTA at once, its threads along the rows.  Each thread
+// first loads all of its rc values (independent loads in flight together) and
+// reuses them for every row.  sX: the CTA's rows in shared memory (row q of the
+// CTA at sX + q nc), or null to read them from the global inverse.
 template <class V, class T>
-__device__ __forceinline__ void coarse_solve(const KArgs<V, T> &A, const T *rc, T *cc, int32_t gw, int32_t nw,
-                                             int lane)
+__device__ __forceinline__ void coarse_solve(const KArgs<V, T> &A, const T *rc, T *cc, const T *sX)
 {
-    const int32_t nc = A.c_nc;
-    for (int32_t k = gw; k < nc; k += nw) {
-        T s = T(0);
-        if constexpr (std::is_same<T, double>::value) {
-            const double *xr = A.c_X64 + (int64_t)k * nc;
-            for (int32_t j = lane; j < nc; j += 32) s += xr[j] * rc[j];
-        } else {
-            const float *xr = A.c_X32 + (int64_t)k * nc;
-            for (int32_t j = lane; j < nc; j += 32) s += xr[j] * rc[j];
+    constexpr int JMAX = (kCoarseMax + kThreads - 1) / kThreads;
+    __shared__ T part[8][kThreads / 32];
+    const int32_t nc = A.c_nc, nb = gridDim.x, b = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    const T *Xg;
+    if constexpr (std::is_same<T, double>::value) Xg = A.c_X64;
+    else Xg = A.c_X32;
+    T rv[JMAX];
+#pragma unroll
+    for (int jj = 0; jj < JMAX; ++jj) {
+        const int32_t j = tid + jj * kThreads;
+        rv[jj] = j < nc ? rc[j] : T(0);
+    }
+    for (int32_t q0 = 0; b + q0 * nb < nc; q0 += 8) {
+        T acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = T(0);
+#pragma unroll
+        for (int jj = 0; jj < JMAX; ++jj) {
+            const int32_t j = tid + jj * kThreads;
+            if (j < nc) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int32_t k = b + (q0 + q) * nb;
+                    if (k < nc) acc[q] += (sX ? sX[(q0 + q) * nc + j] : Xg[(int64_t)k * nc + j]) * rv[jj];
+                }
+            }
         }
-        s = warp_sum_t(s);
-        if (lane == 0) cc[k] = s;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const T s = warp_sum_t(acc[q]);
+            if (lane == 0) part[q][wib] = s;
+        }
+        __syncthreads();
+        if (tid < 8) {
+            const int32_t k = b + (q0 + tid) * nb;
+            if (k < nc) {
+                T s = T(0);
+#pragma unroll
+                for (int w = 0; w < kThreads / 32; ++w) s += part[tid][w];
+                cc[k] = s;
+            }
+        }
+        __syncthreads();
     }
 }
 
-// row sub of P cc for node nd
-template <int NDOF, class V, class T>
-__device__ __forceinline__ T coarse_prolong(const KArgs<V, T> &A, int32_t nd, int sub, const T *cc)
+// row sub of P cc for a node with packed coarse unknowns co and basis values pP
+template <int NDOF, class T>
+__device__ __forceinline__ T coarse_prolong(int sub, const T *cc, int32_t co, const float *pP)
 {
     constexpr int NM = CoarseModes<NDOF>::NM;
-    const int32_t a = A.c_agg[nd], o = A.c_off[a], n = A.c_off[a + 1] - o;
+    const int32_t o = co >> 3, n = co & 7;
     T s = T(0);
-    for (int m = 0; m < n; ++m) s += (T)A.c_P[(nd * NDOF + sub) * NM + m] * cc[o + m];
+#pragma unroll
+    for (int m = 0; m < NM; ++m)
+        if (m < n) s += (T)pP[sub * NM + m] * cc[o + m];
     return s;
 }
 
@@ -324,7 +363,7 @@ __device__ __forceinline__ T node_apply(const T *binv, int64_t nd_wide, bool nod
 }
 
 template <int NDOF, int G, int UP, class V, class T, bool CO = false>
-__global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
+__global__ void __launch_bounds__(kThreads, 2) bicgstab3_kernel(KArgs<V, T> A)
 {
     using M = RowMap<NDOF, G, T>;
     constexpr int LPN = M::LPN, NPW = M::NPW;
@@ -349,16 +388,6 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
         rc1 = A.c_rc + A.c_nc;
         cc = A.c_cc;
     }
-    auto coarse_apply = [&](T *rc, T *dst) {
-        coarse_solve<V, T>(A, rc, cc, gw, nw, lane);
-        grid.sync();
-        for (int32_t ps = 0; ps < passes; ++ps) {
-            const int32_t nd = (gw + ps * nw) * NPW + slot;
-            if (slot < NPW && nd < n_nodes && sub < NDOF) dst[nd * NDOF + sub] += coarse_prolong<NDOF, V, T>(A, nd, sub, cc);
-        }
-        for (int32_t k = blockIdx.x * kThreads + threadIdx.x; k < A.c_nc; k += gridDim.x * kThreads) rc[k] = T(0);
-        grid.sync();
-    };
     // vector roles: r (also s), rh, p, v, q, t, y = M^-1 v (read by phase 2's product),
     // w = M^-1 r (read by phase 4's product), u.  y and w must differ: phase 1 of the
     // next iteration writes y with no barrier after phase 4, whose product still reads
@@ -374,6 +403,70 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
     int32_t *scol = reinterpret_cast<int32_t *>(kdyn);
     V *sval = reinterpret_cast<V *>(kdyn + ((((size_t)n_rec * (A.lmax + 1) * sizeof(int32_t)) + 15) & ~(size_t)15));
     auto rec_of = [&](int32_t ps) { return (ps * (kThreads / 32) + wib) * NPW + slot; };
+    // coarse data of the same records (CO with a row cache): packed coarse unknowns,
+    // then the basis values [NDOF][nm] of every record
+    constexpr int NM = CoarseModes<NDOF>::NM;
+    const bool cco = co && A.cache > 0;
+    int32_t *sco = nullptr;
+    float *sP = nullptr;
+    if (cco) {
+        size_t off = (((size_t)n_rec * (A.lmax + 1) * sizeof(int32_t)) + 15) & ~(size_t)15;
+        if (A.cache == 2) off += ((size_t)n_rec * NDOF * A.lmax * sizeof(V) + 15) & ~(size_t)15;
+        sco = reinterpret_cast<int32_t *>(kdyn + off);
+        sP = reinterpret_cast<float *>(kdyn + off + (((size_t)n_rec * sizeof(int32_t) + 15) & ~(size_t)15));
+    }
+    // the CTA's rows of the coarse inverse (CO with c_xs): after the coarse records
+    T *sX = nullptr;
+    if constexpr (CO) {
+        if (co && A.c_xs) {
+            size_t off = (((size_t)n_rec * (A.lmax + 1) * sizeof(int32_t)) + 15) & ~(size_t)15;
+            if (A.cache == 2) off += ((size_t)n_rec * NDOF * A.lmax * sizeof(V) + 15) & ~(size_t)15;
+            off += (((size_t)n_rec * sizeof(int32_t) + 15) & ~(size_t)15) +
+                   (((size_t)n_rec * NDOF * NM * sizeof(float) + 15) & ~(size_t)15);
+            sX = reinterpret_cast<T *>(kdyn + off);
+            const T *Xg;
+            if constexpr (std::is_same<T, double>::value) Xg = A.c_X64;
+            else Xg = A.c_X32;
+            const int32_t nc = A.c_nc;
+            for (int32_t q = 0; blockIdx.x + q * gridDim.x < nc; ++q)
+                for (int32_t j = threadIdx.x; j < nc; j += kThreads)
+                    sX[(size_t)q * nc + j] = Xg[(int64_t)(blockIdx.x + q * gridDim.x) * nc + j];
+            __syncthreads();
+        }
+    }
+    // a node's coarse data (node_ok lanes only)
+    auto cnode = [&](int32_t ps, int32_t nd, int32_t &c, const float *&pp) {
+        if (cco) {
+            const int32_t rec = rec_of(ps);
+            c = sco[rec];
+            pp = sP + (size_t)rec * NDOF * NM;
+        } else {
+            c = A.c_node[nd];
+            pp = A.c_P + (size_t)nd * NDOF * NM;
+        }
+    };
+    auto coarse_apply = [&](T *rc, T *dst) {
+        coarse_solve<V, T>(A, rc, cc, sX);
+        grid.sync();
+        for (int32_t ps = 0; ps < passes; ++ps) {
+            const int32_t nd = (gw + ps * nw) * NPW + slot;
+            if (slot < NPW && nd < n_nodes && sub < NDOF) {
+                int32_t c;
+                const float *pp;
+                cnode(ps, nd, c, pp);
+                dst[nd * NDOF + sub] += coarse_prolong<NDOF, T>(sub, cc, c, pp);
+            }
+        }
+        for (int32_t k = blockIdx.x * kThreads + threadIdx.x; k < A.c_nc; k += gridDim.x * kThreads) rc[k] = T(0);
+        grid.sync();
+    };
+    // restriction of a node value held by this lane (every lane calls it)
+    auto restrict_node = [&](int32_t ps, int32_t nd, bool node_ok, T val, T *rc) {
+        int32_t c = 0;
+        const float *pp = nullptr;
+        if (node_ok) cnode(ps, nd, c, pp);
+        coarse_restrict<NDOF, LPN, T>(node_ok, sub, nbase, val, rc, c, pp);
+    };
     if (A.cache > 0) {
         for (int32_t ps = 0; ps < passes; ++ps) {
             const int32_t nd = (gw + ps * nw) * NPW + slot;
@@ -388,6 +481,10 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                     V *cv = sval + (size_t)rec * NDOF * A.lmax;
                     for (int i = 0; i < NDOF; ++i)
                         for (int32_t j = sub; j < len; j += LPN) cv[i * A.lmax + j] = A.vals[base + i * len + j];
+                }
+                if (cco) {
+                    if (sub == 0) sco[rec] = A.c_node[nd];
+                    for (int i = sub; i < NDOF * NM; i += LPN) sP[(size_t)rec * NDOF * NM + i] = A.c_P[(size_t)nd * NDOF * NM + i];
                 }
             }
         }
@@ -408,7 +505,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
             const bool fx = own ? A.fixed[row] != 0 : true;
             const T bv = (own && !fx) ? (T)A.b[row] : T(0);
             const T yv = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, bv, fx);
-            if (co) coarse_restrict<NDOF, LPN, V, T>(A, nd, node_ok, sub, nbase, bv, rc0);
+            if (co) restrict_node(ps, nd, node_ok, bv, rc0);
             if (own) {
                 r[row] = bv;
                 rh[row] = bv;
@@ -482,7 +579,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                         s1.add(rh[row], vn);
                     }
                     const T yv = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, vn, fx);
-                    if (co) coarse_restrict<NDOF, LPN, V, T>(A, nd, node_ok, sub, nbase, vn, rc0);
+                    if (co) restrict_node(ps, nd, node_ok, vn, rc0);
                     if (own) y[row] = yv;
                 }
                 double pv[1] = {s1.value()};
@@ -563,7 +660,7 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
                         prr.add(rn, rn);
                     }
                     const T wn = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, rn, fx);
-                    if (co) coarse_restrict<NDOF, LPN, V, T>(A, nd, node_ok, sub, nbase, rn, rc1);
+                    if (co) restrict_node(ps, nd, node_ok, rn, rc1);
                     if (own) wv[row] = wn;
                 }
                 double pv[2] = {prhr.value(), prr.value()};
@@ -639,17 +736,21 @@ __global__ void __launch_bounds__(kThreads) bicgstab3_kernel(KArgs<V, T> A)
         const bool fx = own ? A.fixed[row] != 0 : true;
         const T xv = own ? xt[row] : T(0);
         const T xo = node_apply<NDOF, T>(A.binv, nd, node_ok, sub, nbase, xv, fx);
-        if (co) coarse_restrict<NDOF, LPN, V, T>(A, nd, node_ok, sub, nbase, xv, rc0);
+        if (co) restrict_node(ps, nd, node_ok, xv, rc0);
         if (own) A.x_out[row] = (double)xo;
     }
     if (co) {
         grid.sync();
-        coarse_solve<V, T>(A, rc0, cc, gw, nw, lane);
+        coarse_solve<V, T>(A, rc0, cc, sX);
         grid.sync();
         for (int32_t ps = 0; ps < passes; ++ps) {
             const int32_t nd = (gw + ps * nw) * NPW + slot;
-            if (slot < NPW && nd < n_nodes && sub < NDOF)
-                A.x_out[nd * NDOF + sub] += (double)coarse_prolong<NDOF, V, T>(A, nd, sub, cc);
+            if (slot < NPW && nd < n_nodes && sub < NDOF) {
+                int32_t c;
+                const float *pp;
+                cnode(ps, nd, c, pp);
+                A.x_out[nd * NDOF + sub] += (double)coarse_prolong<NDOF, T>(sub, cc, c, pp);
+            }
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1213,7 +1314,7 @@ cudaError_t solve_t(const KrylovCtx &c, const V *vals, const double *b, double *
     A.lmax = 0;
     A.c_nc = 0;
     A.c_P = nullptr;
-    A.c_agg = A.c_off = nullptr;
+    A.c_node = nullptr;
     A.c_X32 = nullptr;
     A.c_X64 = nullptr;
     A.c_rc = A.c_cc = nullptr;
@@ -1221,15 +1322,16 @@ cudaError_t solve_t(const KrylovCtx &c, const V *vals, const double *b, double *
     const bool co = c.coarse && c.coarse->nc > 0;
     if (co) {
         const CoarseSpace &cs = *c.coarse;
-        e = coarse_setup(cs, NDOF, c.n_nodes, c.rowptr, c.colidx, vals, std::is_same<V, float>::value,
-                         std::is_same<T, double>::value, c.num_sms, c.stream);
-        if (e != cudaSuccess) return e;
+        if (c.coarse_refresh) {
+            e = coarse_setup(cs, NDOF, c.n_nodes, c.rowptr, c.colidx, vals, std::is_same<V, float>::value, true,
+                             c.num_sms, c.stream);
+            if (e != cudaSuccess) return e;
+        }
         e = cudaMemsetAsync(cs.rc, 0, sizeof(T) * 2 * (size_t)cs.nc, c.stream);
         if (e != cudaSuccess) return e;
         A.c_nc = cs.nc;
         A.c_P = cs.P;
-        A.c_agg = cs.agg;
-        A.c_off = cs.coff;
+        A.c_node = cs.node_co;
         A.c_X32 = cs.X32;
         A.c_X64 = cs.X64;
         A.c_rc = (T *)cs.rc;
@@ -1257,10 +1359,23 @@ cudaError_t solve_t(const KrylovCtx &c, const V *vals, const double *b, double *
         const int64_t passes = (c.n_nodes + nw * M::NPW - 1) / (nw * M::NPW);
         const int64_t n_rec = passes * (kThreads / 32) * M::NPW;
         const size_t colb = ((size_t)n_rec * (c.lmax + 1) * sizeof(int32_t) + 15) & ~(size_t)15;
-        const size_t valb = (size_t)n_rec * NDOF * c.lmax * sizeof(V);
+        const size_t valb = ((size_t)n_rec * NDOF * c.lmax * sizeof(V) + 15) & ~(size_t)15;
+        // the two-level kernel keeps every record's coarse data beside its row
+        const size_t cob = co ? (((size_t)n_rec * sizeof(int32_t) + 15) & ~(size_t)15) +
+                                    (((size_t)n_rec * NDOF * CoarseModes<NDOF>::NM * sizeof(float) + 15) & ~(size_t)15)
+                              : 0;
+        // and, for FP32 vectors where it fits, each CTA's rows of the coarse inverse (with
+        // FP64 rows the shared memory they take from the L1 cache slows the products more
+        // than it speeds the coarse solve: measured 108 against 100 us per iteration)
+        const bool want_xs = co && std::is_same<T, float>::value;
+        const size_t xsb = want_xs ? (size_t)((c.coarse->nc + c.blocks - 1) / c.blocks) * c.coarse->nc * sizeof(T) : 0;
         const int need = (c.blocks + c.num_sms - 1) / c.num_sms;      // CTAs per SM of this grid
-        for (int mode = 2; mode >= 1 && A.cache == 0; --mode) {
-            const size_t sm = colb + (mode == 2 ? valb : 0);
+        // preference: values and inverse rows, columns and inverse rows, values, columns
+        const int modes[4][2] = {{2, 1}, {1, 1}, {2, 0}, {1, 0}};
+        for (int mi = 0; mi < 4 && A.cache == 0; ++mi) {
+            const int mode = modes[mi][0], xs = want_xs ? modes[mi][1] : 0;
+            if (!want_xs && modes[mi][1]) continue;
+            const size_t sm = colb + (mode == 2 ? valb : 0) + cob + (xs ? xsb : 0);
             if (sm > 200 * 1024) continue;
             if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
                 cudaGetLastError();
@@ -1274,6 +1389,7 @@ cudaError_t solve_t(const KrylovCtx &c, const V *vals, const double *b, double *
             if (per_sm >= need) {
                 A.cache = mode;
                 A.lmax = c.lmax;
+                A.c_xs = xs;
                 smem = sm;
             }
         }
