@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--inner", default="auto", choices=["auto", "fp64", "refined"],
                     help="Newton inner-solve policy (gd_options.inner_solve)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--coarse", type=int, default=None,
+                    help="coarse unknowns of the two-level preconditioner (gd_options.coarse; 0 = Jacobi only)")
     return ap.parse_args()
 
 
@@ -201,6 +203,8 @@ def mixed_comparison(args, B, torch, prob, batch, stream, flush, reps64, n_qp):
     Newton-step time, and the reaction-force error against the FP64 run step by step."""
     import numpy as np
     opts = B.gd_default_options(precision=B.GD_MIXED, cuda_stream=stream.cuda_stream)
+    if args.coarse is not None:
+        opts.coarse = args.coarse
     h = B.gd_create_batch(prob, opts) if batch else B.gd_create(prob, opts)
     for _ in range(args.warmup):
         B.gd_newton_step(h)
@@ -256,7 +260,10 @@ def run_gd(args):
     prec = B.GD_FP64 if args.precision == "fp64" else B.GD_MIXED
     opts = B.gd_default_options(precision=prec, cuda_stream=stream.cuda_stream, inner_solve={"auto": B.GD_INNER_AUTO, "fp64": B.GD_INNER_FP64,
                                              "refined": B.GD_INNER_REFINED}[args.inner])
+    if args.coarse is not None:
+        opts.coarse = args.coarse
     h = B.gd_create_batch(prob, opts) if batch else B.gd_create(prob, opts)
+    coarse_aggs, coarse_n = B.gd_coarse_info(h)
     probs = prob if batch else [prob]
     n_qp = desc["qp"]
     n_path = h.meta["n_steps"]
@@ -418,7 +425,7 @@ def run_gd(args):
         "data": "synthetic (seeded mesh, seeded ICNN weights)",
         "config": dict(desc, precision=args.precision,
                        parallelism=f"specimen-shards{world}" if batch else f"replicas{world}",
-                       inner_solve=args.inner,
+                       inner_solve=args.inner, coarse_unknowns=coarse_n, coarse_aggregates=coarse_aggs,
                        l2="flushed between timed steps (512 MB write)"),
         "newton_step_ms": total_ms / max(newton, 1),
         "newton_iterations": newton, "krylov_iterations": krylov,

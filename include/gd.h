@@ -138,13 +138,15 @@ typedef struct gd_options {
                                   BiCGStab always.  GD_INNER_REFINED: FP32 BiCGStab cycles
                                   refined by FP64 residuals b - K x until the FP64 tolerance
                                   is met.  A failed FP32 solve falls back to FP64.          */
-    int32_t coarse;            /* single-specimen handles: target number of coarse unknowns of
-                                  the two-level preconditioner M^-1 = D^-1 + P (P^T K P)^-1 P^T
-                                  (D the node-block diagonal, P constants and rigid rotations
-                                  on aggregates of the node graph); default 1536, at most
-                                  3072, 0 = node-block Jacobi only.  The preconditioner
-                                  changes the iteration count, not the solution.  Batches
-                                  ignore it.                                                */
+    int32_t coarse;            /* target number of coarse unknowns of the two-level
+                                  preconditioner M^-1 = D^-1 + P (P^T K P)^-1 P^T (D the
+                                  node-block diagonal, P constants and rigid rotations on
+                                  aggregates of the node graph); default 1536, at most 3072,
+                                  0 = node-block Jacobi only.  The preconditioner changes the
+                                  iteration count, not the solution.  A batch with a coarse
+                                  level (aggregates never span two specimens) solves its
+                                  union system in one recurrence instead of per-specimen
+                                  recurrences.                                              */
 } gd_options;
 
 typedef struct gd_newton_report {

@@ -742,11 +742,12 @@ gd_status newton_batch(gd::Handle &H, gd_newton_report &rep)
         if ((st = set_coef(H, coef))) return st;
         GD_CUDA(&H, gd::launch_scale_spec(H.n_dofs, H.ndof, rhs, H.R, H.d_coef, H.node_spec, H.fixed, 0, H.stream));
         ++H.launches;
-        if (H.bk_ok && H.opt.inner_solve != GD_INNER_REFINED) {
+        if (H.bk_ok && H.opt.inner_solve != GD_INNER_REFINED && H.coarse.nc == 0) {
             // every specimen runs its own recurrences to its own tolerance
             if ((st = solve_direction_batch(H, rhs, delta, eta_s, rep))) return st;
         } else {
-            // one union solve: ||r_s|| <= ||r|| <= eta ||b|| with eta = min_s eta_s ||b_s|| / ||b||
+            // one union solve (the two-level preconditioner's coarse level has aggregates in
+            // every specimen): ||r_s|| <= ||r|| <= eta ||b|| with eta = min_s eta_s ||b_s|| / ||b||
             const double eta = std::max(1e-14, need / std::sqrt(bn2));
             if ((st = solve_direction(H, rhs, delta, eta, rep))) return st;
         }
@@ -1514,7 +1515,8 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
     if (n_spec > 1) {
         gd_status sb = build_batch_krylov(H);
         if (sb) return bail(sb);
-    } else if (o.coarse > 0) {
+    }
+    if (o.coarse > 0) {
         // two-level preconditioner: aggregates sized so the coarse unknowns come near
         // the target (larger aggregates when the kept modes exceed the cap)
         gd::CoarseSpace &C = H.coarse;
