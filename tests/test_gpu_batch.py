@@ -58,11 +58,14 @@ def test_batch_layout(env):
         B.gd_backward(h, np.ones(n_steps * len(probs)))
 
 
-@pytest.mark.parametrize("energy", [I.ENERGY_ICNN_RAW, I.ENERGY_ICNN_ISO])
-def test_batch_matches_individual_runs_and_oracle(env, energy):
+@pytest.mark.parametrize("energy,coarse", [(I.ENERGY_ICNN_RAW, None), (I.ENERGY_ICNN_ISO, None),
+                                           (I.ENERGY_ICNN_RAW, 0)])
+def test_batch_matches_individual_runs_and_oracle(env, energy, coarse):
+    """coarse None: the default two-level union solve; 0: per-specimen Jacobi
+    recurrences (bicgstab3_batch_kernel)."""
     torch, B, oracle = env
     probs = specimens(energy)
-    h = B.gd_create_batch(probs, opts(B))
+    h = B.gd_create_batch(probs, opts(B) if coarse is None else opts(B, coarse=coarse))
     reac, rep = B.gd_run_load_path(h)
     no, eo, n_steps = B.gd_batch_layout(h)
     d_all, k_all = B.gd_get_fields(h)
@@ -85,12 +88,14 @@ def test_batch_matches_individual_runs_and_oracle(env, energy):
         assert rel(reac[:n, s], ro["reaction"]) < 1e-9, (s, reac[:n, s], ro["reaction"])
 
 
-def test_batch_mixed_precision(env):
+@pytest.mark.parametrize("coarse", [None, 0])
+def test_batch_mixed_precision(env, coarse):
     """GD_MIXED batch against the FP64 batch at the mixed path tolerance."""
     torch, B, oracle = env
     probs = specimens()
-    r64, _ = B.gd_run_load_path(B.gd_create_batch(probs, opts(B)))
-    h = B.gd_create_batch(probs, opts(B, precision=B.GD_MIXED))
+    extra = {} if coarse is None else {"coarse": coarse}
+    r64, _ = B.gd_run_load_path(B.gd_create_batch(probs, opts(B, **extra)))
+    h = B.gd_create_batch(probs, opts(B, precision=B.GD_MIXED, **extra))
     r32, _ = B.gd_run_load_path(h)
     for s in range(len(probs)):
         assert rel(r32[:, s], r64[:, s]) < 1e-4, (s, r32[:, s], r64[:, s])
