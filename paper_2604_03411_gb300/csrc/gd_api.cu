@@ -164,6 +164,7 @@ gd::AsmArgs asm_args(gd::Handle &H, const double *dofs, const double *kappa_n, d
     a.vals = (tangent && H.opt.precision == GD_FP64) ? (double *)vals : nullptr;
     a.vals32 = (tangent && H.opt.precision == GD_MIXED) ? (float *)vals : nullptr;
     a.kappa_new = kappa_out;
+    a.kappa_guess = nullptr;
     a.loading = loading;
     a.slot = H.slot;
     a.rowptr = H.rowptr;
@@ -181,8 +182,11 @@ gd::AsmArgs asm_args(gd::Handle &H, const double *dofs, const double *kappa_n, d
 }
 
 // one assembly pass with timing; counters[0] = local failures, [1] = loading points
+// guess: a nearby solution of the local updates (the current Newton iterate's kappa),
+// where the local solves of the loading points start; null: at kappa_n
 gd_status assemble_pass(gd::Handle &H, const double *dofs, const double *kappa_n, double *R, void *vals,
-                        double *kappa_out, int8_t *loading, int tangent, bool force_fp64 = false)
+                        double *kappa_out, int8_t *loading, int tangent, bool force_fp64 = false,
+                        const double *guess = nullptr)
 {
     const size_t vbytes = H.opt.precision == GD_FP64 ? sizeof(double) : sizeof(float);
     if (force_fp64) tangent = 0;
@@ -191,6 +195,7 @@ gd_status assemble_pass(gd::Handle &H, const double *dofs, const double *kappa_n
     GD_CUDA(&H, cudaMemsetAsync(H.counters, 0, sizeof(int) * 8, H.stream));
     GD_CUDA(&H, cudaEventRecord(H.ev0, H.stream));
     gd::AsmArgs a = asm_args(H, dofs, kappa_n, R, vals, kappa_out, loading, tangent);
+    a.kappa_guess = guess;
     if (H.opt.precision == GD_FP64 || force_fp64)
         GD_CUDA(&H, gd::launch_assemble_fp64(H.dim, a, H.num_sms, H.stream, H.asm_tune));
     else GD_CUDA(&H, gd::launch_assemble_fp32(H.dim, a, H.num_sms, H.stream, H.asm_tune));
@@ -508,7 +513,8 @@ gd_status solve_direction_batch(gd::Handle &H, const double *rhs, double *delta,
 // the Newton test is not asked to go below twice this level.
 gd_status mixed_noise(gd::Handle &H, const double *R32, std::vector<double> &noise)
 {
-    gd_status st = assemble_pass(H, H.w_dofs, H.kappa, H.R_trial, nullptr, nullptr, nullptr, 0, true);
+    // the local solves start from the FP32 pass's kappa at this iterate
+    gd_status st = assemble_pass(H, H.w_dofs, H.kappa, H.R_trial, nullptr, nullptr, nullptr, 0, true, H.kappa_trial);
     if (st) return st;
     H.assembly_ms += elapsed_ms(H);
     gd::SolverCtx c = solver_ctx(H, nullptr);
@@ -619,7 +625,8 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
             GD_CUDA(&H, cudaMemcpyAsync(H.w_trial, H.w_dofs, sizeof(double) * H.n_dofs, cudaMemcpyDeviceToDevice,
                                         H.stream));
             GD_CUDA(&H, gd::launch_axpy_free(c, H.w_trial, delta, alpha));
-            if ((st = assemble_pass(H, H.w_trial, H.kappa, H.R_trial, H.vals_trial, H.kappa_trial2, H.loading2, 1)))
+            if ((st = assemble_pass(H, H.w_trial, H.kappa, H.R_trial, H.vals_trial, H.kappa_trial2, H.loading2, 1, false,
+                                     H.kappa_trial)))
                 return st;
             if ((st = norms(H, H.R_trial, nr))) return st;
             H.assembly_ms += elapsed_ms(H);
@@ -778,7 +785,8 @@ gd_status newton_batch(gd::Handle &H, gd_newton_report &rep)
             GD_CUDA(&H, gd::launch_scale_spec(H.n_dofs, H.ndof, H.w_trial, delta, H.d_coef, H.node_spec, H.fixed, 1,
                                               H.stream));
             ++H.launches;
-            if ((st = assemble_pass(H, H.w_trial, H.kappa, H.R_trial, H.vals_trial, H.kappa_trial2, H.loading2, 1)))
+            if ((st = assemble_pass(H, H.w_trial, H.kappa, H.R_trial, H.vals_trial, H.kappa_trial2, H.loading2, 1, false,
+                                     H.kappa_trial)))
                 return st;
             if ((st = norms_batch(H, H.R_trial, nt, ntx))) return st;
             H.assembly_ms += elapsed_ms(H);

@@ -282,41 +282,58 @@ __global__ void __launch_bounds__(32 * KW) asm_fp64_kernel(AsmArgs A)
             double kappa = kn, fail = 0.0, loading = 0.0;
             if (r > 0.0) {
                 loading = 1.0;
-                double lo = kn, step = r > 1e-12 ? r : 1e-12, hi = kn + step;
-                int grow = 0;
-                double rh, drh, gph;
-                r_slope(A.mat, yn, ncp, ppe, pphi, hi, rh, drh, gph, sBuf, lane);
-                ++n_eval;
-                while (rh > 0.0 && grow < 200) {
-                    lo = hi;
-                    step *= 2.0;
-                    hi = kn + step;
-                    ++grow;
-                    r_slope(A.mat, yn, ncp, ppe, pphi, hi, rh, drh, gph, sBuf, lane);
+                // Newton iteration on r(kappa) = G(q(kappa)) - kappa from kappa_n (r > 0 there)
+                // or from the warm-start guess, bracketing lazily: lo keeps the last point with
+                // r > 0; once a point with r <= 0 is met it becomes hi and the iteration turns
+                // into the safeguarded Newton-bisection on [lo, hi].  Before that, a step that
+                // is not a forward Newton step (slope >= 0) probes ahead geometrically.
+                const double kg = A.kappa_guess ? (double)__ldg(A.kappa_guess + e0 * NQ + p) : kn;
+                if (kg > kn && isfinite(kg)) {
+                    kappa = kg;
+                    r_slope(A.mat, yn, ncp, ppe, pphi, kappa, r, dr, Gp, sBuf, lane);
                     ++n_eval;
                 }
-                if (grow >= 200) fail = 1.0;
-                kappa = lo;
-                r_slope(A.mat, yn, ncp, ppe, pphi, kappa, r, dr, Gp, sBuf, lane);
-                ++n_eval;
-                double dx_prev = hi - lo, dx = dx_prev;
+                double lo = kn, hi = kn;
+                bool have_hi = false;
+                if (r > 0.0) lo = kappa;
+                else {
+                    hi = kappa;
+                    have_hi = true;
+                }
+                double dx_prev = have_hi ? hi - lo : 1.0e30, dx = dx_prev;
                 int it;
                 for (it = 0; it < m.local_max; ++it) {
-                    double scale = fabs(kappa) > 1.0 ? fabs(kappa) : 1.0;
-                    if (fabs(r) <= 1e-13 * scale || (hi - lo) <= 4.0 * 2.220446049250313e-16 * scale) break;
-                    double newton = kappa - r / dr;
-                    bool take = (newton > lo) && (newton < hi) && (fabs(2.0 * r) <= fabs(dx_prev * dr));
+                    const double scale = fabs(kappa) > 1.0 ? fabs(kappa) : 1.0;
+                    if (fabs(r) <= 1e-13 * scale || (have_hi && (hi - lo) <= 4.0 * 2.220446049250313e-16 * scale)) break;
+                    const double newton = kappa - r / dr;
+                    bool take;
+                    if (have_hi) {
+                        take = (newton > lo) && (newton < hi) && (fabs(2.0 * r) <= fabs(dx_prev * dr));
+                    } else {
+                        // forward Newton step, at most a few times the distance covered so far
+                        const double cap = 4.0 * ((double)(r > 1e-12 ? r : 1e-12) + (kappa - kn));
+                        take = dr < 0.0 && newton > lo && (newton - kappa) <= cap;
+                    }
                     dx_prev = dx;
                     if (take) {
                         dx = kappa - newton;
                         kappa = newton;
-                    } else {
+                    } else if (have_hi) {
                         dx = 0.5 * (hi - lo);
                         kappa = lo + dx;
+                    } else {
+                        const double step = 2.0 * ((kappa - kn) > (r > 1e-12 ? r : 1e-12) ? (kappa - kn) : (r > 1e-12 ? r : 1e-12));
+                        dx = step;
+                        kappa = lo + step;
                     }
                     r_slope(A.mat, yn, ncp, ppe, pphi, kappa, r, dr, Gp, sBuf, lane);
                     ++n_eval;
-                    if (r > 0.0) lo = kappa; else hi = kappa;
+                    if (r > 0.0) {
+                        lo = kappa;
+                    } else {
+                        hi = kappa;
+                        have_hi = true;
+                    }
                 }
                 if (it >= m.local_max) fail = 1.0;
             }

@@ -68,6 +68,14 @@ __device__ __forceinline__ float sigm(float v)
     float r = 1.0f / (1.0f + e);
     return v >= 0.0f ? r : e * r;
 }
+// softplus(v) and its derivative sigmoid(v) from one exponential
+__device__ __forceinline__ void sp_sig(float v, float &sp, float &sg)
+{
+    const float e = expf(-fabsf(v));
+    sp = fmaxf(v, 0.0f) + log1pf(e);
+    const float r = 1.0f / (1.0f + e);
+    sg = v >= 0.0f ? r : e * r;
+}
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll
@@ -173,8 +181,9 @@ __device__ void psi_net_unit(const DevNet &net, const float *x, float *out10, fl
         if (j < w) {
             float a0 = __ldg(W1 + 3 * j), a1 = __ldg(W1 + 3 * j + 1), a2 = __ldg(W1 + 3 * j + 2);
             float h = __ldg(b1 + j) + a0 * x[0] + a1 * x[1] + a2 * x[2];
-            float sg = sigm(h);
-            sS[j] = softplus(h);
+            float sg, spv;
+            sp_sig(h, spv, sg);
+            sS[j] = spv;
             sD0[j] = sg * a0;
             sD1[j] = sg * a1;
             sD2[j] = sg * a2;
@@ -200,9 +209,11 @@ __device__ void psi_net_unit(const DevNet &net, const float *x, float *out10, fl
                 g1 += wkj * sD1[j];
                 g2 += wkj * sD2[j];
             }
-            float sg = sigm(h), wk = __ldg(w3 + k);
+            float sg, spv;
+            sp_sig(h, spv, sg);
+            const float wk = __ldg(w3 + k);
             float e2 = wk * sg * (1.0f - sg);
-            acc[0] += wk * softplus(h);
+            acc[0] += wk * spv;
             acc[1] += wk * sg * g0;
             acc[2] += wk * sg * g1;
             acc[3] += wk * sg * g2;
@@ -260,8 +271,10 @@ __device__ void yield_unit(const DevNet &net, const NcF &nc, float q, float &G, 
         if (j < w) {
             float a = __ldg(V1 + j);
             float h = __ldg(c1 + j) + a * q;
-            sS[j] = softplus(h);
-            sT[j] = sigm(h) * a;
+            float spv, sg;
+            sp_sig(h, spv, sg);
+            sS[j] = spv;
+            sT[j] = sg * a;
         }
     }
     __syncwarp();
@@ -279,8 +292,10 @@ __device__ void yield_unit(const DevNet &net, const NcF &nc, float q, float &G, 
                 g += wkj * sT[j];
             }
             float vk = __ldg(v3 + k);
-            n0 += vk * softplus(h);
-            n1 += vk * sigm(h) * g;
+            float spv, sg;
+            sp_sig(h, spv, sg);
+            n0 += vk * spv;
+            n1 += vk * sg * g;
         }
     }
     n0 = warp_sum(n0);
@@ -564,41 +579,58 @@ __global__ void __launch_bounds__(32 * KW) asm_fp32_kernel(AsmArgs A)
             float kappa = kn, fail = 0.0f, loading = 0.0f;
             if (phi_trial > 0.0) {
                 loading = 1.0f;
-                float lo = kn, step = r > 1e-12 ? r : 1e-12, hi = kn + step;
-                int grow = 0;
-                float rh, drh, gph;
-                r_slope(yn, m, ncp, ppe, pphi, hi, rh, drh, gph, sBuf, lane);
-                ++n_eval;
-                while (rh > 0.0f && grow < 200) {
-                    lo = hi;
-                    step *= 2.0f;
-                    hi = kn + step;
-                    ++grow;
-                    r_slope(yn, m, ncp, ppe, pphi, hi, rh, drh, gph, sBuf, lane);
+                // Newton iteration on r(kappa) = G(q(kappa)) - kappa from kappa_n (r > 0 there)
+                // or from the warm-start guess, bracketing lazily: lo keeps the last point with
+                // r > 0; once a point with r <= 0 is met it becomes hi and the iteration turns
+                // into the safeguarded Newton-bisection on [lo, hi].  Before that, a step that
+                // is not a forward Newton step (slope >= 0) probes ahead geometrically.
+                const float kg = A.kappa_guess ? (float)__ldg(A.kappa_guess + e0 * NQ + p) : kn;
+                if (kg > kn && isfinite(kg)) {
+                    kappa = kg;
+                    r_slope(yn, m, ncp, ppe, pphi, kappa, r, dr, Gp, sBuf, lane);
                     ++n_eval;
                 }
-                if (grow >= 200) fail = 1.0f;
-                kappa = lo;
-                r_slope(yn, m, ncp, ppe, pphi, kappa, r, dr, Gp, sBuf, lane);
-                ++n_eval;
-                float dx_prev = hi - lo, dx = dx_prev;
+                float lo = kn, hi = kn;
+                bool have_hi = false;
+                if (r > 0.0f) lo = kappa;
+                else {
+                    hi = kappa;
+                    have_hi = true;
+                }
+                float dx_prev = have_hi ? hi - lo : 1.0e30f, dx = dx_prev;
                 int it;
                 for (it = 0; it < m.local_max; ++it) {
-                    float scale = fabsf(kappa) > 1.0f ? fabsf(kappa) : 1.0f;
-                    if (fabsf(r) <= 2e-6f * scale || (hi - lo) <= 4.0f * kEpsF * scale) break;
-                    float newton = kappa - r / dr;
-                    bool take = (newton > lo) && (newton < hi) && (fabsf(2.0f * r) <= fabsf(dx_prev * dr));
+                    const float scale = fabsf(kappa) > 1.0f ? fabsf(kappa) : 1.0f;
+                    if (fabsf(r) <= 2e-6f * scale || (have_hi && (hi - lo) <= 4.0f * kEpsF * scale)) break;
+                    const float newton = kappa - r / dr;
+                    bool take;
+                    if (have_hi) {
+                        take = (newton > lo) && (newton < hi) && (fabsf(2.0f * r) <= fabsf(dx_prev * dr));
+                    } else {
+                        // forward Newton step, at most a few times the distance covered so far
+                        const float cap = 4.0f * ((float)(r > 1e-12f ? r : 1e-12f) + (kappa - kn));
+                        take = dr < 0.0f && newton > lo && (newton - kappa) <= cap;
+                    }
                     dx_prev = dx;
                     if (take) {
                         dx = kappa - newton;
                         kappa = newton;
-                    } else {
+                    } else if (have_hi) {
                         dx = 0.5f * (hi - lo);
                         kappa = lo + dx;
+                    } else {
+                        const float step = 2.0f * ((kappa - kn) > (r > 1e-12f ? r : 1e-12f) ? (kappa - kn) : (r > 1e-12f ? r : 1e-12f));
+                        dx = step;
+                        kappa = lo + step;
                     }
                     r_slope(yn, m, ncp, ppe, pphi, kappa, r, dr, Gp, sBuf, lane);
                     ++n_eval;
-                    if (r > 0.0f) lo = kappa; else hi = kappa;
+                    if (r > 0.0f) {
+                        lo = kappa;
+                    } else {
+                        hi = kappa;
+                        have_hi = true;
+                    }
                 }
                 if (it >= m.local_max) fail = 1.0f;
             }

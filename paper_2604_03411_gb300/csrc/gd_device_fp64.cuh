@@ -14,6 +14,14 @@ __device__ __forceinline__ double sigm(double v)
     double r = 1.0 / (1.0 + e);
     return v >= 0.0 ? r : e * r;
 }
+// softplus(v) and its derivative sigmoid(v) from one exponential
+__device__ __forceinline__ void sp_sig(double v, double &sp, double &sg)
+{
+    const double e = exp(-fabs(v));
+    sp = fmax(v, 0.0) + log1p(e);
+    const double r = 1.0 / (1.0 + e);
+    sg = v >= 0.0 ? r : e * r;
+}
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -119,8 +127,9 @@ __device__ void psi_net_unit(const DevNet &net, const double *x, double *out10, 
         if (j < w) {
             double a0 = __ldg(W1 + 3 * j), a1 = __ldg(W1 + 3 * j + 1), a2 = __ldg(W1 + 3 * j + 2);
             double h = __ldg(b1 + j) + a0 * x[0] + a1 * x[1] + a2 * x[2];
-            double sg = sigm(h);
-            sS[j] = softplus(h);
+            double sg, spv;
+            sp_sig(h, spv, sg);
+            sS[j] = spv;
             sD0[j] = sg * a0;
             sD1[j] = sg * a1;
             sD2[j] = sg * a2;
@@ -146,9 +155,11 @@ __device__ void psi_net_unit(const DevNet &net, const double *x, double *out10, 
                 g1 += wkj * sD1[j];
                 g2 += wkj * sD2[j];
             }
-            double sg = sigm(h), wk = __ldg(w3 + k);
+            double sg, spv;
+            sp_sig(h, spv, sg);
+            const double wk = __ldg(w3 + k);
             double e2 = wk * sg * (1.0 - sg);
-            acc[0] += wk * softplus(h);
+            acc[0] += wk * spv;
             acc[1] += wk * sg * g0;
             acc[2] += wk * sg * g1;
             acc[3] += wk * sg * g2;
@@ -207,8 +218,10 @@ __device__ void yield_unit(const DevNet &net, const NetConst &nc, double q, doub
         if (j < w) {
             double a = __ldg(V1 + j);
             double h = __ldg(c1 + j) + a * q;
-            sS[j] = softplus(h);
-            sT[j] = sigm(h) * a;
+            double spv, sg;
+            sp_sig(h, spv, sg);
+            sS[j] = spv;
+            sT[j] = sg * a;
         }
     }
     __syncwarp();
@@ -226,8 +239,10 @@ __device__ void yield_unit(const DevNet &net, const NetConst &nc, double q, doub
                 g += wkj * sT[j];
             }
             double vk = __ldg(v3 + k);
-            n0 += vk * softplus(h);
-            n1 += vk * sigm(h) * g;
+            double spv, sg;
+            sp_sig(h, spv, sg);
+            n0 += vk * spv;
+            n1 += vk * sg * g;
         }
     }
     n0 = warp_sum(n0);

@@ -50,6 +50,8 @@ struct AsmArgs {
     double *vals;            // FP64 values (may be null)
     float *vals32;           // FP32 values (mixed mode, may be null)
     double *kappa_new;       // may be null
+    const double *kappa_guess;   // may be null: a nearby solution of the local update (the last Newton
+                                 // iterate's kappa), where the local solve starts
     int8_t *loading;         // may be null
     const int32_t *slot;     // [E * nen * nen] CSR position of (row node a dof 0, col node b dof 0)
     const int32_t *rowptr;   // [n_dofs + 1]
