@@ -89,7 +89,7 @@ void free_ckpts(gd::Handle &H);
 void free_handle(gd::Handle &H)
 {
     void *ptrs[] = {H.X, H.conn, H.slot, H.rowptr, H.colidx, H.fixed, H.bc_dof, H.bc_scale, H.react_dof,
-                    H.psi.p, H.psi.W2T, H.yld.p, H.yld.W2T, H.psi.pf, H.psi.W2Tf, H.yld.pf, H.yld.W2Tf, H.netc, H.dofs, H.kappa, H.dofs_prev, H.w_dofs,
+                    H.psi.p, H.psi.W2T, H.yld.p, H.yld.W2T, H.psi.pf, H.psi.W2Tf, H.yld.pf, H.yld.W2Tf, H.netc, H.dofs, H.kappa, H.dofs_prev, H.dofs_pp, H.w_dofs,
                     H.w_trial, H.R, H.R_trial, H.vals, H.vals_trial, H.kappa_trial, H.kappa_trial2, H.loading,
                     H.loading2, H.counters, H.diag, H.binv, H.vals_f32, H.kx, H.red, H.scal};
     for (void *p : ptrs) dfree(p);
@@ -844,6 +844,21 @@ gd_status predict(gd::Handle &H, double t)
         const double Lt = path_load(H, 0, t), L1 = path_load(H, 0, H.load_prev), L2 = path_load(H, 0, H.load_prevprev);
         const double dl = L1 - L2;
         const bool extrap = H.have_prev && dl != 0.0;
+        // three converged states on a monotone stretch of the path: the quadratic through
+        // them (Lagrange in the load), else the line through the last two
+        if (extrap && H.have_pp) {
+            const double L3 = path_load(H, 0, H.load_ppp);
+            const bool mono = (Lt > L1 && L1 > L2 && L2 > L3) || (Lt < L1 && L1 < L2 && L2 < L3);
+            if (mono) {
+                const double w[3] = {(Lt - L2) * (Lt - L3) / ((L1 - L2) * (L1 - L3)),
+                                     (Lt - L1) * (Lt - L3) / ((L2 - L1) * (L2 - L3)),
+                                     (Lt - L1) * (Lt - L2) / ((L3 - L1) * (L3 - L2))};
+                GD_CUDA(&H, gd::launch_predictor3(H.n_dofs, H.w_dofs, H.dofs, H.dofs_prev, H.dofs_pp, w, H.bc_dof,
+                                                  H.bc_scale, H.n_bc, Lt, H.stream));
+                H.launches += H.n_bc > 0 ? 2 : 1;
+                return GD_OK;
+            }
+        }
         GD_CUDA(&H, gd::launch_predictor(H.n_dofs, H.w_dofs, H.dofs, extrap ? H.dofs_prev : nullptr,
                                          extrap ? (Lt - L1) / dl : 0.0, H.bc_dof, H.bc_scale, H.n_bc, Lt, H.stream));
         H.launches += H.n_bc > 0 ? 2 : 1;
@@ -932,6 +947,7 @@ gd_status restore_ckpt(gd::Handle &H, const gd::Checkpoint &c)
     H.load_prev = c.load_prev;
     H.load_prevprev = c.load_prevprev;
     H.have_prev = c.have_prev;
+    H.have_pp = false;                       // checkpoints keep two states
     return GD_OK;
 }
 
@@ -952,8 +968,19 @@ gd_status commit(gd::Handle &H, double target, gd_newton_report &rep)
         GD_CUDA(&H, cudaMemcpyAsync(H.last_reac.data(), H.d_load, sizeof(double) * H.n_spec, cudaMemcpyDeviceToHost,
                                     H.stream));
     }
-    std::swap(H.dofs_prev, H.dofs);
-    std::swap(H.dofs, H.w_dofs);            // dofs <- converged iterate
+    if (H.n_spec == 1) {
+        // dofs_pp <- dofs_prev <- dofs <- converged iterate; the oldest buffer becomes scratch
+        double *old_pp = H.dofs_pp;
+        H.dofs_pp = H.dofs_prev;
+        H.dofs_prev = H.dofs;
+        H.dofs = H.w_dofs;
+        H.w_dofs = old_pp;
+        H.have_pp = H.have_prev;
+        H.load_ppp = H.load_prevprev;
+    } else {
+        std::swap(H.dofs_prev, H.dofs);
+        std::swap(H.dofs, H.w_dofs);        // dofs <- converged iterate
+    }
     std::swap(H.kappa, H.kappa_trial);
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));
     rep.reaction = h[0];
@@ -1503,6 +1530,7 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
     const size_t nq_tot = (size_t)(NE * nen);
     double **vec_d[] = {&H.dofs, &H.dofs_prev, &H.w_dofs, &H.w_trial, &H.R, &H.R_trial, &H.diag};
     for (double **p : vec_d) GD_CREATE_CUDA(dalloc(p, (size_t)n_dofs));
+    if (n_spec == 1) GD_CREATE_CUDA(dalloc(&H.dofs_pp, (size_t)n_dofs));
     for (double *&p : H.kv) GD_CREATE_CUDA(dalloc(&p, (size_t)n_dofs));
     GD_CREATE_CUDA(dalloc(&H.kappa, nq_tot));
     GD_CREATE_CUDA(dalloc(&H.kappa_trial, nq_tot));
@@ -1924,6 +1952,7 @@ gd_status gd_set_state(gd_handle *h, const double *dofs, const double *dofs_prev
     H.rec_on = false;
     H.noise_age = 0;
     H.coarse_age = -1;
+    H.have_pp = false;
     H.have_prev = dofs_prev != nullptr;
     H.load_prev = (double)next_step;
     H.load_prevprev = dofs_prev ? (double)(next_step - 1) : H.load_prev;

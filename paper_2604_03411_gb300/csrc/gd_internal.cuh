@@ -191,6 +191,10 @@ struct Handle {
     double *dofs_prev = nullptr;                         // state before the last committed step
     double load_prev = 0.0, load_prevprev = 0.0;         // step coordinates t of the last two commits
     bool have_prev = false;
+    // single specimens: the state before dofs_prev and its step coordinate (quadratic predictor)
+    double *dofs_pp = nullptr;
+    double load_ppp = 0.0;
+    bool have_pp = false;
     int next_step = 0;
     // work arrays
     double *w_dofs = nullptr, *w_trial = nullptr;
@@ -285,6 +289,10 @@ cudaError_t launch_residual(const SolverCtx &c, const double *b, const double *y
 cudaError_t launch_predictor(int64_t n, double *out, const double *cur, const double *prev, double factor,
                              const int32_t *bc_dof, const double *bc_scale, int64_t n_bc, double load,
                              cudaStream_t s);
+// out = w0 x0 + w1 x1 + w2 x2, then the prescribed dofs set to bc_scale * load
+cudaError_t launch_predictor3(int64_t n, double *out, const double *x0, const double *x1, const double *x2,
+                              const double (&w)[3], const int32_t *bc_dof, const double *bc_scale, int64_t n_bc,
+                              double load, cudaStream_t s);
 cudaError_t launch_reaction(const double *R, const int32_t *react_dof, int64_t n_react, double *out,
                             cudaStream_t s);
 cudaError_t launch_gather(const double *in, const int32_t *perm, double *out, int64_t n, cudaStream_t s);

@@ -146,6 +146,13 @@ __global__ void predictor_kernel(int64_t n, double *out, const double *cur, cons
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = prev ? cur[i] + factor * (cur[i] - prev[i]) : cur[i];
 }
+// quadratic extrapolation through three converged states: out = w0 x0 + w1 x1 + w2 x2
+__global__ void predictor3_kernel(int64_t n, double *out, const double *x0, const double *x1, const double *x2,
+                                  double w0, double w1, double w2)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = w0 * x0[i] + w1 * x1[i] + w2 * x2[i];
+}
 __global__ void set_bc_kernel(double *out, const int32_t *bc_dof, const double *bc_scale, int64_t n_bc, double load)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_bc; i += (int64_t)gridDim.x * blockDim.x)
@@ -349,6 +356,21 @@ cudaError_t launch_predictor(int64_t n, double *out, const double *cur, const do
     int g = (int)((n + kThreads - 1) / kThreads);
     if (g > 1024) g = 1024;
     predictor_kernel<<<g, kThreads, 0, s>>>(n, out, cur, prev, factor);
+    if (n_bc > 0) {
+        int gb = (int)((n_bc + kThreads - 1) / kThreads);
+        if (gb > 1024) gb = 1024;
+        set_bc_kernel<<<gb, kThreads, 0, s>>>(out, bc_dof, bc_scale, n_bc, load);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_predictor3(int64_t n, double *out, const double *x0, const double *x1, const double *x2,
+                              const double (&w)[3], const int32_t *bc_dof, const double *bc_scale, int64_t n_bc,
+                              double load, cudaStream_t s)
+{
+    int g = (int)((n + kThreads - 1) / kThreads);
+    if (g > 1024) g = 1024;
+    predictor3_kernel<<<g, kThreads, 0, s>>>(n, out, x0, x1, x2, w[0], w[1], w[2]);
     if (n_bc > 0) {
         int gb = (int)((n_bc + kThreads - 1) / kThreads);
         if (gb > 1024) gb = 1024;
