@@ -111,6 +111,7 @@ void free_handle(gd::Handle &H)
     dfree(H.d_load);
     dfree(H.d_norm);
     dfree(H.d_coef);
+    dfree(H.d_pw);
     dfree(H.bk_i32);
     dfree(H.bk_f64);
     dfree(H.bk_cnt);
@@ -864,17 +865,32 @@ gd_status predict(gd::Handle &H, double t)
         H.launches += H.n_bc > 0 ? 2 : 1;
         return extrap ? GD_OK : linear_predictor(H);
     }
-    std::vector<double> hl((size_t)2 * H.n_spec);
+    // per specimen: the quadratic through its last three states on a monotone stretch of
+    // its path, else the line through the last two, else the last state
+    std::vector<double> hl((size_t)H.n_spec), hw((size_t)3 * H.n_spec);
     for (int s = 0; s < H.n_spec; ++s) {
         const double Lt = path_load(H, s, t), L1 = path_load(H, s, H.load_prev), L2 = path_load(H, s, H.load_prevprev);
-        const double dl = L1 - L2;
+        const double L3 = path_load(H, s, H.load_ppp), dl = L1 - L2;
+        double *w = hw.data() + 3 * s;
         hl[s] = Lt;
-        hl[H.n_spec + s] = (H.have_prev && dl != 0.0) ? (Lt - L1) / dl : 0.0;
+        w[0] = 1.0;
+        w[1] = w[2] = 0.0;
+        if (H.have_prev && dl != 0.0) {
+            const double f = (Lt - L1) / dl;
+            w[0] = 1.0 + f;
+            w[1] = -f;
+        }
+        if (H.have_prev && H.have_pp && ((Lt > L1 && L1 > L2 && L2 > L3) || (Lt < L1 && L1 < L2 && L2 < L3))) {
+            w[0] = (Lt - L2) * (Lt - L3) / ((L1 - L2) * (L1 - L3));
+            w[1] = (Lt - L1) * (Lt - L3) / ((L2 - L1) * (L2 - L3));
+            w[2] = (Lt - L1) * (Lt - L2) / ((L3 - L1) * (L3 - L2));
+        }
     }
-    GD_CUDA(&H, cudaMemcpyAsync(H.d_load, hl.data(), sizeof(double) * 2 * H.n_spec, cudaMemcpyHostToDevice, H.stream));
+    GD_CUDA(&H, cudaMemcpyAsync(H.d_load, hl.data(), sizeof(double) * H.n_spec, cudaMemcpyHostToDevice, H.stream));
+    GD_CUDA(&H, cudaMemcpyAsync(H.d_pw, hw.data(), sizeof(double) * 3 * H.n_spec, cudaMemcpyHostToDevice, H.stream));
     GD_CUDA(&H, gd::launch_predictor_batch(H.n_dofs, H.ndof, H.w_dofs, H.dofs, H.have_prev ? H.dofs_prev : nullptr,
-                                           H.d_factor, H.node_spec, H.bc_dof, H.bc_scale, H.bc_spec, H.d_load, H.n_bc,
-                                           H.stream));
+                                           H.have_pp ? H.dofs_pp : nullptr, H.d_pw, H.node_spec, H.bc_dof, H.bc_scale,
+                                           H.bc_spec, H.d_load, H.n_bc, H.stream));
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));     // hl is pageable host memory
     H.launches += H.n_bc > 0 ? 2 : 1;
     return H.have_prev ? GD_OK : linear_predictor(H);
@@ -968,7 +984,7 @@ gd_status commit(gd::Handle &H, double target, gd_newton_report &rep)
         GD_CUDA(&H, cudaMemcpyAsync(H.last_reac.data(), H.d_load, sizeof(double) * H.n_spec, cudaMemcpyDeviceToHost,
                                     H.stream));
     }
-    if (H.n_spec == 1) {
+    {
         // dofs_pp <- dofs_prev <- dofs <- converged iterate; the oldest buffer becomes scratch
         double *old_pp = H.dofs_pp;
         H.dofs_pp = H.dofs_prev;
@@ -977,9 +993,6 @@ gd_status commit(gd::Handle &H, double target, gd_newton_report &rep)
         H.w_dofs = old_pp;
         H.have_pp = H.have_prev;
         H.load_ppp = H.load_prevprev;
-    } else {
-        std::swap(H.dofs_prev, H.dofs);
-        std::swap(H.dofs, H.w_dofs);        // dofs <- converged iterate
     }
     std::swap(H.kappa, H.kappa_trial);
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));
@@ -1517,7 +1530,7 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
         GD_CREATE_CUDA(dalloc(&H.d_load, (size_t)2 * n_spec));
         GD_CREATE_CUDA(dalloc(&H.d_norm, (size_t)2 * n_spec));
         GD_CREATE_CUDA(dalloc(&H.d_coef, (size_t)n_spec));
-        H.d_factor = H.d_load + n_spec;
+        GD_CREATE_CUDA(dalloc(&H.d_pw, (size_t)3 * n_spec));
         if (NE > 0) GD_CREATE_CUDA(cudaMemcpy(H.elem_spec, es.data(), sizeof(int32_t) * es.size(), cudaMemcpyHostToDevice));
         GD_CREATE_CUDA(cudaMemcpy(H.node_spec, ns.data(), sizeof(int32_t) * ns.size(), cudaMemcpyHostToDevice));
         if (!bs.empty()) GD_CREATE_CUDA(cudaMemcpy(H.bc_spec, bs.data(), sizeof(int32_t) * bs.size(), cudaMemcpyHostToDevice));
@@ -1530,7 +1543,7 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
     const size_t nq_tot = (size_t)(NE * nen);
     double **vec_d[] = {&H.dofs, &H.dofs_prev, &H.w_dofs, &H.w_trial, &H.R, &H.R_trial, &H.diag};
     for (double **p : vec_d) GD_CREATE_CUDA(dalloc(p, (size_t)n_dofs));
-    if (n_spec == 1) GD_CREATE_CUDA(dalloc(&H.dofs_pp, (size_t)n_dofs));
+    GD_CREATE_CUDA(dalloc(&H.dofs_pp, (size_t)n_dofs));
     for (double *&p : H.kv) GD_CREATE_CUDA(dalloc(&p, (size_t)n_dofs));
     GD_CREATE_CUDA(dalloc(&H.kappa, nq_tot));
     GD_CREATE_CUDA(dalloc(&H.kappa_trial, nq_tot));

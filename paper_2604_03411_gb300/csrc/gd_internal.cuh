@@ -173,7 +173,8 @@ struct Handle {
     int64_t *node_off = nullptr;                         // [n_spec + 1] device (batches only)
     std::vector<int64_t> h_node_off, h_elem_off;         // [n_spec + 1]
     std::vector<int64_t> spec_nbc;                       // prescribed dofs per specimen
-    double *d_load = nullptr, *d_factor = nullptr;       // [n_spec] device (batches only)
+    double *d_load = nullptr;                            // [2 n_spec] device loads / reactions (batches only)
+    double *d_pw = nullptr;                              // [3 n_spec] predictor weights (batches only)
     double *d_norm = nullptr, *d_coef = nullptr;         // [2 n_spec], [n_spec] device (batches only)
     // per-specimen Krylov layout (batches whose specimens are not too small for the grid)
     bool bk_ok = false;
@@ -191,7 +192,7 @@ struct Handle {
     double *dofs_prev = nullptr;                         // state before the last committed step
     double load_prev = 0.0, load_prevprev = 0.0;         // step coordinates t of the last two commits
     bool have_prev = false;
-    // single specimens: the state before dofs_prev and its step coordinate (quadratic predictor)
+    // the state before dofs_prev and its step coordinate (quadratic predictor)
     double *dofs_pp = nullptr;
     double load_ppp = 0.0;
     bool have_pp = false;
@@ -296,8 +297,9 @@ cudaError_t launch_predictor3(int64_t n, double *out, const double *x0, const do
 cudaError_t launch_reaction(const double *R, const int32_t *react_dof, int64_t n_react, double *out,
                             cudaStream_t s);
 cudaError_t launch_gather(const double *in, const int32_t *perm, double *out, int64_t n, cudaStream_t s);
+// out = w0 cur + w1 prev + w2 pp per specimen (w [3 n_spec]), then the prescribed dofs
 cudaError_t launch_predictor_batch(int64_t n, int ndof, double *out, const double *cur, const double *prev,
-                                   const double *factor, const int32_t *node_spec, const int32_t *bc_dof,
+                                   const double *pp, const double *w, const int32_t *node_spec, const int32_t *bc_dof,
                                    const double *bc_scale, const int32_t *bc_spec, const double *load, int64_t n_bc,
                                    cudaStream_t s);
 cudaError_t launch_norms_batch(const double *R, const uint8_t *fixed, const int64_t *node_off, int ndof, int n_spec,

@@ -160,12 +160,17 @@ __global__ void set_bc_kernel(double *out, const int32_t *bc_dof, const double *
 }
 
 // batched specimens: per-specimen extrapolation factor and prescribed load
+// batched specimens: per-specimen weights of the current, previous and earlier state
+// (w[3 s + 0..2]; an absent state has weight 0)
 __global__ void predictor_batch_kernel(int64_t n, int ndof, double *out, const double *cur, const double *prev,
-                                       const double *factor, const int32_t *node_spec)
+                                       const double *pp, const double *w, const int32_t *node_spec)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double f = factor[node_spec[i / ndof]];
-        out[i] = (prev && f != 0.0) ? cur[i] + f * (cur[i] - prev[i]) : cur[i];
+        const double *ws = w + 3 * node_spec[i / ndof];
+        double v = ws[0] == 1.0 ? cur[i] : ws[0] * cur[i];
+        if (prev && ws[1] != 0.0) v += ws[1] * prev[i];
+        if (pp && ws[2] != 0.0) v += ws[2] * pp[i];
+        out[i] = v;
     }
 }
 __global__ void set_bc_batch_kernel(double *out, const int32_t *bc_dof, const double *bc_scale, const int32_t *bc_spec,
@@ -407,11 +412,11 @@ cudaError_t launch_axpby(int64_t n, double *out, const double *x, double b, cons
 }
 
 cudaError_t launch_predictor_batch(int64_t n, int ndof, double *out, const double *cur, const double *prev,
-                                   const double *factor, const int32_t *node_spec, const int32_t *bc_dof,
+                                   const double *pp, const double *w, const int32_t *node_spec, const int32_t *bc_dof,
                                    const double *bc_scale, const int32_t *bc_spec, const double *load, int64_t n_bc,
                                    cudaStream_t s)
 {
-    predictor_batch_kernel<<<1024, kThreads, 0, s>>>(n, ndof, out, cur, prev, factor, node_spec);
+    predictor_batch_kernel<<<1024, kThreads, 0, s>>>(n, ndof, out, cur, prev, pp, w, node_spec);
     if (n_bc > 0) set_bc_batch_kernel<<<256, kThreads, 0, s>>>(out, bc_dof, bc_scale, bc_spec, load, n_bc);
     return cudaGetLastError();
 }
