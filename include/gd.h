@@ -9,7 +9,8 @@
  * function with the local damage/history update, the degraded stress and the
  * non-local fluxes; per element the coupled residual and consistent tangent,
  * scattered into a CSR matrix through a precomputed slot map; and the global
- * Newton iteration with a Jacobi-preconditioned Krylov solver on the device.
+ * Newton iteration with a Krylov solver on the device, preconditioned by node-block
+ * Jacobi plus an aggregation coarse level.
  *
  * Conventions
  *  - Every call returns gd_status; after a non-OK status gd_last_error() gives a
@@ -363,8 +364,11 @@ gd_status gd_get_fields(gd_handle *h, double *dofs, double *kappa, double *damag
  * dofs, kappa as in gd_get_fields (NULL keeps the handle's).  dofs_prev (may be
  * NULL) is the converged state of step next_step - 1's predecessor, i.e. the
  * state one step before `dofs`: with it the next step's initial guess
- * extrapolates the last increment exactly as an uninterrupted run does; without
- * it the next step starts from `dofs` itself. */
+ * extrapolates the last increment linearly; without it the next step starts from
+ * `dofs` itself.  (An uninterrupted run takes the quadratic through its last three
+ * converged states where the path is monotone; after gd_set_state that resumes
+ * once two more steps are committed.  The converged states agree to the Newton
+ * tolerance either way.) */
 gd_status gd_set_state(gd_handle *h, const double *dofs, const double *dofs_prev, const double *kappa,
                        int32_t next_step);
 
