@@ -240,7 +240,7 @@ gd_status norms(gd::Handle &H, const double *R, NormPair &out)
 // converges at under 0.7 times the rate (log reduction per iteration) of the solve
 // that computed it.  kind: 0 the Newton tangent, 1 its transpose (adjoint), 2 a
 // caller's matrix (always recomputed, and not kept).
-constexpr int kCoarseReuse = 4;
+constexpr int kCoarseReuse = 8;
 
 gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, int &iters, double &rel,
                  double rtol, bool inner_fp32 = false, double accept = -1.0, int kind = 0)
