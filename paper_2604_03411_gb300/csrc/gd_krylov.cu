@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(kThreads, 2) bicgstab3_kernel(KArgs<V, T> A)
     const int32_t passes = (n_nodes + nw * NPW - 1) / (nw * NPW);   // warp-uniform
     // CO: two-level preconditioner M^-1 = D^-1 + P Ac^-1 P^T.  The node-block part is
     // applied where the vector is formed, together with the restriction P^T (atomic
-    // sums into rc); after the phase's barrier, Ac^-1 rc (one warp per coarse row),
+    // sums into rc); after the phase's barrier, Ac^-1 rc (coarse rows spread over the CTAs),
     // a barrier, the prolongation P added to the owned rows, and a barrier before
     // the product reads them.  Skipped when the inversion reported a zero pivot.
     bool co = false;
