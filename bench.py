@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gd", choices=["gd", "reference"])
-    ap.add_argument("--workload", default="notched", choices=["notched", "cube", "square", "batch"])
+    ap.add_argument("--workload", default="notched", choices=["notched", "notched3d", "cube", "square", "batch"])
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
                     help="default: fp64 (mixed for the batch workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -86,6 +86,11 @@ def make_workload(name, rank=0, world=1):
         desc = {"workload": "notched_plate_q4", "elements": p.mesh.n_elems, "qp": p.mesh.n_elems * 4,
                 "dofs": p.mesh.n_nodes * 3, "icnn_width": [32, 32], "load_steps": int(p.load.size),
                 "length_scale": 0.02}
+    elif name == "notched3d":
+        p = I.notched_plate_3d()
+        desc = {"workload": "notched_plate_hex8", "elements": p.mesh.n_elems, "qp": p.mesh.n_elems * 8,
+                "dofs": p.mesh.n_nodes * 4, "icnn_width": [32, 32], "load_steps": int(p.load.size),
+                "length_scale": 0.04}
     elif name == "cube":
         p = I.config3(precision="fp64")
         desc = {"workload": "cube_hex8_64", "elements": p.mesh.n_elems, "qp": p.mesh.n_elems * 8,

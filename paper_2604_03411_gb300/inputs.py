@@ -181,6 +181,27 @@ def notched_plate_q4(n_long: int, n_wide: int, length: float = 2.0, width: float
     return _q4_from_grid(coords, n_long, n_wide)
 
 
+def extrude_hex8(m2: Mesh, n_thick: int, thickness: float) -> Mesh:
+    """HEX8 mesh of a Q4 mesh extruded along z through n_thick equal layers:
+    node (i, layer k) = k * n_nodes_2d + i; each hexahedron is the quadrilateral on
+    layer k followed by the same quadrilateral on layer k + 1 (the node order of
+    structured_hex8)."""
+    nn = m2.n_nodes
+    zs = np.linspace(0.0, thickness, n_thick + 1)
+    coords = np.concatenate([np.column_stack([m2.coords, np.full(nn, z)]) for z in zs])
+    q = m2.conn.astype(np.int64)
+    conn = np.concatenate([np.concatenate([q + k * nn, q + (k + 1) * nn], axis=1) for k in range(n_thick)])
+    return Mesh(3, coords.astype(np.float64), conn.astype(np.int32), np.zeros(0, np.int32), np.zeros(0, np.int8),
+                np.zeros(0, np.float64), np.zeros(0, np.int32), 0)
+
+
+def notched_plate_hex8(n_long: int, n_wide: int, n_thick: int = 1, length: float = 1.0, width: float = 1.0,
+                       thickness: float = 0.01, radius: float = 0.1) -> Mesh:
+    """Thin 3D notched plate (the paper's 100 x 100 x 1 plate, nondimensionalised):
+    the graded Q4 notched plate of notched_plate_q4 extruded through the thickness."""
+    return extrude_hex8(notched_plate_q4(n_long, n_wide, length, width, radius), n_thick, thickness)
+
+
 # ---------------------------------------------------------------------------
 # boundary sets
 # ---------------------------------------------------------------------------
@@ -196,6 +217,28 @@ def uniaxial_bc_2d(mesh: Mesh, scale: float = 1.0) -> Mesh:
     comps = np.concatenate([np.zeros(left.size), [1], np.zeros(right.size)]).astype(np.int8)
     scales = np.concatenate([np.zeros(left.size), [0.0], np.full(right.size, scale)]).astype(np.float64)
     mesh.bc_node, mesh.bc_comp, mesh.bc_scale = nodes, comps, scales
+    mesh.react_node = right.astype(np.int32)
+    mesh.react_comp = 0
+    return mesh
+
+
+def uniaxial_bc_3d(mesh: Mesh, scale: float = 1.0) -> Mesh:
+    """Uniaxial pull of a 3D body along x: u_x = 0 on the x=min face, u_y = 0 on its
+    y=min edge, u_z = 0 on the z=min face (a symmetry plane), u_x = scale*load on the
+    x=max face; the reaction is the x force on that face."""
+    c = mesh.coords
+    lo = c.min(axis=0)
+    hi = c.max(axis=0)
+    tol = 1e-9 * float((hi - lo).max())
+    left = np.nonzero(np.abs(c[:, 0] - lo[0]) < tol)[0]
+    edge = left[np.abs(c[left, 1] - lo[1]) < tol]
+    bottom = np.nonzero(np.abs(c[:, 2] - lo[2]) < tol)[0]
+    right = np.nonzero(np.abs(c[:, 0] - hi[0]) < tol)[0]
+    mesh.bc_node = np.concatenate([left, edge, bottom, right]).astype(np.int32)
+    mesh.bc_comp = np.concatenate([np.zeros(left.size), np.ones(edge.size), np.full(bottom.size, 2),
+                                   np.zeros(right.size)]).astype(np.int8)
+    mesh.bc_scale = np.concatenate([np.zeros(left.size + edge.size + bottom.size),
+                                    np.full(right.size, scale)]).astype(np.float64)
     mesh.react_node = right.astype(np.int32)
     mesh.react_comp = 0
     return mesh
@@ -283,6 +326,19 @@ def config4(seed: int = 4, n_long: int = 222, n_wide: int = 90, n_steps: int = 3
     fd_idx = fd_rng.choice(theta.size, size=20, replace=False)
     return Problem(f"notched_plate_q4_{mesh.n_elems}_adjoint", mesh, psi, yld, mat, load, "fp64",
                    extra={"theta_star": theta_star, "fd_index": fd_idx, "checkpoint_every": 5})
+
+
+def notched_plate_3d(seed: int = 6, n_long: int = 49, n_wide: int = 48, n_steps: int = 100, ell: float = 0.04,
+                     width_psi: int = 32, width_yield: int = 32, precision: str = "fp64") -> Problem:
+    """The paper's 3D notched-plate geometry: a thin square plate (thickness 1/100 of
+    its side) with semicircular edge notches, one HEX8 layer; 2,352 elements for the
+    defaults (the paper's finest mesh has 2,350; 16 x 15 and 26 x 24 give its 241
+    and 625), pulled along x to 25% nominal strain in n_steps steps."""
+    mesh = uniaxial_bc_3d(notched_plate_hex8(n_long, n_wide))
+    psi, yld = icnn_pair(seed, width_psi, width_yield)
+    mat = Material(beta_d=10.0, c_d=10.0 * ell * ell)
+    load = np.linspace(0.0, 0.25, n_steps + 1)[1:]
+    return Problem(f"notched_plate_hex8_{mesh.n_elems}", mesh, psi, yld, mat, load, precision)
 
 
 def config5(seed: int = 5, n_specimens: int = 96) -> List[Problem]:
