@@ -60,6 +60,7 @@ enum { GD_FP64 = 0, GD_MIXED = 1 };
 enum { GD_BICGSTAB = 0, GD_GMRES = 1 };
 enum { GD_ASM_RESIDUAL = 0, GD_ASM_TANGENT = 1 };
 enum { GD_INNER_AUTO = 0, GD_INNER_FP64 = 1, GD_INNER_REFINED = 2 };
+enum { GD_MONOLITHIC = 0, GD_STAGGERED = 1 };
 
 /* Mesh and boundary data (Sec. 3.1, Table kernel_inputs; Dirichlet data of the
  * incremental load, Sec. 3.2).
@@ -148,6 +149,16 @@ typedef struct gd_options {
                                   level (aggregates never span two specimens) solves its
                                   union system in one recurrence instead of per-specimen
                                   recurrences.                                              */
+    int32_t scheme;            /* GD_MONOLITHIC (default, Sec. 3.2): kappa is updated inside
+                                  every Newton iteration and its sensitivity enters the
+                                  tangent.  GD_STAGGERED (single specimens): the (u, phi)
+                                  equilibrium is solved by Newton with kappa frozen, then the
+                                  local update runs at the converged fields, and the two
+                                  alternate until the residual with the updated kappa meets
+                                  the Newton test; the converged step solves the same
+                                  equations as the monolithic one.                         */
+    int32_t stagger_max;       /* alternations per load step before the step counts as failed
+                                  (default 100)                                              */
 } gd_options;
 
 typedef struct gd_newton_report {
@@ -183,7 +194,7 @@ typedef struct gd_handle gd_handle;
 /* Fills *opt with the defaults: FP64, newton_rtol 1e-10, newton_atol 1e-12,
  * newton_max 25, line_search_max 12, BiCGStab with krylov_rtol 1e-12 and
  * krylov_max 20000, local_max 100, checkpoint_every 5, max_step_cuts 4,
- * default stream, coarse 1536. */
+ * default stream, coarse 1536, monolithic scheme (stagger_max 100). */
 void gd_default_options(gd_options *opt);
 
 /* Creates a problem (Sec. 3.1 kernel inputs, Sec. 3.2 load path): copies and

@@ -24,6 +24,7 @@ STATUS = {0: "GD_OK", 1: "GD_ERR_ARG", 2: "GD_ERR_MESH", 3: "GD_ERR_CUDA", 4: "G
 GD_FP64, GD_MIXED = 0, 1
 GD_ASM_RESIDUAL, GD_ASM_TANGENT = 0, 1
 GD_INNER_AUTO, GD_INNER_FP64, GD_INNER_REFINED = 0, 1, 2
+GD_MONOLITHIC, GD_STAGGERED = 0, 1
 GD_NOALLOC_MAX_DOFS = 131072
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -59,7 +60,7 @@ class GdOptions(ctypes.Structure):
                 ("krylov_rtol", ctypes.c_double), ("krylov_max", ctypes.c_int32), ("gmres_m", ctypes.c_int32),
                 ("local_max", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
                 ("max_step_cuts", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p), ("inner_solve", ctypes.c_int32),
-                ("coarse", ctypes.c_int32)]
+                ("coarse", ctypes.c_int32), ("scheme", ctypes.c_int32), ("stagger_max", ctypes.c_int32)]
 
 
 class GdNewtonReport(ctypes.Structure):

@@ -112,6 +112,7 @@ void free_handle(gd::Handle &H)
     dfree(H.d_norm);
     dfree(H.d_coef);
     dfree(H.d_pw);
+    dfree(H.kappa_stag);
     dfree(H.bk_i32);
     dfree(H.bk_f64);
     dfree(H.bk_cnt);
@@ -166,6 +167,7 @@ gd::AsmArgs asm_args(gd::Handle &H, const double *dofs, const double *kappa_n, d
     a.vals32 = (tangent && H.opt.precision == GD_MIXED) ? (float *)vals : nullptr;
     a.kappa_new = kappa_out;
     a.kappa_guess = nullptr;
+    a.kappa_fixed = H.kappa_fix;
     a.loading = loading;
     a.slot = H.slot;
     a.rowptr = H.rowptr;
@@ -1011,6 +1013,65 @@ gd_status commit(gd::Handle &H, double target, gd_newton_report &rep)
     return GD_OK;
 }
 
+// Staggered scheme (gd_options.scheme): Newton on the (u, phi) equilibrium with the
+// history frozen, then the local update at the converged fields; the two alternate
+// until the residual with the updated history meets the Newton test (then the step
+// solves the same equations as the monolithic scheme).  The loading test of every
+// local update is against the committed history kappa_n, as in the monolithic scheme.
+gd_status newton_staggered(gd::Handle &H, gd_newton_report &rep)
+{
+    const size_t nq_bytes = sizeof(double) * (size_t)(H.n_elems * H.nq);
+    GD_CUDA(&H, cudaMemcpyAsync(H.kappa_stag, H.kappa, nq_bytes, cudaMemcpyDeviceToDevice, H.stream));
+    gd_status st = GD_OK;
+    double r0 = -1.0;
+    for (int s = 0; s < H.opt.stagger_max; ++s) {
+        gd_newton_report sub{};
+        H.kappa_fix = H.kappa_stag;
+        st = newton(H, sub);
+        H.kappa_fix = nullptr;
+        rep.iterations += sub.iterations;
+        rep.krylov_iterations += sub.krylov_iterations;
+        rep.krylov_fp32_iterations += sub.krylov_fp32_iterations;
+        rep.line_search_cuts += sub.line_search_cuts;
+        rep.yield_evals += sub.yield_evals;
+        if (s == 0) rep.residual0 = sub.residual0;
+        if (st) return st;
+        if (!sub.converged) {
+            rep.residual = sub.residual;
+            rep.converged = 0;
+            return GD_OK;
+        }
+        // the fields already met the Newton test with this history (which the update
+        // computed from them): a fixed point to that test (in GD_MIXED, to its noise floor)
+        if (s > 0 && sub.iterations == 0) {
+            rep.residual = sub.residual;
+            rep.converged = 1;
+            return GD_OK;
+        }
+        // local update at the converged fields, and the residual with it
+        if ((st = assemble_pass(H, H.w_dofs, H.kappa, H.R, nullptr, H.kappa_trial, H.loading, 0))) return st;
+        NormPair nr;
+        if ((st = norms(H, H.R, nr))) return st;
+        H.assembly_ms += elapsed_ms(H);
+        int hc[3];
+        GD_CUDA(&H, cudaMemcpy(hc, H.counters, 3 * sizeof(int), cudaMemcpyDeviceToHost));
+        rep.yield_evals += hc[2];
+        rep.local_failures = hc[0];
+        rep.loading_points = hc[1];
+        if (r0 < 0.0) r0 = std::max(std::max(sub.residual0, nr.free_), nr.fixed_);
+        rep.residual = nr.free_;
+        const double tol = std::max(H.opt.newton_rtol * r0, H.opt.newton_atol);
+        if (!std::isfinite(nr.free_)) return fail(&H, GD_ERR_NAN, "non-finite residual in the staggered scheme");
+        if (nr.free_ <= tol) {
+            rep.converged = 1;
+            return GD_OK;
+        }
+        GD_CUDA(&H, cudaMemcpyAsync(H.kappa_stag, H.kappa_trial, nq_bytes, cudaMemcpyDeviceToDevice, H.stream));
+    }
+    rep.converged = 0;
+    return GD_OK;
+}
+
 gd_status advance(gd::Handle &H, double target, int depth, gd_newton_report &rep)
 {
     gd_status sp = predict(H, target);
@@ -1019,7 +1080,9 @@ gd_status advance(gd::Handle &H, double target, int depth, gd_newton_report &rep
     const double a0 = H.assembly_ms, k0 = H.krylov_ms;
     const int n0 = H.assemblies;
     const long long l0 = H.launches;
-    gd_status st = H.n_spec > 1 ? newton_batch(H, sub) : newton(H, sub);
+    gd_status st = H.n_spec > 1                      ? newton_batch(H, sub)
+                   : H.opt.scheme == GD_STAGGERED ? newton_staggered(H, sub)
+                                                  : newton(H, sub);
     rep.assembly_ms += H.assembly_ms - a0;
     rep.krylov_ms += H.krylov_ms - k0;
     rep.assemblies += H.assemblies - n0;
@@ -1193,6 +1256,8 @@ void gd_default_options(gd_options *o)
     o->max_step_cuts = 4;
     o->cuda_stream = nullptr;
     o->coarse = 1536;
+    o->scheme = GD_MONOLITHIC;
+    o->stagger_max = 100;
 }
 
 const char *gd_last_error(const gd_handle *h) { return h ? h->h.err.c_str() : g_create_error.c_str(); }
@@ -1393,6 +1458,9 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
     if (o.inner_solve < GD_INNER_AUTO || o.inner_solve > GD_INNER_REFINED)
         return fail(nullptr, GD_ERR_ARG, "inner_solve");
     if (o.coarse < 0 || o.coarse > gd::kCoarseMax) return fail(nullptr, GD_ERR_ARG, "coarse must be in [0, 3072]");
+    if (o.scheme != GD_MONOLITHIC && o.scheme != GD_STAGGERED) return fail(nullptr, GD_ERR_ARG, "scheme");
+    if (o.scheme == GD_STAGGERED && (n_spec > 1 || o.stagger_max < 1))
+        return fail(nullptr, GD_ERR_ARG, "the staggered scheme needs one specimen and stagger_max >= 1");
 
     const int dim = mesh->dim, nen = dim == 2 ? 4 : 8, ndof = dim + 1;
     const int64_t NN = mesh->n_nodes, NE = mesh->n_elems;
@@ -1550,6 +1618,7 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
     GD_CREATE_CUDA(dalloc(&H.kappa_trial2, nq_tot));
     GD_CREATE_CUDA(dalloc(&H.loading, nq_tot));
     GD_CREATE_CUDA(dalloc(&H.loading2, nq_tot));
+    if (o.scheme == GD_STAGGERED) GD_CREATE_CUDA(dalloc(&H.kappa_stag, nq_tot));
     GD_CREATE_CUDA(dalloc(&H.vals, (size_t)nnz));
     GD_CREATE_CUDA(dalloc(&H.vals_trial, (size_t)nnz));
     GD_CREATE_CUDA(dalloc(&H.counters, 8));

@@ -270,6 +270,15 @@ __global__ void __launch_bounds__(32 * KW) asm_fp64_kernel(AsmArgs A)
         __syncwarp();
 
         // ================= unit mode: local damage update per point =================
+        if (A.kappa_fixed) {
+            // frozen history (staggered scheme): the point keeps the given kappa
+            double *o = sOut + lane * 10;
+            o[0] = valid ? __ldg(A.kappa_fixed + e_me * NQ + q) : 0.0;
+            o[1] = 0.0;
+            o[2] = 0.0;
+            o[3] = -1.0;
+            o[4] = 0.0;
+        } else
         for (int p = 0; p < 32; ++p) {
             if (e0 + p / NQ >= A.n_elems) break;
             const double ppe = sIn[p * 4], pphi = sIn[p * 4 + 1], kn = sIn[p * 4 + 2];

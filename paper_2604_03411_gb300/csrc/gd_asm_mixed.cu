@@ -564,6 +564,16 @@ __global__ void __launch_bounds__(32 * KW) asm_fp32_kernel(AsmArgs A)
         __syncwarp();
 
         // ================= unit mode: local damage update per point =================
+        if (A.kappa_fixed) {
+            // frozen history (staggered scheme): the point keeps the given kappa
+            float *o = sOut + lane * 10;
+            o[0] = valid ? (float)__ldg(A.kappa_fixed + e_me * NQ + q) : 0.0f;
+            o[1] = 0.0f;
+            o[2] = 0.0f;
+            o[3] = -1.0f;
+            o[4] = 0.0f;
+            o[5] = 0.0f;
+        } else
         for (int p = 0; p < 32; ++p) {
             if (e0 + p / NQ >= A.n_elems) break;
             const float ppe = sIn[p * 4], pphi = sIn[p * 4 + 1], kn = sIn[p * 4 + 2];
@@ -655,7 +665,8 @@ __global__ void __launch_bounds__(32 * KW) asm_fp32_kernel(AsmArgs A)
             if (valid) {
                 if (A.kappa_new) {
                     const double kn_d = __ldg(A.kappa_n + e_me * NQ + q);
-                    A.kappa_new[e_me * NQ + q] = o[5] > 0.5f ? kn_d : fmax(kn_d, (double)kappa);
+                    A.kappa_new[e_me * NQ + q] = A.kappa_fixed ? __ldg(A.kappa_fixed + e_me * NQ + q)
+                                                 : o[5] > 0.5f ? kn_d : fmax(kn_d, (double)kappa);
                 }
                 if (A.loading) A.loading[e_me * NQ + q] = loading ? 1 : 0;
                 if (o[4] > 0.5f) atomicAdd(A.counters, 1);

@@ -52,6 +52,8 @@ struct AsmArgs {
     double *kappa_new;       // may be null
     const double *kappa_guess;   // may be null: a nearby solution of the local update (the last Newton
                                  // iterate's kappa), where the local solve starts
+    const double *kappa_fixed;   // may be null: a frozen history (staggered scheme): every point takes
+                                 // this kappa, no local update and no kappa sensitivity in the tangent
     int8_t *loading;         // may be null
     const int32_t *slot;     // [E * nen * nen] CSR position of (row node a dof 0, col node b dof 0)
     const int32_t *rowptr;   // [n_dofs + 1]
@@ -224,6 +226,10 @@ struct Handle {
     int krylov_up = 0;                                   // 0: the precision's default
     int krylov_lmax = 0;                                 // longest CSR row
     CoarseSpace coarse;                                  // two-level preconditioner (nc = 0: off)
+    // staggered scheme: the frozen history of the current equilibrium solve (null: none)
+    // and its storage
+    const double *kappa_fix = nullptr;
+    double *kappa_stag = nullptr;
     // reuse of the coarse inverse across solves: solves since it was computed (-1: none
     // valid), the kind of matrix it belongs to, and the convergence rate of that solve
     int coarse_age = -1, coarse_kind = -1;
