@@ -278,8 +278,10 @@ gd_status gd_assemble(gd_handle *h, const double *dofs, const double *kappa_n, d
  * system).  Works on the handle's stream; does not synchronise. */
 gd_status gd_spmv(gd_handle *h, const double *x, double *y, int32_t free_only);
 
-/* Solves K x = b on the free dofs (the eliminated Newton system) with
- * node-block-Jacobi BiCGStab (opt.krylov_rtol / krylov_max).  csr_vals: device
+/* Solves K x = b on the free dofs (the eliminated Newton system) with BiCGStab,
+ * preconditioned by node-block Jacobi plus the handle's coarse level when it has
+ * one (opt.coarse; recomputed from csr_vals for the call) (opt.krylov_rtol /
+ * krylov_max).  csr_vals: device
  * tangent values in the handle's precision from gd_assemble, or NULL for the
  * tangent of the handle's last Newton iteration.  b, x device FP64
  * [n_nodes*ndof]; prescribed dofs of x are returned as 0.  iterations and
@@ -309,8 +311,9 @@ gd_status gd_coarse_aggregates(const gd_mesh *mesh, int32_t target_nodes, int32_
  * CUDA graph is being captured, applications whose own pool owns the device
  * memory, runtimes that forbid allocation after start-up).
  * Solves K x = b on the free dofs of a caller-provided node-block CSR system
- * (the layout of gd_csr_pattern, ndof 3 or 4, FP64 values) with the same
- * node-block-Jacobi BiCGStab as gd_solve.  All arrays are device pointers owned
+ * (the layout of gd_csr_pattern, ndof 3 or 4, FP64 values) with the persistent
+ * BiCGStab of gd_solve and node-block Jacobi alone (no coarse level: it would need
+ * work space of its own).  All arrays are device pointers owned
  * by the caller: rowptr [n_nodes*ndof + 1], colidx, vals [nnz], fixed
  * [n_nodes*ndof] (1 = prescribed dof), b, x [n_nodes*ndof]; prescribed dofs of x
  * come back as 0.  iterations and rel_residual (host, may be NULL) report the
