@@ -303,6 +303,19 @@ gd_status gd_coarse_info(gd_handle *h, int32_t *n_aggregates, int32_t *n_coarse)
  * Errors: GD_ERR_ARG, GD_ERR_MESH (as gd_build_pattern). */
 gd_status gd_coarse_aggregates(const gd_mesh *mesh, int32_t target_nodes, int32_t *agg, int32_t *n_aggregates);
 
+/* The coarse basis the two-level preconditioner would build for `mesh` with
+ * aggregates of about target_nodes nodes (host only, no device needed).  agg
+ * [n_nodes] and *n_aggregates as gd_coarse_aggregates; coff [n_nodes + 1] receives
+ * the first coarse unknown of every aggregate (coff[a + 1] - coff[a] columns kept
+ * for aggregate a, at most *n_modes); P [n_nodes * ndof * n_modes] (row-major
+ * [node][dof][mode]) the basis values: per aggregate, the constant field of each
+ * nodal unknown and the rigid rotations of the displacement, zero on prescribed
+ * dofs, orthonormalised over the aggregate (columns beyond coff[a + 1] - coff[a]
+ * are zero).  *n_modes = ndof + 1 in 2D, ndof + 3 in 3D.
+ * Errors: GD_ERR_ARG, GD_ERR_MESH (as gd_build_pattern). */
+gd_status gd_coarse_basis(const gd_mesh *mesh, int32_t target_nodes, int32_t *agg, int32_t *n_aggregates,
+                          int32_t *coff, float *P, int32_t *n_modes);
+
 /* Largest system (n_nodes * ndof) that gd_solve_noalloc accepts. */
 #define GD_NOALLOC_MAX_DOFS 131072
 

@@ -105,6 +105,8 @@ PROTOTYPES = {
     "gd_coarse_info": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "gd_coarse_aggregates": (ctypes.c_int, [ctypes.POINTER(GdMesh), ctypes.c_int32, _i32p,
                                             ctypes.POINTER(ctypes.c_int32)]),
+    "gd_coarse_basis": (ctypes.c_int, [ctypes.POINTER(GdMesh), ctypes.c_int32, _i32p, ctypes.POINTER(ctypes.c_int32),
+                                       _i32p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32)]),
     "gd_assemble": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "gd_spmv": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
@@ -229,6 +231,23 @@ def gd_coarse_aggregates(m, target_nodes: int):
     na = ctypes.c_int32()
     _check(lib().gd_coarse_aggregates(ctypes.byref(mesh), int(target_nodes), _hp(agg, _i32p), ctypes.byref(na)), None)
     return agg, na.value
+
+
+def gd_coarse_basis(m, target_nodes: int):
+    """Host-only: (agg [n_nodes], coff [n_agg + 1], P [n_nodes, ndof, n_modes]) of the
+    two-level preconditioner's coarse basis."""
+    mesh, keep = _mesh_struct(m)
+    ndof = m.dim + 1
+    nm_max = ndof + (1 if m.dim == 2 else 3)
+    agg = np.zeros(m.n_nodes, np.int32)
+    coff = np.zeros(m.n_nodes + 1, np.int32)
+    P = np.zeros(m.n_nodes * ndof * nm_max, np.float32)
+    na = ctypes.c_int32()
+    nm = ctypes.c_int32()
+    _check(lib().gd_coarse_basis(ctypes.byref(mesh), int(target_nodes), _hp(agg, _i32p), ctypes.byref(na),
+                                 _hp(coff, _i32p), P.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                 ctypes.byref(nm)), None)
+    return agg, coff[: na.value + 1], P.reshape(m.n_nodes, ndof, nm.value)
 
 
 def gd_coarse_info(h: Handle):

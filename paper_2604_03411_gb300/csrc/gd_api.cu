@@ -1784,6 +1784,26 @@ gd_status gd_coarse_aggregates(const gd_mesh *mesh, int32_t target_nodes, int32_
     return GD_OK;
 }
 
+gd_status gd_coarse_basis(const gd_mesh *mesh, int32_t target_nodes, int32_t *agg, int32_t *n_aggregates,
+                          int32_t *coff, float *P, int32_t *n_modes)
+{
+    if (!agg || !n_aggregates || !coff || !P || !n_modes) return fail(nullptr, GD_ERR_ARG, "output arrays are null");
+    if (target_nodes < 1) return fail(nullptr, GD_ERR_ARG, "target_nodes must be positive");
+    Pattern pat;
+    gd_status st = build_pattern(mesh, pat);
+    if (st) return st;
+    std::vector<int32_t> a, co;
+    std::vector<float> Pv;
+    const int32_t na = gd::coarse_aggregate(mesh->n_nodes, mesh->dim + 1, pat.rowptr, pat.colidx, target_nodes, a);
+    gd::coarse_basis(mesh->dim, mesh->n_nodes, mesh->coords, pat.fixed.data(), a, na, Pv, co);
+    std::memcpy(agg, a.data(), sizeof(int32_t) * a.size());
+    std::memcpy(coff, co.data(), sizeof(int32_t) * co.size());
+    std::memcpy(P, Pv.data(), sizeof(float) * Pv.size());
+    *n_aggregates = na;
+    *n_modes = gd::coarse_modes(mesh->dim);
+    return GD_OK;
+}
+
 gd_status gd_assemble(gd_handle *h, const double *dofs, const double *kappa_n, double *R, void *csr_vals,
                       double *kappa_trial, int8_t *loading, int32_t mode)
 {

@@ -84,3 +84,47 @@ def test_bad_arguments(B):
     mesh = I.uniaxial_bc_2d(I.structured_q4(3, 3))
     with pytest.raises(B.GDError):
         B.gd_coarse_aggregates(mesh, 0)
+
+
+def rigid_and_constant_modes(coords, nodes, ndof):
+    """Constant field of every nodal unknown and the rigid rotations of the
+    displacement on the given nodes (about their centroid): [len(nodes) * ndof, m]."""
+    dim = coords.shape[1]
+    x = coords[nodes] - coords[nodes].mean(axis=0)
+    cols = []
+    for k in range(ndof):
+        v = np.zeros((len(nodes), ndof)); v[:, k] = 1.0; cols.append(v.ravel())
+    pairs = [(0, 1)] if dim == 2 else [(1, 2), (2, 0), (0, 1)]
+    for a, b in pairs:
+        v = np.zeros((len(nodes), ndof)); v[:, a] = -x[:, b]; v[:, b] = x[:, a]; cols.append(v.ravel())
+    return np.stack(cols, axis=1)
+
+
+@pytest.mark.parametrize("dim,target", [(2, 20), (2, 5), (3, 27)])
+def test_coarse_basis_orthonormal_and_spanning(B, dim, target):
+    """Per aggregate: the kept columns are orthonormal, vanish on prescribed dofs, and
+    span the constant fields and rigid rotations restricted to the free dofs."""
+    if dim == 2:
+        mesh = I.uniaxial_bc_2d(I.notched_plate_q4(24, 10))
+    else:
+        mesh = I.biaxial_bc_3d(I.structured_hex8(6, 5, 4))
+    ndof = dim + 1
+    agg, coff, P = B.gd_coarse_basis(mesh, target)
+    n_agg = coff.size - 1
+    fixed = np.zeros((mesh.n_nodes, ndof), bool)
+    fixed[mesh.bc_node, mesh.bc_comp] = True
+    assert np.all(P[fixed] == 0.0)
+    full = 0
+    for a in range(n_agg):
+        nodes = np.nonzero(agg == a)[0]
+        k = coff[a + 1] - coff[a]
+        assert 1 <= k <= P.shape[2]
+        assert np.all(P[nodes][:, :, k:] == 0.0)
+        Q = P[nodes][:, :, :k].reshape(len(nodes) * ndof, k).astype(np.float64)
+        assert np.abs(Q.T @ Q - np.eye(k)).max() < 1e-5
+        M = rigid_and_constant_modes(mesh.coords, nodes, ndof)
+        M[fixed[nodes].ravel()] = 0.0
+        resid = M - Q @ (Q.T @ M)
+        assert np.abs(resid).max() <= 1e-5 * max(np.abs(M).max(), 1.0)
+        full += k == P.shape[2]
+    assert full >= n_agg // 2                                   # most aggregates keep every mode
