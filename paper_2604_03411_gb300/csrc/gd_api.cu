@@ -240,12 +240,13 @@ gd_status norms(gd::Handle &H, const double *R, NormPair &out)
 // next, and a slightly stale coarse level is still a good one): it is recomputed
 // after kCoarseReuse solves, for another kind of matrix, and as soon as a solve
 // converges at under 0.7 times the rate (log reduction per iteration) of the solve
-// that computed it.  kind: 0 the Newton tangent, 1 its transpose (adjoint), 2 a
+// that computed it.  kind: the Newton tangent, its transpose (adjoint), or a
 // caller's matrix (always recomputed, and not kept).
 constexpr int kCoarseReuse = 8;
+enum MatKind { kTangent = 0, kTransposed = 1, kCallerMatrix = 2 };
 
 gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, int &iters, double &rel,
-                 double rtol, bool inner_fp32 = false, double accept = -1.0, int kind = 0)
+                 double rtol, bool inner_fp32 = false, double accept = -1.0, int kind = kTangent)
 {
     gd::KrylovCtx kc;
     kc.n_nodes = H.n_nodes;
@@ -265,7 +266,8 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
     kc.up = H.krylov_up;
     kc.lmax = H.krylov_lmax;
     kc.coarse = H.coarse.nc > 0 ? &H.coarse : nullptr;
-    const bool refresh = kind == 2 || H.coarse_age < 0 || H.coarse_kind != kind || H.coarse_age >= kCoarseReuse;
+    const bool refresh =
+        kind == kCallerMatrix || H.coarse_age < 0 || H.coarse_kind != kind || H.coarse_age >= kCoarseReuse;
     kc.coarse_refresh = refresh;
     GD_CUDA(&H, cudaEventRecord(H.kv0, H.stream));
     bool fp32_vals = H.opt.precision == GD_MIXED;
@@ -288,7 +290,7 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
     rel = kout[1];
     if (kc.coarse) {
         const double rate = (iters > 0 && rel > 0.0 && std::isfinite(rel)) ? -std::log(rel) / iters : 0.0;
-        if (kind == 2) {
+        if (kind == kCallerMatrix) {
             H.coarse_age = -1;
         } else if (refresh) {
             H.coarse_age = 1;
@@ -390,7 +392,7 @@ gd_status krylov_true(gd::Handle &H, const double *vals, const double *b, double
     double *res = H.R_trial, *dx = H.kv[8], *y = H.diag;
     int kit = 0;
     double rel = 0.0;
-    const int kind = vals == H.vals_T ? 1 : 0;
+    const int kind = vals == H.vals_T ? kTransposed : kTangent;
     gd_status st = krylov(H, vals, b, x, kit, rel, rtol, false, std::max(rtol, 1e-10), kind);
     if (st) return st;
     double bn = 0.0;
@@ -1841,7 +1843,7 @@ gd_status gd_solve(gd_handle *h, const void *csr_vals, const double *b, double *
     int it = 0;
     double rel = 0.0;
     gd_status st = krylov(H, csr_vals ? csr_vals : H.vals, b, x, it, rel, H.opt.krylov_rtol, false, -1.0,
-                          csr_vals ? 2 : 0);
+                          csr_vals ? kCallerMatrix : kTangent);
     if (iterations) *iterations = it;
     if (rel_residual) *rel_residual = rel;
     return st;
