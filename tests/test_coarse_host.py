@@ -128,3 +128,23 @@ def test_coarse_basis_orthonormal_and_spanning(B, dim, target):
         assert np.abs(resid).max() <= 1e-5 * max(np.abs(M).max(), 1.0)
         full += k == P.shape[2]
     assert full >= n_agg // 2                                   # most aggregates keep every mode
+
+
+def test_degenerate_meshes(B):
+    """Nodes no element touches form aggregates of their own (the node graph has only
+    self-loops there); an aggregate whose displacements are all prescribed keeps only
+    the damage field's constant (the rotation and displacement columns vanish)."""
+    m = I.uniaxial_bc_2d(I.structured_q4(3, 2))
+    n_used = m.n_nodes
+    m.coords = np.concatenate([m.coords, [[5.0, 5.0], [6.0, 5.0]]])     # two isolated nodes
+    agg, n_agg = B.gd_coarse_aggregates(m, 4)
+    assert agg[n_used] != agg[n_used + 1]
+    assert np.sum(agg == agg[n_used]) == 1 and np.sum(agg == agg[n_used + 1]) == 1
+    # every dof of one isolated node prescribed: its aggregate keeps no column
+    m.bc_node = np.concatenate([m.bc_node, [n_used, n_used]]).astype(np.int32)
+    m.bc_comp = np.concatenate([m.bc_comp, [0, 1]]).astype(np.int8)
+    m.bc_scale = np.concatenate([m.bc_scale, [0.0, 0.0]])
+    agg, coff, P = B.gd_coarse_basis(m, 4)
+    a = agg[n_used]
+    assert coff[a + 1] - coff[a] == 1                     # only the damage field's constant remains
+    assert np.all(P[n_used, :2, :] == 0.0)
