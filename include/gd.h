@@ -159,6 +159,15 @@ typedef struct gd_options {
                                   equations as the monolithic one.                         */
     int32_t stagger_max;       /* alternations per load step before the step counts as failed
                                   (default 100)                                              */
+    int32_t asm_grid_max;      /* cap on the CTAs of the persistent element-kernel grid (0, the
+                                  default: SMs x resident CTAs).  A small cap makes every warp
+                                  take several element batches in turn; results do not depend
+                                  on it beyond the order of the atomic additions.            */
+    int32_t krylov_row_cache;  /* shared-memory copy of each Krylov block's matrix rows:
+                                  0 (default) column lists and values where they fit, else
+                                  column lists only; 1 column lists only; 2 none (every
+                                  product reads the rows from global memory).  Changes the
+                                  speed, not the iterates.                                  */
 } gd_options;
 
 typedef struct gd_newton_report {
@@ -194,7 +203,8 @@ typedef struct gd_handle gd_handle;
 /* Fills *opt with the defaults: FP64, newton_rtol 1e-10, newton_atol 1e-12,
  * newton_max 25, line_search_max 12, BiCGStab with krylov_rtol 1e-12 and
  * krylov_max 20000, local_max 100, checkpoint_every 5, max_step_cuts 4,
- * default stream, coarse 1536, monolithic scheme (stagger_max 100). */
+ * default stream, coarse 1536, monolithic scheme (stagger_max 100), no element
+ * grid cap, automatic Krylov row cache. */
 void gd_default_options(gd_options *opt);
 
 /* Creates a problem (Sec. 3.1 kernel inputs, Sec. 3.2 load path): copies and

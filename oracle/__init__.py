@@ -35,13 +35,24 @@ ENERGY = {"raw": 0, "iso": 1, "nh": 2}
 
 
 def build(force: bool = False) -> str:
-    """Compile gd_oracle.c into oracle/_build/libgdoracle.so (plain -O2, IEEE math)."""
+    """Compile gd_oracle.c into oracle/_build/libgdoracle.so (plain -O2, IEEE math),
+    with OpenMP over the element loop of or_assemble where the compiler has it
+    (results do not depend on the thread count)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _SO)
     return _SO
+
+
+def threads(n: int = 0) -> int:
+    """Sets the oracle's element-loop thread count (n > 0) and returns the count in use."""
+    return int(lib().or_threads(int(n)))
 
 
 _lib = None
@@ -89,6 +100,8 @@ def lib():
         L.or_element_energy.argtypes = [P, _dp, _dp, _dp]
         L.or_element_energy.restype = ctypes.c_double
         L.or_sizeof_mat.restype = ctypes.c_int
+        L.or_threads.argtypes = [ctypes.c_int]
+        L.or_threads.restype = ctypes.c_int
         assert L.or_sizeof_mat() == ctypes.sizeof(_OrMat), "oracle struct layout mismatch"
         _lib = L
     return _lib
@@ -381,3 +394,51 @@ def material_point_uniaxial(model: Model, stretches, tol=1e-13):
         out_l2.append(l2)
         out_k.append(kappa_n)
     return np.array(out_P), np.array(out_l2), np.array(out_k)
+
+
+# ---------------------------------------------------------------------------
+# homogeneous material-point driver (3D biaxial)
+# ---------------------------------------------------------------------------
+def material_point_biaxial(model: Model, stretches, tol=1e-13):
+    """Homogeneous 3D states F = diag(lam, lam, lam3) with P33 = 0: equal stretch of
+    the x and y faces, the z face traction free (the uniform-deformation block of
+    Sec. 5.2 under biaxial load).  As in the plane-strain driver, grad phi = 0 makes
+    the phi-equation give phi = kappa, so q_nloc = 0 and on loading kappa = G(psi_e)
+    (Sec. 5.1).  lam3 is found by a bracketed root search on P33.
+    Returns arrays (P11, lam3, kappa) along the stretch history; P11 is also the
+    reaction of a unit cube's x = 1 face."""
+    from scipy.optimize import brentq
+    assert model.dim == 3
+    kappa_n = 0.0
+    out_P, out_l3, out_k = [], [], []
+    lam3_prev = 1.0
+
+    def state(lam, lam3, kn):
+        z = np.zeros(13)
+        z[0] = lam - 1.0
+        z[4] = lam - 1.0
+        z[8] = lam3 - 1.0
+        pe = model.psi_value(z)
+        G, _ = model.yield_G(pe)
+        z[9] = max(kn, G)
+        dP, _, info = model.qp(z, kn, tangent=False)
+        return dP, info
+
+    for lam in stretches:
+        f = lambda l3: state(lam, l3, kappa_n)[0][8]
+        a, b = lam3_prev * 0.7, lam3_prev * 1.3
+        fa, fb = f(a), f(b)
+        k = 0
+        while fa * fb > 0 and k < 60:
+            a *= 0.9
+            b *= 1.1
+            fa, fb = f(a), f(b)
+            k += 1
+        l3 = brentq(f, a, b, xtol=tol, rtol=1e-15, maxiter=500)
+        dP, info = state(lam, l3, kappa_n)
+        kappa_n = info[0]
+        lam3_prev = l3
+        out_P.append(dP[0])
+        out_l3.append(l3)
+        out_k.append(kappa_n)
+    return np.array(out_P), np.array(out_l3), np.array(out_k)

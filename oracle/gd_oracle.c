@@ -37,6 +37,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------ */
 /* hyper-dual numbers                                                  */
@@ -591,31 +594,65 @@ int or_element(const or_mat *m, const double *Xe, const double *de, const double
 
 /* Whole-mesh loop of or_element.  R[n_nodes*ndof] is overwritten with the
  * assembled residual; Ke_all[E*nd*nd] receives every element matrix (NULL to
- * skip); kappa_new[E*nq]; qinfo[E*nq*6] optional.  Elements [e0, e1). */
+ * skip); kappa_new[E*nq]; qinfo[E*nq*6] optional.  Elements [e0, e1).
+ * When built with OpenMP the elements are computed on several threads (each
+ * element independently, into its own slots); the element residuals are then
+ * added into R one element after another in element order, so R is the same
+ * to the last bit for any thread count. */
 int64_t or_assemble(const or_mat *m, int64_t n_nodes, int64_t e0, int64_t e1, const int32_t *conn,
                     const double *X, const double *dofs, const double *kappa_n, double *R, double *Ke_all,
                     double *kappa_new, double *qinfo)
 {
     int dim = m->dim, nen = nen_of(dim), nq = nq_of(dim), ndof = dim + 1, nd = nen * ndof;
     memset(R, 0, sizeof(double) * (size_t)(n_nodes * ndof));
-    int64_t fails = 0;
-    double Xe[24], de[32], Re[32];
+    if (e1 <= e0) return 0;
+    double *Re_all = (double *)malloc(sizeof(double) * (size_t)(e1 - e0) * (size_t)nd);
+    if (!Re_all) return -1 - e0;
+    int64_t fails = 0, bad = e1;
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : fails)
     for (int64_t e = e0; e < e1; ++e) {
+        double Xe[24], de[32];
         for (int a = 0; a < nen; ++a) {
             int32_t n = conn[e * nen + a];
             for (int J = 0; J < dim; ++J) Xe[a * dim + J] = X[(int64_t)n * dim + J];
             for (int c = 0; c < ndof; ++c) de[a * ndof + c] = dofs[(int64_t)n * ndof + c];
         }
-        int f = or_element(m, Xe, de, kappa_n + e * nq, Re, Ke_all ? Ke_all + (e - e0) * nd * nd : NULL,
-                           kappa_new ? kappa_new + e * nq : NULL, qinfo ? qinfo + e * nq * 6 : NULL);
-        if (f < 0) return -1 - e;
-        fails += f;
+        int f = or_element(m, Xe, de, kappa_n + e * nq, Re_all + (e - e0) * nd,
+                           Ke_all ? Ke_all + (e - e0) * nd * nd : NULL, kappa_new ? kappa_new + e * nq : NULL,
+                           qinfo ? qinfo + e * nq * 6 : NULL);
+        if (f < 0) {
+#pragma omp critical
+            if (e < bad) bad = e;
+        } else {
+            fails += f;
+        }
+    }
+    if (bad < e1) {
+        free(Re_all);
+        return -1 - bad;
+    }
+    for (int64_t e = e0; e < e1; ++e) {
+        const double *Re = Re_all + (e - e0) * nd;
         for (int a = 0; a < nen; ++a) {
             int32_t n = conn[e * nen + a];
             for (int c = 0; c < ndof; ++c) R[(int64_t)n * ndof + c] += Re[a * ndof + c];
         }
     }
+    free(Re_all);
     return fails;
+}
+
+/* Number of threads of the element loop (OpenMP builds; 1 otherwise).  n <= 0
+ * leaves the setting unchanged.  Returns the number that the loop will use. */
+int or_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* ------------------------------------------------------------------ */

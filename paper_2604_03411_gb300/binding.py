@@ -60,7 +60,8 @@ class GdOptions(ctypes.Structure):
                 ("krylov_rtol", ctypes.c_double), ("krylov_max", ctypes.c_int32), ("gmres_m", ctypes.c_int32),
                 ("local_max", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
                 ("max_step_cuts", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p), ("inner_solve", ctypes.c_int32),
-                ("coarse", ctypes.c_int32), ("scheme", ctypes.c_int32), ("stagger_max", ctypes.c_int32)]
+                ("coarse", ctypes.c_int32), ("scheme", ctypes.c_int32), ("stagger_max", ctypes.c_int32),
+                ("asm_grid_max", ctypes.c_int32), ("krylov_row_cache", ctypes.c_int32)]
 
 
 class GdNewtonReport(ctypes.Structure):

@@ -265,6 +265,7 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
     kc.num_sms = H.num_sms;
     kc.up = H.krylov_up;
     kc.lmax = H.krylov_lmax;
+    kc.row_cache = H.opt.krylov_row_cache;
     kc.coarse = H.coarse.nc > 0 ? &H.coarse : nullptr;
     const bool refresh =
         kind == kCallerMatrix || H.coarse_age < 0 || H.coarse_kind != kind || H.coarse_age >= kCoarseReuse;
@@ -1463,6 +1464,9 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
     if (o.scheme != GD_MONOLITHIC && o.scheme != GD_STAGGERED) return fail(nullptr, GD_ERR_ARG, "scheme");
     if (o.scheme == GD_STAGGERED && (n_spec > 1 || o.stagger_max < 1))
         return fail(nullptr, GD_ERR_ARG, "the staggered scheme needs one specimen and stagger_max >= 1");
+    if (o.asm_grid_max < 0) return fail(nullptr, GD_ERR_ARG, "asm_grid_max must be >= 0");
+    if (o.krylov_row_cache < 0 || o.krylov_row_cache > 2)
+        return fail(nullptr, GD_ERR_ARG, "krylov_row_cache must be 0, 1 or 2");
 
     const int dim = mesh->dim, nen = dim == 2 ? 4 : 8, ndof = dim + 1;
     const int64_t NN = mesh->n_nodes, NE = mesh->n_elems;
@@ -1490,6 +1494,7 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
     H.n_dofs = n_dofs;
     H.nnz = nnz;
     H.opt = o;
+    H.asm_tune.grid_max = o.asm_grid_max;
     H.stream = (cudaStream_t)o.cuda_stream;
     H.load.assign(path->load, path->load + path->n_steps);
     H.n_spec = n_spec;

@@ -893,7 +893,7 @@ size_t smem_bytes(int wmax)
 }
 
 template <int DIM, int KW>
-cudaError_t launch_kw(const AsmArgs &a, int num_sms, int cta_per_sm, cudaStream_t s)
+cudaError_t launch_kw(const AsmArgs &a, int num_sms, const AsmTune &t, cudaStream_t s)
 {
     size_t sm = smem_bytes<DIM>(a.wmax) * KW;
     int dev = 0, optin = 0;
@@ -907,12 +907,13 @@ cudaError_t launch_kw(const AsmArgs &a, int num_sms, int cta_per_sm, cudaStream_
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, asm_fp32_kernel<DIM, KW>, 32 * KW, sm);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) per_sm = 1;
-    if (cta_per_sm > 0 && cta_per_sm < per_sm) per_sm = cta_per_sm;
+    if (t.cta_per_sm > 0 && t.cta_per_sm < per_sm) per_sm = t.cta_per_sm;
     using G_ = Geo<DIM>;
     int64_t batches = (a.n_elems + G_::EPW - 1) / G_::EPW;
     int64_t need = (batches + KW - 1) / KW;
     int64_t grid = (int64_t)num_sms * per_sm;
     if (grid > need) grid = need;
+    if (t.grid_max > 0 && grid > t.grid_max) grid = t.grid_max;
     if (grid < 1) grid = 1;
     asm_fp32_kernel<DIM, KW><<<(unsigned)grid, 32 * KW, sm, s>>>(a);
     return cudaGetLastError();
@@ -926,17 +927,17 @@ cudaError_t launch_dim(const AsmArgs &a, int num_sms, const AsmTune &t, cudaStre
 {
     if (t.exact) {
         switch (t.warps) {
-        case 1: return launch_kw<DIM, 1>(a, num_sms, t.cta_per_sm, s);
-        case 2: return launch_kw<DIM, 2>(a, num_sms, t.cta_per_sm, s);
-        case 8: return launch_kw<DIM, 8>(a, num_sms, t.cta_per_sm, s);
-        default: return launch_kw<DIM, 4>(a, num_sms, t.cta_per_sm, s);
+        case 1: return launch_kw<DIM, 1>(a, num_sms, t, s);
+        case 2: return launch_kw<DIM, 2>(a, num_sms, t, s);
+        case 8: return launch_kw<DIM, 8>(a, num_sms, t, s);
+        default: return launch_kw<DIM, 4>(a, num_sms, t, s);
         }
     }
     cudaError_t e = cudaErrorInvalidConfiguration;
-    if (t.warps >= 8) e = launch_kw<DIM, 8>(a, num_sms, t.cta_per_sm, s);
-    if (e == cudaErrorInvalidConfiguration && t.warps >= 4) e = launch_kw<DIM, 4>(a, num_sms, t.cta_per_sm, s);
-    if (e == cudaErrorInvalidConfiguration && t.warps >= 2) e = launch_kw<DIM, 2>(a, num_sms, t.cta_per_sm, s);
-    if (e == cudaErrorInvalidConfiguration) e = launch_kw<DIM, 1>(a, num_sms, t.cta_per_sm, s);
+    if (t.warps >= 8) e = launch_kw<DIM, 8>(a, num_sms, t, s);
+    if (e == cudaErrorInvalidConfiguration && t.warps >= 4) e = launch_kw<DIM, 4>(a, num_sms, t, s);
+    if (e == cudaErrorInvalidConfiguration && t.warps >= 2) e = launch_kw<DIM, 2>(a, num_sms, t, s);
+    if (e == cudaErrorInvalidConfiguration) e = launch_kw<DIM, 1>(a, num_sms, t, s);
     return e;
 }
 

@@ -103,6 +103,7 @@ struct AsmTune {
     int warps = 4;
     int cta_per_sm = 0;
     bool exact = false;      // true: fail instead of falling back to a narrower CTA that fits
+    int grid_max = 0;        // cap on the persistent grid's CTAs (gd_options.asm_grid_max; 0: none)
 };
 // Batched specimens: the Krylov grid's blocks take contiguous node chunks and
 // every specimen runs its own BiCGStab recurrences (own scalars, own stopping
@@ -356,6 +357,7 @@ struct KrylovCtx {
     int lmax = 0;               // longest row (0: rows are not copied to shared memory)
     const CoarseSpace *coarse = nullptr;   // two-level preconditioner (single systems; null: Jacobi only)
     bool coarse_refresh = true;            // recompute P^T A P and its inverse before the solve
+    int row_cache = 0;                     // gd_options.krylov_row_cache: 0 automatic, 1 column lists only, 2 none
 };
 cudaError_t krylov_solve_batch(const KrylovCtx &c, const BatchKrylov &L, const void *vals, bool fp32_vals,
                                const double *b, double *x, int max_it, bool fp32_vectors);

@@ -1353,7 +1353,7 @@ cudaError_t solve_t(const KrylovCtx &c, const V *vals, const double *b, double *
     // The products then wait on the gathered x alone instead of the chain
     // row pointer -> column index -> x.
     size_t smem = 0;
-    if (c.lmax > 0) {
+    if (c.lmax > 0 && c.row_cache < 2) {
         using M = RowMap<NDOF, G, T>;
         const int64_t nw = (int64_t)c.blocks * (kThreads / 32);
         const int64_t passes = (c.n_nodes + nw * M::NPW - 1) / (nw * M::NPW);
@@ -1375,6 +1375,7 @@ cudaError_t solve_t(const KrylovCtx &c, const V *vals, const double *b, double *
         for (int mi = 0; mi < 4 && A.cache == 0; ++mi) {
             const int mode = modes[mi][0], xs = want_xs ? modes[mi][1] : 0;
             if (!want_xs && modes[mi][1]) continue;
+            if (mode == 2 && c.row_cache == 1) continue;      // column lists only
             const size_t sm = colb + (mode == 2 ? valb : 0) + cob + (xs ? xsb : 0);
             if (sm > 200 * 1024) continue;
             if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {

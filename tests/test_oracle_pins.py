@@ -362,6 +362,28 @@ def test_homogeneous_patch_matches_material_point():
         np.testing.assert_allclose(d[:, 1], (lam2[s] - 1.0) * y, rtol=1e-8, atol=1e-11)
 
 
+def test_biaxial_block_matches_material_point():
+    """Biaxial stretch of a HEX8 block with rollers on three faces and a free top
+    face (the uniform-deformation block of Sec. 5.2): the FE solution is homogeneous,
+    F = diag(lam, lam, lam3) with P33 = 0, phi = kappa, and the x-face reaction of the
+    unit cube equals P11 of the 3D material-point driver along a load-unload-reload
+    history (Sec. 5.1, phi = kappa)."""
+    p = I.config3(n=3, n_steps=10)
+    m = oracle.Model.from_problem(p)
+    load = I.piecewise_path([0.0, 0.4, 0.2, 0.45], [4, 2, 3])
+    res = oracle.run_load_path(m, p.mesh, load, keep_states=True)
+    P11, lam3, kap = oracle.material_point_biaxial(m, 1.0 + load)
+    assert kap[-1] > kap[3] > 0.5, "the path should damage the block and damage again on reloading"
+    np.testing.assert_allclose(res["reaction"], P11, rtol=0, atol=1e-9 * np.abs(P11).max())
+    np.testing.assert_array_equal(kap[4:6], kap[3])           # unloading keeps the history
+    z = p.mesh.coords[:, 2]
+    for s, (dofs, kappa, qi) in enumerate(res["states"]):
+        np.testing.assert_allclose(kappa, kap[s], rtol=1e-9, atol=1e-12)
+        d = dofs.reshape(-1, 4)
+        np.testing.assert_allclose(d[:, 3], kap[s], rtol=1e-8, atol=1e-11)
+        np.testing.assert_allclose(d[:, 2], (lam3[s] - 1.0) * z, rtol=1e-8, atol=1e-11)
+
+
 def test_mullins_load_unload_reload():
     """Sec. 1: unloading and reloading follow the same curve below the previous
     maximum stretch, kappa is frozen there, and damage resumes beyond it."""
