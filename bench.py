@@ -398,13 +398,15 @@ def run_gd(args):
     # the device-timed loop: each step uploads the committed state (dofs, the previous
     # step's dofs for the predictor, kappa) from pinned host memory and reads the new
     # state back ---
-    d_np, dp_np, k_np, nxt = saved
-    if nxt == 0 or nxt + args.steps > n_path:      # no history to restart from: begin after step 0
+    d_np, dp_np, k_np, nxt, dpp_np = saved
+    if nxt < 2 or nxt + args.steps > n_path:      # no history to restart from: begin after step 1
         B.gd_set_state(h, np.zeros_like(d_np), np.zeros_like(k_np), 0)
         B.gd_newton_step(h)
-        d_np, dp_np, k_np, nxt = B.gd_get_state(h)
+        B.gd_newton_step(h)
+        d_np, dp_np, k_np, nxt, dpp_np = B.gd_get_state(h)
     d_host = torch.from_numpy(d_np).pin_memory().numpy()
     dp_host = torch.from_numpy(dp_np).pin_memory().numpy()
+    dpp_host = torch.from_numpy(dpp_np).pin_memory().numpy()
     k_host = torch.from_numpy(k_np).pin_memory().numpy()
     e2e_ms = 0.0
     e2e_units = 0
@@ -412,13 +414,13 @@ def run_gd(args):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        B.gd_set_state(h, d_host, k_host, nxt, dofs_prev=dp_host)    # host -> device
+        B.gd_set_state(h, d_host, k_host, nxt, dofs_prev=dp_host, dofs_prev2=dpp_host)    # host -> device
         r = B.gd_newton_step(h)
-        d2, dp2, k2, nxt2 = B.gd_get_state(h)                         # device -> host
+        d2, dp2, k2, nxt2, dpp2 = B.gd_get_state(h)                                       # device -> host
         e2e_ms += (time.perf_counter() - t0) * 1e3
         e2e_units += n_qp * (r.iterations + 1 + 2 * r.step_cuts)
-        d_host[:], dp_host[:], k_host[:], nxt = d2, dp2, k2, nxt2
-    h2d = d_host.nbytes + dp_host.nbytes + k_host.nbytes
+        d_host[:], dp_host[:], dpp_host[:], k_host[:], nxt = d2, dp2, dpp2, k2, nxt2
+    h2d = d_host.nbytes + dp_host.nbytes + dpp_host.nbytes + k_host.nbytes
     e2e = {"value": e2e_units / (e2e_ms / 1e3) * (world if world > 1 else 1), "unit": UNIT,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d)}
 

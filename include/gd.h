@@ -61,6 +61,7 @@ enum { GD_BICGSTAB = 0, GD_GMRES = 1 };
 enum { GD_ASM_RESIDUAL = 0, GD_ASM_TANGENT = 1 };
 enum { GD_INNER_AUTO = 0, GD_INNER_FP64 = 1, GD_INNER_REFINED = 2 };
 enum { GD_MONOLITHIC = 0, GD_STAGGERED = 1 };
+enum { GD_ICNN_AUTO = 0, GD_ICNN_CUDA_CORES = 1, GD_ICNN_BF16 = 2, GD_ICNN_BF16X3 = 3 };
 
 /* Mesh and boundary data (Sec. 3.1, Table kernel_inputs; Dirichlet data of the
  * incremental load, Sec. 3.2).
@@ -168,6 +169,20 @@ typedef struct gd_options {
                                   column lists only; 1 column lists only; 2 none (every
                                   product reads the rows from global memory).  Changes the
                                   speed, not the iterates.                                  */
+    int32_t icnn_mma;          /* arithmetic of the networks' second layers in GD_MIXED (Sec. 4.2
+                                  ICNNs; the layer is a dense contraction over the points of a
+                                  thread block):
+                                  GD_ICNN_CUDA_CORES  FP32 on the CUDA cores;
+                                  GD_ICNN_BF16        tensor cores, BF16 operands, FP32
+                                                      accumulation;
+                                  GD_ICNN_BF16X3      tensor cores, every operand split into
+                                                      a BF16 high part and a BF16 residual,
+                                                      three products accumulated in FP32
+                                                      (about 16 significant bits);
+                                  GD_ICNN_AUTO (0, the default) GD_ICNN_BF16X3 for a single
+                                  specimen, GD_ICNN_CUDA_CORES for batches.  The tensor-core
+                                  modes need a single specimen (GD_ERR_ARG for batches).
+                                  Ignored in GD_FP64.                                        */
 } gd_options;
 
 typedef struct gd_newton_report {
@@ -204,7 +219,7 @@ typedef struct gd_handle gd_handle;
  * newton_max 25, line_search_max 12, BiCGStab with krylov_rtol 1e-12 and
  * krylov_max 20000, local_max 100, checkpoint_every 5, max_step_cuts 4,
  * default stream, coarse 1536, monolithic scheme (stagger_max 100), no element
- * grid cap, automatic Krylov row cache. */
+ * grid cap, automatic Krylov row cache, automatic network arithmetic. */
 void gd_default_options(gd_options *opt);
 
 /* Creates a problem (Sec. 3.1 kernel inputs, Sec. 3.2 load path): copies and
@@ -330,18 +345,21 @@ gd_status gd_coarse_basis(const gd_mesh *mesh, int32_t target_nodes, int32_t *ag
 #define GD_NOALLOC_MAX_DOFS 131072
 
 /* Krylov solve that allocates no device memory (the paper has no counterpart;
- * this exists for callers that cannot call cudaMalloc -- code that runs while a
- * CUDA graph is being captured, applications whose own pool owns the device
- * memory, runtimes that forbid allocation after start-up).
+ * this exists for callers that cannot call cudaMalloc -- applications whose own
+ * pool owns all of the device memory, runtimes that forbid allocation after
+ * start-up).
  * Solves K x = b on the free dofs of a caller-provided node-block CSR system
- * (the layout of gd_csr_pattern, ndof 3 or 4, FP64 values) with the persistent
- * BiCGStab of gd_solve and node-block Jacobi alone (no coarse level: it would need
- * work space of its own).  All arrays are device pointers owned
+ * (the layout of gd_csr_pattern, ndof 3 or 4, FP64 values: every node's rows
+ * share one ascending column list, and that list holds the node's own ndof x
+ * ndof diagonal block, whose inverse preconditions the solve) with the persistent
+ * BiCGStab of gd_solve and node-block Jacobi alone (no coarse level: it would
+ * need work space of its own).  All arrays are device pointers owned
  * by the caller: rowptr [n_nodes*ndof + 1], colidx, vals [nnz], fixed
  * [n_nodes*ndof] (1 = prescribed dof), b, x [n_nodes*ndof]; prescribed dofs of x
  * come back as 0.  iterations and rel_residual (host, may be NULL) report the
  * solve.  Work runs on `stream` (a cudaStream_t, NULL for the legacy default
- * stream), which the call synchronises.
+ * stream); the call copies its result words to host memory and synchronises
+ * `stream` before it returns.
  * Work space: one fixed device array inside the library, sized for
  * GD_NOALLOC_MAX_DOFS dofs (about 13.7 MB), held by every GPU that loads the
  * library until the process exits; larger systems are rejected with GD_ERR_ARG.
@@ -399,21 +417,26 @@ gd_status gd_get_fields(gd_handle *h, double *dofs, double *kappa, double *damag
 
 /* Overwrites the committed state from host arrays and sets the next step index.
  * dofs, kappa as in gd_get_fields (NULL keeps the handle's).  dofs_prev (may be
- * NULL) is the converged state of step next_step - 1's predecessor, i.e. the
- * state one step before `dofs`: with it the next step's initial guess
- * extrapolates the last increment linearly; without it the next step starts from
- * `dofs` itself.  (An uninterrupted run takes the quadratic through its last three
- * converged states where the path is monotone; after gd_set_state that resumes
- * once two more steps are committed.  The converged states agree to the Newton
- * tolerance either way.) */
-gd_status gd_set_state(gd_handle *h, const double *dofs, const double *dofs_prev, const double *kappa,
-                       int32_t next_step);
+ * NULL) is the converged state one step before `dofs` (needs next_step >= 1) and
+ * dofs_prev2 (may be NULL) the one two steps before (needs dofs_prev and next_step
+ * >= 2).  The next step's initial guess extrapolates from the states given: the
+ * quadratic through all three where the path is monotone (as an uninterrupted run
+ * does), the last increment linearly with dofs_prev alone, else `dofs` itself; the
+ * converged states agree to the Newton tolerance either way.  The coarse level of
+ * the preconditioner and the mixed-precision residual-noise estimate are kept:
+ * the coarse inverse is recomputed when a solve slows down or fails with it, the
+ * noise estimate at its usual interval.  gd_get_state gives the arrays that
+ * continue the path. */
+gd_status gd_set_state(gd_handle *h, const double *dofs, const double *dofs_prev, const double *dofs_prev2,
+                       const double *kappa, int32_t next_step);
 
-/* Copies the committed state to host: dofs, dofs_prev (the state one committed
- * step earlier, the predictor's second point) [n_nodes*ndof], kappa
- * [n_elems*nq]; any may be NULL.  next_step (may be NULL) receives the index of
- * the next load step.  gd_set_state(dofs, dofs_prev, kappa, next_step) restores it. */
-gd_status gd_get_state(gd_handle *h, double *dofs, double *dofs_prev, double *kappa, int32_t *next_step);
+/* Copies the committed state to host: dofs, dofs_prev and dofs_prev2 (the states
+ * one and two committed steps earlier, the predictor's other points)
+ * [n_nodes*ndof], kappa [n_elems*nq]; any may be NULL.  next_step (may be NULL)
+ * receives the index of the next load step.  gd_set_state(dofs, dofs_prev,
+ * dofs_prev2, kappa, next_step) restores it. */
+gd_status gd_get_state(gd_handle *h, double *dofs, double *dofs_prev, double *dofs_prev2, double *kappa,
+                       int32_t *next_step);
 
 /* Message for the last non-OK status of this handle (or of gd_create when h is NULL). */
 const char *gd_last_error(const gd_handle *h);

@@ -69,7 +69,9 @@ class _OrMat(ctypes.Structure):
                 ("psi_p", _dp), ("y_p", _dp),
                 ("local_max", ctypes.c_int),
                 ("psi_N0", ctypes.c_double), ("psi_n", ctypes.c_double),
-                ("y_N0", ctypes.c_double), ("y_s", ctypes.c_double)]
+                ("y_N0", ctypes.c_double), ("y_s", ctypes.c_double),
+                ("seeded", ctypes.c_int), ("psi_ph", ctypes.c_void_p), ("y_ph", ctypes.c_void_p),
+                ("c_hd", ctypes.c_double * 16)]
 
 
 def lib():
@@ -100,6 +102,8 @@ def lib():
         L.or_element_energy.argtypes = [P, _dp, _dp, _dp]
         L.or_element_energy.restype = ctypes.c_double
         L.or_sizeof_mat.restype = ctypes.c_int
+        L.or_element_sens.argtypes = [P, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.or_element_sens.restype = ctypes.c_int
         L.or_threads.argtypes = [ctypes.c_int]
         L.or_threads.restype = ctypes.c_int
         assert L.or_sizeof_mat() == ctypes.sizeof(_OrMat), "oracle struct layout mismatch"
@@ -178,6 +182,33 @@ class Model:
                                        _ptr(_f64(kappa).ravel()))
 
     # -- element -------------------------------------------------------
+    @property
+    def n_theta(self):
+        """Number of network weights theta = [psi params | yield params]."""
+        def size(n_in, w):
+            return w * n_in + w + w * w + w * n_in + w + w + n_in if w > 0 else 0
+        npsi = 0 if self.m.energy == ENERGY["nh"] else size(3, self.m.psi_w)
+        return npsi + size(1, self.m.y_w)
+
+    def element_sens(self, Xe, de, kappa_n):
+        """Partial derivatives of an element's converged-step outputs (see or_element_sens):
+        dR/dtheta [nd, nth], dkappa_new/dtheta [nq, nth], dR/dkappa_n [nd, nq],
+        dkappa_new/dkappa_n [nq], dkappa_new/dd [nq, nd]."""
+        nen = 4 if self.dim == 2 else 8
+        nq = nen
+        nd = nen * (self.dim + 1)
+        nth = self.n_theta
+        dR = np.zeros(nd * nth)
+        dk = np.zeros(nq * nth)
+        dRk = np.zeros(nd * nq)
+        dkk = np.zeros(nq)
+        dkd = np.zeros(nq * nd)
+        f = lib().or_element_sens(ctypes.byref(self.m), _ptr(_f64(Xe).ravel()), _ptr(_f64(de).ravel()),
+                                  _ptr(_f64(kappa_n).ravel()), _ptr(dR), _ptr(dk), _ptr(dRk), _ptr(dkk), _ptr(dkd))
+        if f < 0:
+            raise ValueError("non-positive element Jacobian")
+        return dR.reshape(nd, nth), dk.reshape(nq, nth), dRk.reshape(nd, nq), dkk, dkd.reshape(nq, nd)
+
     def element(self, Xe, de, kappa_n, tangent=True):
         nen = 4 if self.dim == 2 else 8
         nq = nen
@@ -348,6 +379,72 @@ def run_load_path(model: Model, mesh, load, dofs0=None, kappa0=None, rtol=1e-10,
             states.append((dofs.copy(), kappa.copy(), res.qinfo.copy()))
     return {"reaction": np.array(reac), "iterations": np.array(iters), "dofs": dofs, "kappa": kappa,
             "states": states, "cuts": hist["cuts"]}
+
+
+# ---------------------------------------------------------------------------
+# discrete adjoint of the load path
+# ---------------------------------------------------------------------------
+def adjoint_gradient(model: Model, mesh, load, dL_dF, rtol=1e-12, atol=1e-14):
+    """Gradient dL/dtheta of a loss of the reaction curve, L(F_1..F_N) with the
+    weights dL_dF[n] = dL/dF_n given, through the whole quasi-static path (Sec. 3.2
+    monolithic steps), by the discrete adjoint with every state stored.  Step n has
+    the equilibrium R_free(d_n, kappa_{n-1}; theta) = 0 with the local update
+    kappa_n = K(d_n, kappa_{n-1}; theta) inside (Eq. (dd_7_no_nn)) and the reaction
+    F_n = e_r . R(d_n, kappa_{n-1}; theta).  Backwards from n = N with mu_N = 0
+    (mu_n = dL/dkappa_n, one entry per qp):
+        K_ff^T lambda_n = w_n dF_n/dd + mu_n dK_n/dd            (free dofs)
+        dL/dtheta     += w_n dF_n/dtheta + mu_n dK_n/dtheta - lambda_n . dR_free/dtheta
+        mu_{n-1}       = w_n dF_n/dkappa_{n-1} + mu_n dK_n/dkappa_{n-1}
+                         - lambda_n . dR_free/dkappa_{n-1}
+    The partial derivatives come from the element routine (hyper-dual numbers,
+    or_element_sens); the transposed systems are solved by sparse LU (the paper's
+    direct solve).  Needs a path that converges without step cuts.  Returns
+    (gradient [n_theta], reaction curve [N])."""
+    res = run_load_path(model, mesh, load, rtol=rtol, atol=atol, keep_states=True)
+    if res["cuts"]:
+        raise RuntimeError("the adjoint check needs a path without step cuts")
+    N = len(load)
+    E, nq, nd_n = mesh.n_elems, mesh.nq, mesh.ndof
+    n = mesh.n_nodes * nd_n
+    edm = element_dof_map(mesh)                        # [E, nd]
+    bidx, _ = dirichlet(mesh)
+    free = np.ones(n, bool)
+    free[bidx] = False
+    fidx = np.nonzero(free)[0]
+    er = np.zeros(n)
+    er[mesh.react_node.astype(np.int64) * nd_n + mesh.react_comp] = 1.0
+    nth = model.n_theta
+    grad = np.zeros(nth)
+    mu = np.zeros((E, nq))
+    X = mesh.coords
+    for s in range(N - 1, -1, -1):
+        d = res["states"][s][0]
+        kprev = res["states"][s - 1][1] if s > 0 else np.zeros((E, nq))
+        R, Ke, _, _, _ = model.assemble(mesh, d, kprev)
+        K = global_matrix(mesh, Ke)
+        dR_th = np.zeros((n, nth))
+        dR_kp = sp.lil_matrix((n, E * nq))
+        dk_th = np.zeros((E, nq, nth))
+        dk_kp = np.zeros((E, nq))
+        dk_d = np.zeros(n)                             # mu_n . dK_n/dd, scattered to dofs
+        for e in range(E):
+            c = mesh.conn[e]
+            a, b, cc, dd, ee = model.element_sens(X[c], d.reshape(-1, nd_n)[c], kprev[e])
+            np.add.at(dR_th, edm[e], a)
+            dk_th[e] = b
+            for q in range(nq):
+                dR_kp[edm[e], e * nq + q] = cc[:, q:q + 1]
+            dk_kp[e] = dd
+            np.add.at(dk_d, edm[e], mu[e] @ ee)
+        dR_kp = dR_kp.tocsr()
+        w = float(dL_dF[s])
+        rhs = w * (K.T @ er) + dk_d
+        Kff = K[fidx][:, fidx].tocsc()
+        lam = np.zeros(n)
+        lam[fidx] = spla.spsolve(Kff.T.tocsc(), rhs[fidx])
+        grad += w * (er @ dR_th) + np.einsum("eq,eqk->k", mu, dk_th) - lam[fidx] @ dR_th[fidx]
+        mu = (w * (dR_kp.T @ er) + (mu * dk_kp).ravel() - dR_kp[fidx].T @ lam[fidx]).reshape(E, nq)
+    return grad, res["reaction"]
 
 
 # ---------------------------------------------------------------------------

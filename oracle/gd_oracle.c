@@ -96,6 +96,13 @@ typedef struct {
     int local_max;    /* cap on local (kappa) iterations */
     /* filled by or_prepare */
     double psi_N0, psi_n, y_N0, y_s;
+    /* derivatives with respect to the network weights (the discrete adjoint's
+     * element sensitivities): when seeded != 0 the networks read their parameters
+     * from the hyper-dual copies psi_ph / y_ph, one entry of which carries a unit
+     * derivative, and the normalising constants from the hyper-dual c_* */
+    int seeded;
+    const hd *psi_ph, *y_ph;
+    hd c_N0, c_n, c_yN0, c_ys;
 } or_mat;
 
 /* Two-layer input-convex network (Amos et al.), softplus activations, input
@@ -119,6 +126,28 @@ static hd icnn(const double *p, int n_in, int w, const hd *x)
         for (int j = 0; j < w; ++j) h = hadd(h, hscale(z1[j], W2[k * w + j]));
         for (int i = 0; i < n_in; ++i) h = hadd(h, hscale(x[i], A2[k * n_in + i]));
         out = hadd(out, hscale(hsoftplus(h), w3[k]));
+    }
+    return out;
+}
+
+/* The same network with hyper-dual parameters (weight derivatives). */
+static hd icnn_p(const hd *p, int n_in, int w, const hd *x)
+{
+    const hd *W1 = p, *b1 = W1 + w * n_in, *W2 = b1 + w, *A2 = W2 + w * w, *b2 = A2 + w * n_in, *w3 = b2 + w,
+             *a3 = w3 + w;
+    hd z1[256];
+    for (int j = 0; j < w; ++j) {
+        hd h = b1[j];
+        for (int i = 0; i < n_in; ++i) h = hadd(h, hmul(x[i], W1[j * n_in + i]));
+        z1[j] = hsoftplus(h);
+    }
+    hd out = hc(0.0);
+    for (int i = 0; i < n_in; ++i) out = hadd(out, hmul(x[i], a3[i]));
+    for (int k = 0; k < w; ++k) {
+        hd h = b2[k];
+        for (int j = 0; j < w; ++j) h = hadd(h, hmul(z1[j], W2[k * w + j]));
+        for (int i = 0; i < n_in; ++i) h = hadd(h, hmul(x[i], A2[k * n_in + i]));
+        out = hadd(out, hmul(hsoftplus(h), w3[k]));
     }
     return out;
 }
@@ -183,8 +212,14 @@ static hd psi_e(const or_mat *m, hd H[3][3])
         /* I2G - 3 = 3 ((I2/3)^3 J^(-4) - 1) */
         xi[1] = hscale(hexpm1(hsub(hscale(hlog1p(hscale(x[1], 1.0 / 3.0)), 3.0), hscale(L, 4.0))), 3.0);
     }
-    hd N = icnn(m->psi_p, 3, m->psi_w, xi);
-    hd iso = hsub(hsub(N, hc(m->psi_N0)), hscale(x[2], m->psi_n));
+    hd N, iso;
+    if (m->seeded) {
+        N = icnn_p(m->psi_ph, 3, m->psi_w, xi);
+        iso = hsub(hsub(N, m->c_N0), hmul(x[2], m->c_n));
+    } else {
+        N = icnn(m->psi_p, 3, m->psi_w, xi);
+        iso = hsub(hsub(N, hc(m->psi_N0)), hscale(x[2], m->psi_n));
+    }
     /* psi_vol = (J + 1/J - 2)^2 = ((J-1)^2 / J)^2 */
     hd t = hdiv(hsq(x[2]), hadd(hc(1.0), x[2]));
     return hadd(hscale(iso, m->mu_e), hscale(hsq(t), m->lambda_e));
@@ -267,6 +302,7 @@ static hd q_force(const or_mat *m, hd pe, hd phi, hd kappa)
 static hd yield_G(const or_mat *m, hd q)
 {
     if (m->y_w == 0) return q;      /* closed-form model: Phi_d = q - kappa (Eq. (ostwald_potential)) */
+    if (m->seeded) return hmul(hsub(icnn_p(m->y_ph, 1, m->y_w, &q), m->c_yN0), m->c_ys);
     hd N = icnn(m->y_p, 1, m->y_w, &q);
     return hscale(hsub(N, hc(m->y_N0)), m->y_s);
 }
@@ -653,6 +689,177 @@ int or_threads(int n)
     (void)n;
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------ */
+/* element sensitivities for the discrete adjoint of the load path      */
+/* ------------------------------------------------------------------ */
+static int net_size(int n_in, int w) { return w > 0 ? w * n_in + w + w * w + w * n_in + w + w + n_in : 0; }
+
+/* Seeds weight k of theta = [psi params | yield params] in direction dir (1: the
+ * a part, 2: the b part) on m, using the hyper-dual copy ph of theta (set up by the
+ * caller, no entry seeded), and forms the normalising constants N(0), n, N_k(0),
+ * s = 1/N_k'(0) of or_prepare as hyper-duals carrying their derivative with respect
+ * to that weight (n: the weight derivative of 2 dN/dx1 + 4 dN/dx2 + dN/dx3 at 0,
+ * raw inputs, or of dN/dx3, isochoric inputs). */
+static void seed_weight(or_mat *m, hd *ph, int k, int dir)
+{
+    const int np = m->energy == OR_NEO_HOOKE ? 0 : net_size(3, m->psi_w);
+    if (dir == 1) ph[k].a = 1.0;
+    else ph[k].b = 1.0;
+    m->seeded = 1;
+    m->psi_ph = ph;
+    m->y_ph = ph + np;
+    m->c_N0 = hc(0.0);
+    m->c_n = hc(0.0);
+    if (np > 0) {
+        hd x0[3] = {hc(0.0), hc(0.0), hc(0.0)};
+        m->c_N0 = icnn_p(m->psi_ph, 3, m->psi_w, x0);
+        hd dN[3];
+        for (int i = 0; i < 3; ++i) {
+            hd x[3] = {hc(0.0), hc(0.0), hc(0.0)};
+            if (dir == 1) x[i].b = 1.0;                  /* the input derivative in the other part */
+            else x[i].a = 1.0;
+            hd v = icnn_p(m->psi_ph, 3, m->psi_w, x);
+            dN[i] = hc(dir == 1 ? v.b : v.a);
+            if (dir == 1) dN[i].a = v.ab;
+            else dN[i].b = v.ab;
+        }
+        if (m->energy == OR_ICNN_RAW) m->c_n = hadd(hadd(hscale(dN[0], 2.0), hscale(dN[1], 4.0)), dN[2]);
+        else m->c_n = dN[2];
+    }
+    m->c_yN0 = hc(0.0);
+    m->c_ys = hc(1.0);
+    if (m->y_w > 0) {
+        hd q0 = hc(0.0);
+        m->c_yN0 = icnn_p(m->y_ph, 1, m->y_w, &q0);
+        hd q1 = hc(0.0);
+        if (dir == 1) q1.b = 1.0;
+        else q1.a = 1.0;
+        hd v = icnn_p(m->y_ph, 1, m->y_w, &q1);
+        hd Np = hc(dir == 1 ? v.b : v.a);
+        if (dir == 1) Np.a = v.ab;
+        else Np.b = v.ab;
+        m->c_ys = hinv(Np);
+    }
+}
+static void unseed_weight(or_mat *m, hd *ph, int k)
+{
+    ph[k].a = 0.0;
+    ph[k].b = 0.0;
+    m->seeded = 0;
+}
+
+/* Partial derivatives of one element's converged-step outputs, at its dofs de and
+ * committed history kappa_n (the local update kappa_{n+1}(z, kappa_n; theta) inside,
+ * Sec. 3.2 Eq. (dd_7_no_nn)), with theta = [psi params | yield params]:
+ *   dR_dth[nd * nth]  dR^e / dtheta_k: the weights' direct part d2Psi/dz dtheta_k plus,
+ *                     on loading points, d2Psi/dz dkappa dkappa_{n+1}/dtheta_k
+ *   dk_dth[nq * nth]  dkappa_{n+1} / dtheta_k = -(dr/dtheta_k) / (dr/dkappa) on
+ *                     loading points (implicit function theorem on r = G(q) - kappa
+ *                     = 0), 0 elsewhere
+ *   dR_dkp[nd * nq]   dR^e / dkappa_{n,q}: on unloading points kappa_{n+1} = kappa_n,
+ *                     so d2Psi/dz dkappa; 0 on loading points (the root does not
+ *                     depend on kappa_n)
+ *   dk_dkp[nq]        dkappa_{n+1} / dkappa_n: 1 unloading, 0 loading
+ *   dk_dd[nq * nd]    dkappa_{n+1} / dd^e (loading points; 0 elsewhere)
+ * Row-major; any output may be NULL.  Returns -1 for a non-positive Jacobian. */
+int or_element_sens(const or_mat *m0, const double *Xe, const double *de, const double *kappa_n, double *dR_dth,
+                    double *dk_dth, double *dR_dkp, double *dk_dkp, double *dk_dd)
+{
+    or_mat m = *m0;
+    m.seeded = 0;
+    const int dim = m.dim, nen = nen_of(dim), nq = nq_of(dim), ndof = dim + 1, nd = nen * ndof;
+    const int nz = nz_of(dim);
+    const int np = m.energy == OR_NEO_HOOKE ? 0 : net_size(3, m.psi_w), ny = net_size(1, m.y_w), nth = np + ny;
+    hd *ph = (hd *)malloc(sizeof(hd) * (size_t)(nth > 0 ? nth : 1));
+    if (!ph) return -1;
+    for (int i = 0; i < np; ++i) ph[i] = hc(m.psi_p[i]);
+    for (int i = 0; i < ny; ++i) ph[np + i] = hc(m.y_p[i]);
+    if (dR_dth) memset(dR_dth, 0, sizeof(double) * (size_t)nd * nth);
+    if (dk_dth) memset(dk_dth, 0, sizeof(double) * (size_t)nq * nth);
+    if (dR_dkp) memset(dR_dkp, 0, sizeof(double) * (size_t)nd * nq);
+    if (dk_dd) memset(dk_dd, 0, sizeof(double) * (size_t)nq * nd);
+    for (int q = 0; q < nq; ++q) {
+        double N[8], dN[8][3], Jw;
+        if (shape_at(dim, Xe, q, N, dN, &Jw)) {
+            free(ph);
+            return -1;
+        }
+        double B[13][32];
+        memset(B, 0, sizeof(B));
+        for (int a = 0; a < nen; ++a) {
+            for (int i = 0; i < dim; ++i)
+                for (int J = 0; J < dim; ++J) B[i * dim + J][a * ndof + i] = dN[a][J];
+            B[dim * dim][a * ndof + dim] = N[a];
+            for (int J = 0; J < dim; ++J) B[dim * dim + 1 + J][a * ndof + dim] = dN[a][J];
+        }
+        double z[13];
+        for (int c = 0; c < nz; ++c) {
+            double s = 0.0;
+            for (int A = 0; A < nd; ++A) s += B[c][A] * de[A];
+            z[c] = s;
+        }
+        or_qp_info inf;
+        local_update(&m, z, kappa_n[q], &inf);
+        const double kap = inf.kappa;
+        hd zz[13];
+        /* d2Psi / dz_c dkappa at the converged kappa */
+        double mixed[13], dkdz[13];
+        for (int c = 0; c < nz; ++c) {
+            for (int f = 0; f < nz; ++f) zz[f] = hc(z[f]);
+            zz[c].a = 1.0;
+            hd k = hc(kap);
+            k.b = 1.0;
+            mixed[c] = Psi(&m, zz, k).ab;
+        }
+        double drk = 1.0;
+        if (inf.loading) {
+            drk = dr_dkappa(&m, z, kap);
+            for (int c = 0; c < nz; ++c) {
+                for (int f = 0; f < nz; ++f) zz[f] = hc(z[f]);
+                zz[c].a = 1.0;
+                dkdz[c] = -yield_residual(&m, zz, hc(kap)).a / drk;
+            }
+        }
+        if (dk_dkp) dk_dkp[q] = inf.loading ? 0.0 : 1.0;
+        for (int A = 0; A < nd; ++A) {
+            double sk = 0.0, sr = 0.0;
+            for (int c = 0; c < nz; ++c) {
+                if (inf.loading) sk += dkdz[c] * B[c][A];
+                else sr += B[c][A] * mixed[c];
+            }
+            if (dk_dd) dk_dd[q * nd + A] = sk;
+            if (dR_dkp) dR_dkp[A * nq + q] = sr * Jw;
+        }
+        if (!dR_dth && !dk_dth) continue;
+        for (int k = 0; k < nth; ++k) {
+            double dk = 0.0;
+            if (inf.loading) {
+                for (int f = 0; f < nz; ++f) zz[f] = hc(z[f]);
+                seed_weight(&m, ph, k, 1);
+                dk = -yield_residual(&m, zz, hc(kap)).a / drk;
+                unseed_weight(&m, ph, k);
+            }
+            if (dk_dth) dk_dth[q * nth + k] = dk;
+            if (!dR_dth) continue;
+            seed_weight(&m, ph, k, 2);
+            double v[13];
+            for (int c = 0; c < nz; ++c) {
+                for (int f = 0; f < nz; ++f) zz[f] = hc(z[f]);
+                zz[c].a = 1.0;
+                v[c] = Psi(&m, zz, hc(kap)).ab + mixed[c] * dk;
+            }
+            unseed_weight(&m, ph, k);
+            for (int A = 0; A < nd; ++A) {
+                double s = 0.0;
+                for (int c = 0; c < nz; ++c) s += B[c][A] * v[c];
+                dR_dth[A * nth + k] += s * Jw;
+            }
+        }
+    }
+    free(ph);
+    return 0;
 }
 
 /* ------------------------------------------------------------------ */

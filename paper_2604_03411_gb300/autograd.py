@@ -30,11 +30,15 @@ class GDLoadPath(torch.autograd.Function):
         B.gd_set_state(handle, np.zeros(n), np.zeros((meta["n_elems"], meta["nq"])), 0)
         reac, _ = B.gd_run_load_path(handle)
         ctx.handle = handle
+        ctx.generation = handle.generation
         ctx.device = theta.device
         return torch.as_tensor(np.array(reac), dtype=torch.float64, device=theta.device)
 
     @staticmethod
     def backward(ctx, grad_reaction: torch.Tensor):
+        if ctx.handle.generation != ctx.generation:
+            raise RuntimeError("the handle ran another path or changed its weights or state after this forward; "
+                               "its adjoint would belong to that path")
         g = grad_reaction.detach().to(torch.float64).cpu().numpy()
         d_theta = B.gd_backward(ctx.handle, g)
         return torch.as_tensor(d_theta, dtype=torch.float64, device=ctx.device), None

@@ -25,6 +25,7 @@ GD_FP64, GD_MIXED = 0, 1
 GD_ASM_RESIDUAL, GD_ASM_TANGENT = 0, 1
 GD_INNER_AUTO, GD_INNER_FP64, GD_INNER_REFINED = 0, 1, 2
 GD_MONOLITHIC, GD_STAGGERED = 0, 1
+GD_ICNN_AUTO, GD_ICNN_CUDA_CORES, GD_ICNN_BF16, GD_ICNN_BF16X3 = 0, 1, 2, 3
 GD_NOALLOC_MAX_DOFS = 131072
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -61,7 +62,7 @@ class GdOptions(ctypes.Structure):
                 ("local_max", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
                 ("max_step_cuts", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p), ("inner_solve", ctypes.c_int32),
                 ("coarse", ctypes.c_int32), ("scheme", ctypes.c_int32), ("stagger_max", ctypes.c_int32),
-                ("asm_grid_max", ctypes.c_int32), ("krylov_row_cache", ctypes.c_int32)]
+                ("asm_grid_max", ctypes.c_int32), ("krylov_row_cache", ctypes.c_int32), ("icnn_mma", ctypes.c_int32)]
 
 
 class GdNewtonReport(ctypes.Structure):
@@ -122,8 +123,8 @@ PROTOTYPES = {
     "gd_run_load_path": (ctypes.c_int, [_H, _dp, ctypes.POINTER(GdPathReport)]),
     "gd_backward": (ctypes.c_int, [_H, _dp, _dp]),
     "gd_get_fields": (ctypes.c_int, [_H, _dp, _dp, _dp]),
-    "gd_set_state": (ctypes.c_int, [_H, _dp, _dp, _dp, ctypes.c_int32]),
-    "gd_get_state": (ctypes.c_int, [_H, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_int32)]),
+    "gd_set_state": (ctypes.c_int, [_H, _dp, _dp, _dp, _dp, ctypes.c_int32]),
+    "gd_get_state": (ctypes.c_int, [_H, _dp, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_int32)]),
     "gd_last_error": (ctypes.c_char_p, [_H]),
     "gd_destroy": (None, [_H]),
 }
@@ -187,6 +188,9 @@ class Handle:
     def __init__(self, ptr, meta):
         self.ptr = ptr
         self.meta = meta
+        # bumped by every call that changes the committed path or the weights (the
+        # autograd view checks that the path it differentiates is still the handle's)
+        self.generation = 0
 
     def __del__(self):
         if getattr(self, "ptr", None):
@@ -331,6 +335,7 @@ def gd_batch_layout(h: Handle):
 
 def gd_set_params(h: Handle, theta_psi=None, theta_yield=None):
     """theta_* may be numpy arrays (host) or CUDA tensors (device), or None to keep."""
+    h.generation += 1
     keep = []
 
     def ptr(a):
@@ -395,6 +400,7 @@ def gd_autotune(h: Handle) -> GdTuneReport:
 
 
 def gd_newton_step(h: Handle) -> GdNewtonReport:
+    h.generation += 1
     rep = GdNewtonReport()
     _check(lib().gd_newton_step(h.ptr, ctypes.byref(rep)), h.ptr)
     return rep
@@ -402,6 +408,7 @@ def gd_newton_step(h: Handle) -> GdNewtonReport:
 
 def gd_run_load_path(h: Handle):
     """(reaction [n_steps], report); a batch returns reaction [n_steps, n_spec]."""
+    h.generation += 1
     ns = h.meta.get("n_spec", 1)
     reac = np.zeros(max(h.meta["n_steps"], 1) * ns)
     rep = GdPathReport()
@@ -432,21 +439,24 @@ def gd_get_fields(h: Handle, damage: bool = False):
     return d, k.reshape(shape)
 
 
-def gd_set_state(h: Handle, dofs=None, kappa=None, next_step: int = 0, dofs_prev=None):
+def gd_set_state(h: Handle, dofs=None, kappa=None, next_step: int = 0, dofs_prev=None, dofs_prev2=None):
+    h.generation += 1
     d = np.ascontiguousarray(dofs, np.float64).ravel() if dofs is not None else None
     dp = np.ascontiguousarray(dofs_prev, np.float64).ravel() if dofs_prev is not None else None
+    dpp = np.ascontiguousarray(dofs_prev2, np.float64).ravel() if dofs_prev2 is not None else None
     k = np.ascontiguousarray(kappa, np.float64).ravel() if kappa is not None else None
-    _check(lib().gd_set_state(h.ptr, _hp(d), _hp(dp), _hp(k), int(next_step)), h.ptr)
+    _check(lib().gd_set_state(h.ptr, _hp(d), _hp(dp), _hp(dpp), _hp(k), int(next_step)), h.ptr)
 
 
 def gd_get_state(h: Handle):
-    """(dofs, dofs_prev, kappa [n_elems, nq], next_step) of the committed state."""
+    """(dofs, dofs_prev, kappa [n_elems, nq], next_step, dofs_prev2) of the committed state."""
     d = np.zeros(h.meta["n_nodes"] * h.meta["ndof"])
     dp = np.zeros_like(d)
+    dpp = np.zeros_like(d)
     k = np.zeros(h.meta["n_elems"] * h.meta["nq"])
     ns = ctypes.c_int32()
-    _check(lib().gd_get_state(h.ptr, _hp(d), _hp(dp), _hp(k), ctypes.byref(ns)), h.ptr)
-    return d, dp, k.reshape(h.meta["n_elems"], h.meta["nq"]), ns.value
+    _check(lib().gd_get_state(h.ptr, _hp(d), _hp(dp), _hp(dpp), _hp(k), ctypes.byref(ns)), h.ptr)
+    return d, dp, k.reshape(h.meta["n_elems"], h.meta["nq"]), ns.value, dpp
 
 
 def gd_last_error(h: Optional[Handle] = None) -> str:

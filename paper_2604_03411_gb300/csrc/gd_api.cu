@@ -37,6 +37,13 @@ gd_status fail(gd::Handle *H, gd_status st, const std::string &msg)
                         std::string(#call) + ": " + cudaGetErrorString(e_));                               \
     } while (0)
 
+// counters[3] is set by the tensor-core element kernel when one of its bounded waits
+// gave up (the kernel then frees its tensor memory and returns)
+#define GD_TC_CHECK(H, hc)                                                                                 \
+    do {                                                                                                   \
+        if ((hc)[3]) return fail((H), GD_ERR_TIMEOUT, "tensor-core element kernel: a bounded wait gave up"); \
+    } while (0)
+
 template <class T>
 cudaError_t dalloc(T **p, size_t count)
 {
@@ -118,6 +125,7 @@ void free_handle(gd::Handle &H)
     dfree(H.bk_cnt);
     dfree(H.psi_tab);
     dfree(H.yld_tab);
+    dfree(H.tc_blob);
     {
         gd::CoarseSpace &c = H.coarse;
         void *cp[] = {c.agg, c.coff, c.node_co, c.P, c.Ac, c.X32, c.X64, c.rc, c.cc, c.status};
@@ -199,9 +207,18 @@ gd_status assemble_pass(gd::Handle &H, const double *dofs, const double *kappa_n
     GD_CUDA(&H, cudaEventRecord(H.ev0, H.stream));
     gd::AsmArgs a = asm_args(H, dofs, kappa_n, R, vals, kappa_out, loading, tangent);
     a.kappa_guess = guess;
-    if (H.opt.precision == GD_FP64 || force_fp64)
+    if (H.opt.precision == GD_FP64 || force_fp64) {
         GD_CUDA(&H, gd::launch_assemble_fp64(H.dim, a, H.num_sms, H.stream, H.asm_tune));
-    else GD_CUDA(&H, gd::launch_assemble_fp32(H.dim, a, H.num_sms, H.stream, H.asm_tune));
+    } else if (H.icnn_mode == GD_ICNN_BF16 || H.icnn_mode == GD_ICNN_BF16X3) {
+        gd::TcLaunch c;
+        c.L = H.tc;
+        c.blob = H.tc_blob;
+        c.status = H.counters + 3;
+        c.grid_max = H.asm_tune.grid_max;
+        GD_CUDA(&H, gd::launch_assemble_tc(H.dim, a, c, H.stream));
+    } else {
+        GD_CUDA(&H, gd::launch_assemble_fp32(H.dim, a, H.num_sms, H.stream, H.asm_tune));
+    }
     ++H.launches;
     GD_CUDA(&H, cudaEventRecord(H.ev1, H.stream));
     ++H.assemblies;
@@ -267,7 +284,7 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
     kc.lmax = H.krylov_lmax;
     kc.row_cache = H.opt.krylov_row_cache;
     kc.coarse = H.coarse.nc > 0 ? &H.coarse : nullptr;
-    const bool refresh =
+    bool refresh =
         kind == kCallerMatrix || H.coarse_age < 0 || H.coarse_kind != kind || H.coarse_age >= kCoarseReuse;
     kc.coarse_refresh = refresh;
     GD_CUDA(&H, cudaEventRecord(H.kv0, H.stream));
@@ -280,10 +297,21 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
     }
     GD_CUDA(&H, gd::krylov_solve(kc, vals, fp32_vals, b, x, rtol, H.opt.krylov_max, inner_fp32));
     H.launches += kc.coarse ? 4 : 2;
-    GD_CUDA(&H, cudaEventRecord(H.kv1, H.stream));
     double kout[3];
     GD_CUDA(&H, cudaMemcpyAsync(kout, H.scal + 24, 3 * sizeof(double), cudaMemcpyDeviceToHost, H.stream));
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));
+    if (kc.coarse && !refresh && kout[2] != 0.0) {
+        // a reused coarse inverse (from another state of the path) may no longer fit:
+        // recompute it and solve again
+        kc.coarse_refresh = true;
+        refresh = true;
+        GD_CUDA(&H, gd::krylov_solve(kc, vals, fp32_vals, b, x, rtol, H.opt.krylov_max, inner_fp32));
+        H.launches += 4;
+        GD_CUDA(&H, cudaMemcpyAsync(kout, H.scal + 24, 3 * sizeof(double), cudaMemcpyDeviceToHost, H.stream));
+        GD_CUDA(&H, cudaStreamSynchronize(H.stream));
+    }
+    GD_CUDA(&H, cudaEventRecord(H.kv1, H.stream));
+    GD_CUDA(&H, cudaEventSynchronize(H.kv1));
     float kms = 0.0f;
     cudaEventElapsedTime(&kms, H.kv0, H.kv1);
     H.krylov_ms += kms;
@@ -577,8 +605,9 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
     NormPair nr;
     if ((st = norms(H, H.R, nr))) return st;
     H.assembly_ms += elapsed_ms(H);
-    int hc[3];
-    GD_CUDA(&H, cudaMemcpy(hc, H.counters, 3 * sizeof(int), cudaMemcpyDeviceToHost));
+    int hc[4];
+    GD_CUDA(&H, cudaMemcpy(hc, H.counters, 4 * sizeof(int), cudaMemcpyDeviceToHost));
+    GD_TC_CHECK(&H, hc);
     rep.yield_evals += hc[2];
     double nrm = nr.free_;
     const double r0 = std::max(nr.free_, nr.fixed_);
@@ -636,7 +665,8 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
                 return st;
             if ((st = norms(H, H.R_trial, nr))) return st;
             H.assembly_ms += elapsed_ms(H);
-            GD_CUDA(&H, cudaMemcpy(hc, H.counters, 3 * sizeof(int), cudaMemcpyDeviceToHost));
+            GD_CUDA(&H, cudaMemcpy(hc, H.counters, 4 * sizeof(int), cudaMemcpyDeviceToHost));
+    GD_TC_CHECK(&H, hc);
             rep.yield_evals += hc[2];
             nt = nr.free_;
             decreased = std::isfinite(nt) && nt <= (1.0 - 1e-4 * alpha) * nrm;
@@ -705,8 +735,9 @@ gd_status newton_batch(gd::Handle &H, gd_newton_report &rep)
     std::vector<double> nf, nx, nt, ntx;
     if ((st = norms_batch(H, H.R, nf, nx))) return st;
     H.assembly_ms += elapsed_ms(H);
-    int hc[3];
-    GD_CUDA(&H, cudaMemcpy(hc, H.counters, 3 * sizeof(int), cudaMemcpyDeviceToHost));
+    int hc[4];
+    GD_CUDA(&H, cudaMemcpy(hc, H.counters, 4 * sizeof(int), cudaMemcpyDeviceToHost));
+    GD_TC_CHECK(&H, hc);
     rep.yield_evals += hc[2];
     std::vector<double> r0(S), ntol(S), coef(S), alpha(S);
     std::vector<char> done(S, 0), accepted(S, 0);
@@ -796,7 +827,8 @@ gd_status newton_batch(gd::Handle &H, gd_newton_report &rep)
                 return st;
             if ((st = norms_batch(H, H.R_trial, nt, ntx))) return st;
             H.assembly_ms += elapsed_ms(H);
-            GD_CUDA(&H, cudaMemcpy(hc, H.counters, 3 * sizeof(int), cudaMemcpyDeviceToHost));
+            GD_CUDA(&H, cudaMemcpy(hc, H.counters, 4 * sizeof(int), cudaMemcpyDeviceToHost));
+    GD_TC_CHECK(&H, hc);
             rep.yield_evals += hc[2];
             bool all_acc = true;
             for (int s = 0; s < S; ++s) {
@@ -1056,8 +1088,9 @@ gd_status newton_staggered(gd::Handle &H, gd_newton_report &rep)
         NormPair nr;
         if ((st = norms(H, H.R, nr))) return st;
         H.assembly_ms += elapsed_ms(H);
-        int hc[3];
-        GD_CUDA(&H, cudaMemcpy(hc, H.counters, 3 * sizeof(int), cudaMemcpyDeviceToHost));
+        int hc[4];
+        GD_CUDA(&H, cudaMemcpy(hc, H.counters, 4 * sizeof(int), cudaMemcpyDeviceToHost));
+    GD_TC_CHECK(&H, hc);
         rep.yield_evals += hc[2];
         rep.local_failures = hc[0];
         rep.loading_points = hc[1];
@@ -1467,6 +1500,9 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
     if (o.asm_grid_max < 0) return fail(nullptr, GD_ERR_ARG, "asm_grid_max must be >= 0");
     if (o.krylov_row_cache < 0 || o.krylov_row_cache > 2)
         return fail(nullptr, GD_ERR_ARG, "krylov_row_cache must be 0, 1 or 2");
+    if (o.icnn_mma < GD_ICNN_AUTO || o.icnn_mma > GD_ICNN_BF16X3) return fail(nullptr, GD_ERR_ARG, "icnn_mma");
+    if (n_spec > 1 && o.precision == GD_MIXED && (o.icnn_mma == GD_ICNN_BF16 || o.icnn_mma == GD_ICNN_BF16X3))
+        return fail(nullptr, GD_ERR_ARG, "the tensor-core networks need a single specimen (one weight set per launch)");
 
     const int dim = mesh->dim, nen = dim == 2 ? 4 : 8, ndof = dim + 1;
     const int64_t NN = mesh->n_nodes, NE = mesh->n_elems;
@@ -1570,7 +1606,15 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
         GD_CREATE_CUDA(dalloc(&H.netc, 1));
         GD_CREATE_CUDA(gd::launch_prep_nets(H.psi, H.yld, H.mat.energy, H.netc, H.stream));
         H.wmax = std::max(H.psi.width, H.yld.width);
+        // tensor-core networks: the weight blob the element kernel stages per CTA
+        H.icnn_mode = o.icnn_mma == GD_ICNN_AUTO ? GD_ICNN_BF16X3 : o.icnn_mma;
+        if (o.precision == GD_MIXED && H.icnn_mode != GD_ICNN_CUDA_CORES) {
+            H.tc = gd::tc_layout(H.psi.width, H.yld.width, H.icnn_mode == GD_ICNN_BF16X3);
+            GD_CREATE_CUDA(dalloc(&H.tc_blob, (size_t)H.tc.bytes));
+            GD_CREATE_CUDA(gd::tc_build_blob(H.psi, H.yld, H.tc, H.tc_blob, H.stream));
+        }
     } else {
+        H.icnn_mode = GD_ICNN_CUDA_CORES;
         // per-specimen networks in device tables indexed by the element's specimen
         H.h_psi_tab.resize(n_spec);
         H.h_yld_tab.resize(n_spec);
@@ -1754,6 +1798,7 @@ gd_status gd_set_params(gd_handle *h, const double *theta_psi, const double *the
         GD_CUDA(&H, gd::launch_net_to_float(H.yld, H.stream));
     }
     GD_CUDA(&H, gd::launch_prep_nets(H.psi, H.yld, H.mat.energy, H.netc, H.stream));
+    if (H.tc_blob) GD_CUDA(&H, gd::tc_build_blob(H.psi, H.yld, H.tc, H.tc_blob, H.stream));
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));
     H.coarse_age = -1;                       // new networks, new tangents
     return GD_OK;
@@ -1820,9 +1865,10 @@ gd_status gd_assemble(gd_handle *h, const double *dofs, const double *kappa_n, d
     const int tangent = (mode == GD_ASM_TANGENT && csr_vals) ? 1 : 0;
     gd_status st = assemble_pass(H, dofs, kappa_n ? kappa_n : H.kappa, R, csr_vals, kappa_trial, loading, tangent);
     if (st) return st;
-    int hc[2];
+    int hc[4];
     GD_CUDA(&H, cudaMemcpyAsync(hc, H.counters, sizeof(hc), cudaMemcpyDeviceToHost, H.stream));
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));
+    GD_TC_CHECK(&H, hc);
     H.assembly_ms += elapsed_ms(H);
     if (hc[0] > 0) return fail(&H, GD_ERR_LOCAL_SOLVE, std::to_string(hc[0]) + " local solves hit local_max");
     return GD_OK;
@@ -2044,37 +2090,46 @@ gd_status gd_get_fields(gd_handle *h, double *dofs, double *kappa, double *damag
     return GD_OK;
 }
 
-gd_status gd_set_state(gd_handle *h, const double *dofs, const double *dofs_prev, const double *kappa,
-                       int32_t next_step)
+gd_status gd_set_state(gd_handle *h, const double *dofs, const double *dofs_prev, const double *dofs_prev2,
+                       const double *kappa, int32_t next_step)
 {
     if (!h) return fail(nullptr, GD_ERR_ARG, "null handle");
     gd::Handle &H = h->h;
     if (next_step < 0 || next_step > H.n_steps_max) return fail(&H, GD_ERR_ARG, "next_step out of range");
     if (dofs_prev && next_step < 1) return fail(&H, GD_ERR_ARG, "dofs_prev needs next_step >= 1");
+    if (dofs_prev2 && (!dofs_prev || next_step < 2))
+        return fail(&H, GD_ERR_ARG, "dofs_prev2 needs dofs_prev and next_step >= 2");
     if (dofs) GD_CUDA(&H, cudaMemcpyAsync(H.dofs, dofs, sizeof(double) * H.n_dofs, cudaMemcpyHostToDevice, H.stream));
     if (dofs_prev)
         GD_CUDA(&H, cudaMemcpyAsync(H.dofs_prev, dofs_prev, sizeof(double) * H.n_dofs, cudaMemcpyHostToDevice, H.stream));
+    if (dofs_prev2)
+        GD_CUDA(&H, cudaMemcpyAsync(H.dofs_pp, dofs_prev2, sizeof(double) * H.n_dofs, cudaMemcpyHostToDevice, H.stream));
     if (kappa)
         GD_CUDA(&H, cudaMemcpyAsync(H.kappa, kappa, sizeof(double) * H.n_elems * H.nq, cudaMemcpyHostToDevice, H.stream));
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));
     H.next_step = next_step;
     H.rec_on = false;
-    H.noise_age = 0;
-    H.coarse_age = -1;
-    H.have_pp = false;
+    // the coarse inverse and the mixed-precision noise estimate are kept: the first is
+    // recomputed by its own convergence-rate test (and after a failed solve), the second
+    // at its usual interval
     H.have_prev = dofs_prev != nullptr;
+    H.have_pp = dofs_prev2 != nullptr;
     H.load_prev = (double)next_step;
     H.load_prevprev = dofs_prev ? (double)(next_step - 1) : H.load_prev;
+    H.load_ppp = dofs_prev2 ? (double)(next_step - 2) : H.load_prevprev;
     return GD_OK;
 }
 
-gd_status gd_get_state(gd_handle *h, double *dofs, double *dofs_prev, double *kappa, int32_t *next_step)
+gd_status gd_get_state(gd_handle *h, double *dofs, double *dofs_prev, double *dofs_prev2, double *kappa,
+                       int32_t *next_step)
 {
     if (!h) return fail(nullptr, GD_ERR_ARG, "null handle");
     gd::Handle &H = h->h;
     if (dofs) GD_CUDA(&H, cudaMemcpyAsync(dofs, H.dofs, sizeof(double) * H.n_dofs, cudaMemcpyDeviceToHost, H.stream));
     if (dofs_prev)
         GD_CUDA(&H, cudaMemcpyAsync(dofs_prev, H.dofs_prev, sizeof(double) * H.n_dofs, cudaMemcpyDeviceToHost, H.stream));
+    if (dofs_prev2)
+        GD_CUDA(&H, cudaMemcpyAsync(dofs_prev2, H.dofs_pp, sizeof(double) * H.n_dofs, cudaMemcpyDeviceToHost, H.stream));
     if (kappa)
         GD_CUDA(&H, cudaMemcpyAsync(kappa, H.kappa, sizeof(double) * H.n_elems * H.nq, cudaMemcpyDeviceToHost, H.stream));
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));

@@ -97,6 +97,36 @@ struct Checkpoint {
     bool have_prev = false;
 };
 
+// Tensor-core element kernel (gd_asm_tc.cu): byte layout of the per-handle weight
+// blob that every CTA copies into shared memory: the layer-2 tiles of both networks
+// in the canonical K-major BF16 layout (energy W2 for the forward columns, W2^T for
+// the reverse column, yield V2; with split operands each tile is followed by its
+// residual tile), then FP32 vectors (energy W1 b1 A2 b2 w3 a3, yield V1 c1 B2 c2 v3 b3).
+struct TcLayout {
+    int we = 0, wy = 0;          // widths (0: no network)
+    int wpe = 0, wpy = 0;        // widths padded to 16
+    int split = 0;               // 1: high and residual BF16 parts (three products)
+    int off_w2f = 0, off_w2r = 0, off_v2f = 0, off_e32 = 0, off_y32 = 0;
+    int bytes = 0;               // multiple of 16
+};
+struct TcArgs {
+    TcLayout L;
+    const uint8_t *blob;
+    int *status;                 // set to 1 when a bounded wait gave up
+    float tol_r, tol_br;         // local-solve stopping tests (residual, bracket) relative to max(1, kappa)
+    int ncols;                   // tensor-memory columns per CTA
+    int tiles_off, tile_bytes, warp_off, warp_floats, bar_off;   // shared-memory layout
+};
+struct TcLaunch {
+    TcLayout L;
+    const uint8_t *blob = nullptr;
+    int *status = nullptr;
+    int grid_max = 0;
+};
+TcLayout tc_layout(int we, int wy, bool split);
+cudaError_t tc_build_blob(const DevNet &psi, const DevNet &yld, const TcLayout &L, uint8_t *blob, cudaStream_t s);
+cudaError_t launch_assemble_tc(int dim, const AsmArgs &a, const TcLaunch &c, cudaStream_t s);
+
 // launch shape of the element kernels (chosen by gd_autotune): warps per CTA
 // (2, 4 or 8) and a cap on resident CTAs per SM for the persistent grid (0: none)
 struct AsmTune {
@@ -227,6 +257,10 @@ struct Handle {
     int krylov_up = 0;                                   // 0: the precision's default
     int krylov_lmax = 0;                                 // longest CSR row
     CoarseSpace coarse;                                  // two-level preconditioner (nc = 0: off)
+    // tensor-core networks of the mixed element kernel (icnn_mma): mode and weight blob
+    int icnn_mode = 0;                                   // GD_ICNN_CUDA_CORES, GD_ICNN_BF16 or GD_ICNN_BF16X3
+    TcLayout tc;
+    uint8_t *tc_blob = nullptr;
     // staggered scheme: the frozen history of the current equilibrium solve (null: none)
     // and its storage
     const double *kappa_fix = nullptr;

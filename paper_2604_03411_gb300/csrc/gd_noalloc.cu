@@ -1,14 +1,17 @@
 // gd_noalloc.cu -- gd_solve_noalloc: the Newton-system Krylov solve for callers
 // that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is being
-// captured, an application that hands the whole device to its own memory pool,
-// or an embedding runtime that forbids allocation after start-up.  For them this
+// Some callers cannot call cudaMalloc: an application that hands the whole device
+// to its own memory pool (every byte belongs to the pool, so an allocation from
+// outside it fails or breaks the pool's accounting), or an embedding runtime that
+// forbids allocation once it has started (allocation can fail and synchronises the
+// device, which such runtimes keep out of their steady state).  For them this
 // entry point takes the CSR system and the vectors from the caller and keeps all
 // of its work space (the nine BiCGStab vectors, the node-block inverses, the
 // reduction partials and the result words) in one file-scope device array of
 // fixed size.  Every GPU that loads the library holds that array until the
-// process exits.
+// process exits.  The call reads its iteration count and residual back to host
+// memory and synchronises the caller's stream before it returns.
 //
 // The array is a device symbol: in host code its name is only a stand-in, so
 // its device address is looked up once per device with cudaGetSymbolAddress
@@ -86,8 +89,10 @@ extern "C" gd_status gd_solve_noalloc(int32_t ndof, int64_t n_nodes, const int32
     kc.blocks = gd::krylov_blocks(ndof, false, num_sms);
     if (kc.blocks > kMaxBlocks) kc.blocks = kMaxBlocks;
     if (kc.blocks < 1) return gd::set_error(GD_ERR_CUDA, "gd_solve_noalloc: no cooperative grid fits");
-    // every work vector, the partials and the result words are written by the
-    // solve before they are read, so nothing left by an earlier call needs clearing
+    // nothing left in the array by an earlier call reaches this one: krylov_solve
+    // zeroes the grid-wide accumulator words (atomic sums) with a memset before its
+    // launch, and every work vector, block partial and result word is written by the
+    // solve before it is read
     e = gd::krylov_solve(kc, vals, false, b, x, rtol, max_it);
     if (e != cudaSuccess) return gd::set_error(GD_ERR_CUDA, std::string("krylov launch: ") + cudaGetErrorString(e));
     double out[3];

@@ -52,3 +52,33 @@ def compare_assembly(Rg, Kg, kg, lg, Ro, Ko, ko, qi, tol=1e-10):
     Ko.sort_indices()
     assert np.array_equal(Kg.indptr, Ko.indptr) and np.array_equal(Kg.indices, Ko.indices), "CSR pattern differs"
     return eR, eK, ek, flags_ok
+
+
+def node_size(mesh):
+    """Shortest edge of the elements around every node (graded meshes vary 8x)."""
+    x = mesh.coords
+    c = mesh.conn
+    nen = c.shape[1]
+    edges = [(0, 1), (1, 2), (2, 3), (3, 0)]
+    if nen == 8:
+        edges = edges + [(a + 4, b + 4) for a, b in edges] + [(a, a + 4) for a in range(4)]
+    le = np.min([np.linalg.norm(x[c[:, a]] - x[c[:, b]], axis=1) for a, b in edges], axis=0)
+    h = np.full(mesh.n_nodes, np.inf)
+    for a in range(nen):
+        np.minimum.at(h, c[:, a], le)
+    return h
+
+
+def smooth_state(mesh, rng, u_amp=0.05, noise=0.1, phi_amp=0.3, kappa_amp=0.3):
+    """Affine displacement plus nodal noise scaled by the local element size (so that
+    fine and graded meshes stay far from inversion), phi in [0, phi_amp], kappa_n in
+    [0, kappa_amp]."""
+    x = mesh.coords
+    h = node_size(mesh)
+    d = np.zeros((mesh.n_nodes, mesh.ndof))
+    for c in range(mesh.dim):
+        A = rng.normal(0.0, u_amp, size=mesh.dim)
+        d[:, c] = x @ A + noise * h * rng.uniform(-1.0, 1.0, mesh.n_nodes)
+    d[:, mesh.dim] = phi_amp * rng.random(mesh.n_nodes)
+    kappa = kappa_amp * rng.random((mesh.n_elems, mesh.nq))
+    return d, kappa

@@ -151,3 +151,19 @@ def test_autograd_function_matches_backward(env):
     # a second call on the same handle restarts the path from the undeformed state
     reac_again = reaction_curve(theta.detach(), h)
     assert torch.allclose(reac_again, reac.detach(), rtol=1e-10, atol=0)
+
+
+def test_autograd_refuses_a_stale_path(env):
+    """The backward pass differentiates the path the handle holds; when the handle ran
+    another path (or changed its state or weights) after the forward, backward raises
+    instead of returning that other path's gradient."""
+    torch, B, oracle = env
+    from paper_2604_03411_gb300.autograd import reaction_curve
+    prob = small_problem(n_long=8, n_wide=4, steps=3)
+    theta0 = np.concatenate([prob.psi.params, prob.yld.params])
+    h = B.gd_create(prob, opts(B))
+    theta = torch.tensor(theta0, dtype=torch.float64, device="cuda", requires_grad=True)
+    reac = reaction_curve(theta, h)
+    reaction_curve(torch.tensor(theta0 * 1.02, dtype=torch.float64, device="cuda"), h)   # another path
+    with pytest.raises(RuntimeError):
+        reac.sum().backward()

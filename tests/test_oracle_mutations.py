@@ -36,12 +36,17 @@ MUTATIONS = [
     ("yield normalisation", "m->y_s = 1.0 / N.a;", "m->y_s = 1.0;"),
     ("volumetric term", "return hadd(hscale(iso, m->mu_e), hscale(hsq(t), m->lambda_e));",
      "return hadd(hscale(iso, m->mu_e), hscale(t, m->lambda_e));"),
+    ("adjoint: history coupling of the weight sensitivity", "v[c] = Psi(&m, zz, hc(kap)).ab + mixed[c] * dk;",
+     "v[c] = Psi(&m, zz, hc(kap)).ab;"),
+    ("adjoint: unloading history sensitivity", "if (dk_dkp) dk_dkp[q] = inf.loading ? 0.0 : 1.0;",
+     "if (dk_dkp) dk_dkp[q] = 0.0;"),
+    ("adjoint: weight derivative of the yield normalisation", "m->c_ys = hinv(Np);", "m->c_ys = hc(1.0 / Np.v);"),
 ]
 
 # the pins that run against each mutant (the fast ones)
 PINS = ("stress_free or dd1 or closed_form_chain or objectivity or neo_hooke or small_strain or "
         "residual_is_energy or tangent_is or homogeneous_patch or mullins or kkt or single_hex8 or "
-        "yield_function or degradation or local_equals or patch_test or nonlocal_field")
+        "yield_function or degradation or local_equals or patch_test or nonlocal_field or adjoint")
 
 
 @pytest.mark.parametrize("name,orig,mut", MUTATIONS, ids=[m[0] for m in MUTATIONS])

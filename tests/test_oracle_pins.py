@@ -540,3 +540,42 @@ def test_nonlocal_field_matches_analytic_solution(stretch):
     phi = dofs.reshape(-1, 3)[:, 2]
     exact = k0 + A * np.cos(np.pi * x) / (1.0 + c_d * np.pi ** 2 / (beta * stretch ** 2))
     assert np.abs(phi - exact).max() < 3e-4
+
+
+def test_adjoint_matches_central_differences():
+    """The oracle's discrete adjoint of the load path (every state stored, transposed
+    LU solves, element sensitivities by hyper-dual numbers) against central
+    differences of the whole path (Sec. 3.2 steps re-solved at perturbed weights),
+    along a load-unload-reload path with loading and unloading points, for weights of
+    both networks and the normalising constants they feed."""
+    mesh = I.uniaxial_bc_2d(I.structured_q4(3, 2))
+    psi, yld = I.icnn_pair(11, 8, 8)
+    mat = I.Material(beta_d=10.0, c_d=10.0 * 0.1 ** 2)
+    load = np.array([0.25, 0.5, 0.35, 0.45, 0.6])
+    m = oracle.Model(2, mat, psi.params, 8, yld.params, 8)
+    w = np.array([1.0, -0.5, 2.0, 0.7, 1.5])
+    g, reac = oracle.adjoint_gradient(m, mesh, load, w)
+    st = oracle.run_load_path(m, mesh, load, keep_states=True)["states"]
+    loading = np.array([qi[..., 5].sum() for _, _, qi in st])
+    # unloading, then reloading below the previous maximum (the history is carried
+    # through unloading points), then damage again beyond it
+    assert loading[2] == 0 and loading[3] == 0 and loading[4] > 0, loading
+    theta0 = np.concatenate([psi.params, yld.params])
+    npsi = psi.params.size
+    assert g.size == theta0.size
+
+    def loss(th):
+        mm = oracle.Model(2, mat, th[:npsi], 8, th[npsi:], 8)
+        return float(w @ oracle.run_load_path(mm, mesh, load, rtol=1e-13, atol=1e-15)["reaction"])
+
+    # first-layer, second-layer, skip and output weights and biases of both networks
+    idx = [0, 5, 30, 100, 130, 137, npsi + 2, npsi + 9, npsi + 40, npsi + 90, npsi + 100, theta0.size - 1]
+    scale = np.abs(g).max()
+    for i in idx:
+        h = 1e-5 * max(abs(theta0[i]), 1e-2)
+        tp = theta0.copy()
+        tp[i] += h
+        tm = theta0.copy()
+        tm[i] -= h
+        fd = (loss(tp) - loss(tm)) / (2 * h)
+        assert abs(g[i] - fd) <= 2e-8 * scale, (i, g[i], fd)
