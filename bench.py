@@ -1,20 +1,23 @@
 #!/usr/bin/env python3
 """Benchmark of the gradient-enhanced damage hot path on one GB300 per rank.
 
-Metric: qp constitutive+assembly updates/s and Newton-step ms.  One bench step
-is one quasi-static load step of the monolithic scheme: Newton iterations, each
-an element-kernel pass (kinematics, ICNN energy with derivatives, yield network
-and local damage update, degraded stress, residual and consistent tangent,
-CSR scatter), the residual norms, a Jacobi-preconditioned BiCGStab solve and a
-backtracking line search.  value = (#qp x Newton iterates in the timed steps) /
-(timed device time), an iterate being the first pass of a (sub)step or the
-accepted pass of a Newton direction: whole-step throughput, inputs resident in
+Metric: qp constitutive+assembly updates/s and Newton-step ms, mixed vs FP64.  One
+bench step is one quasi-static load step of the monolithic scheme: Newton
+iterations, each an element-kernel pass (kinematics, ICNN energy with derivatives,
+yield network and local damage update, degraded stress, residual and consistent
+tangent, CSR scatter), the residual norms, the two-level preconditioned BiCGStab
+solve and a backtracking line search.  value = (#qp x Newton iterates in the timed
+steps) / (timed device time), an iterate being the first pass of a (sub)step or
+the accepted pass of a Newton direction: whole-step throughput, inputs resident in
 HBM.  Rejected line-search trials are timed but not counted.
 
 Workloads (synthetic, seeded; see paper_2604_03411_gb300/inputs.py):
+  cube      3D cube, 64^3 HEX8 (2,097,152 qp), biaxial to lambda = 1.8 in 30 steps,
+            both ICNNs width 64; mixed precision with the tensor-core networks
+            (default), the same steps in FP64 reported beside it
   notched   2D notched plate 2:1, graded Q4 mesh of 39,936 elements (159,744 qp),
-            both ICNNs width 32, 50 steps to 60% nominal strain, FP64 (default)
-  cube      3D cube, 64^3 HEX8 (2,097,152 qp), biaxial, both ICNNs width 64
+            both ICNNs width 32, 50 steps to 60% nominal strain, FP64 (mixed beside)
+  notched3d the paper's thin 3D notched plate, one HEX8 layer of 2,352 elements
   square    2D 8x8 Q4 square, load-unload-reload
   batch     96 independent Q4 specimens (16..96 x 16..48 elements, widths 16/24/32,
             20..60 steps each) in one batched handle, mixed precision; under
@@ -45,8 +48,13 @@ if ROOT not in sys.path:
 METRIC = "qp constitutive+assembly updates/s & Newton-step ms, mixed vs FP64, 1 GB300"
 UNIT = "qp-updates/s"
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
-FP64_PEAK_TFLOPS_NOMINAL = 1.25     # GB300 dense FP64 (nominal, the recipe's table)
-FP32_PEAK_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: SMs x FP32 lanes x FMA x max clock
+D_STOP = 0.995                      # damage at which a load path ends (Sec. 5.2)
+# FMA throughput measured on this part (a kernel of independent FMA chains, 152 x
+# {2, 4, 8} CTAs of 256 threads, timed with CUDA events): FP64 1.19 TFLOP/s, FP32
+# 72.8 TFLOP/s.  The copy bandwidth and the BF16 tensor rate come from
+# MEASURED_PEAKS.json.
+FP64_PEAK_TFLOPS = 1.19
+FP32_PEAK_TFLOPS = 72.8
 
 
 def parse():
@@ -55,12 +63,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gd", choices=["gd", "reference"])
-    ap.add_argument("--workload", default="notched", choices=["notched", "notched3d", "cube", "square", "batch"])
+    ap.add_argument("--workload", default="cube", choices=["notched", "notched3d", "cube", "square", "batch"])
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
-                    help="default: fp64 (mixed for the batch workload)")
+                    help="default: mixed for the cube and the batch, fp64 otherwise")
+    ap.add_argument("--icnn", default="auto", choices=["auto", "cuda", "bf16", "bf16x3"],
+                    help="network arithmetic of the mixed element kernel (gd_options.icnn_mma)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true",
-                    help="FP64 runs only: skip the mixed-precision comparison on the same steps")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the other precision's run on the same steps")
     ap.add_argument("--inner", default="auto", choices=["auto", "fp64", "refined"],
                     help="Newton inner-solve policy (gd_options.inner_solve)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
@@ -92,7 +102,7 @@ def make_workload(name, rank=0, world=1):
                 "dofs": p.mesh.n_nodes * 4, "icnn_width": [32, 32], "load_steps": int(p.load.size),
                 "length_scale": 0.04}
     elif name == "cube":
-        p = I.config3(precision="fp64")
+        p = I.config3()
         desc = {"workload": "cube_hex8_64", "elements": p.mesh.n_elems, "qp": p.mesh.n_elems * 8,
                 "dofs": p.mesh.n_nodes * 4, "icnn_width": [64, 64], "load_steps": int(p.load.size)}
     else:
@@ -152,13 +162,15 @@ def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return d.get("hbm_gbs"), "measured"
-    return 6800.0, "fallback"
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "bf16_tflops": d.get("bf16_tflops", 1900.0),
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", 1700.0), "kind": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "kind": "fallback"}
 
 
-def cpu_baseline(prob, seconds, seed=7):
-    """The oracle as it stands (single thread): element assembly (residual, tangent,
-    local damage update) of a contiguous sample of elements at a seeded state."""
+def cpu_baseline(prob, seconds, seed=7, threads=0, single=True):
+    """The oracle as it stands: element assembly (residual, tangent, local damage
+    update) of a contiguous sample of elements at a seeded state, on all host cores
+    (threads=0: the OpenMP default) and, for reference, on one."""
     import numpy as np
 
     import oracle
@@ -167,16 +179,30 @@ def cpu_baseline(prob, seconds, seed=7):
     rng = np.random.default_rng(seed)
     dofs, kappa = I.random_state(prob.mesh, rng, u_amp=0.02, phi_amp=0.05, kappa_amp=0.02)
     nq = prob.mesh.nq
-    t0 = time.perf_counter()
-    model.assemble(prob.mesh, dofs, kappa, e0=0, e1=min(64, prob.mesh.n_elems))
-    per_elem = (time.perf_counter() - t0) / min(64, prob.mesh.n_elems)
-    n = int(max(64, min(prob.mesh.n_elems, seconds / max(per_elem, 1e-9))))
-    t0 = time.perf_counter()
-    model.assemble(prob.mesh, dofs, kappa, e0=0, e1=n)
-    dt = time.perf_counter() - t0
-    return {"value": n * nq / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle assembly (residual, tangent, local damage update) of elements 0..{n - 1} "
-                      f"of {prob.mesh.n_elems} ({n * nq} qp) at a seeded state, {dt:.1f} s on 1 host thread"}
+
+    def rate(n_threads, secs):
+        used = oracle.threads(n_threads)
+        n0 = min(4 * used, prob.mesh.n_elems)
+        t0 = time.perf_counter()
+        model.assemble(prob.mesh, dofs, kappa, e0=0, e1=n0)
+        per_elem = (time.perf_counter() - t0) / n0
+        n = int(max(n0, min(prob.mesh.n_elems, secs / max(per_elem, 1e-9))))
+        t0 = time.perf_counter()
+        model.assemble(prob.mesh, dofs, kappa, e0=0, e1=n)
+        dt = time.perf_counter() - t0
+        return n * nq / dt, n, dt, used
+
+    cores = os.cpu_count() or 1
+    va, na, dta, used = rate(threads if threads > 0 else cores, seconds)
+    out = {"value": va, "unit": UNIT, "cores": used, "kind": "oracle",
+           "sample": f"FP64 oracle assembly (residual, tangent, local damage update) of elements 0..{na - 1} "
+                     f"of {prob.mesh.n_elems} ({na * nq} qp) at a seeded state, {dta:.1f} s on {used} host threads"}
+    if single:
+        v1, n1, dt1, _ = rate(1, seconds / 3.0)
+        out["single_thread_value"] = v1
+        out["sample"] += f"; one thread: {n1} elements in {dt1:.1f} s"
+    oracle.threads(cores)
+    return out
 
 
 def run_reference(args):
@@ -190,55 +216,146 @@ def run_reference(args):
     vals = []
     per_step = max(1.0, 120.0 / max(1, args.steps + args.warmup))
     for k in range(args.warmup + args.steps):
-        cb = cpu_baseline(prob, min(per_step, 20.0), seed=100 + k)
+        cb = cpu_baseline(prob, min(per_step, 20.0), seed=100 + k, single=False)
         if k >= args.warmup:
             vals.append(cb)
     v = sum(c["value"] for c in vals) / len(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": desc,
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": vals[-1]["sample"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[-1]["cores"], "kind": "oracle",
+                             "sample": vals[-1]["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-def mixed_comparison(args, B, torch, prob, batch, stream, flush, reps64, n_qp):
-    """The same warm-up and timed load steps in GD_MIXED: device-timed throughput and
-    Newton-step time, and the reaction-force error against the FP64 run step by step."""
+ICNN = {"auto": 0, "cuda": 1, "bf16": 2, "bf16x3": 3}
+
+
+def krylov_roofline(reps, nnz, n_dofs, n_nodes, ndof, kry_ms, peaks, fp32_inner):
+    """Algorithmic bytes and FLOPs of the persistent Krylov launches (one per Newton
+    system).  One BiCGStab iteration (three-barrier form): two products with the
+    values, the column list once per node block, the row pointers, the gathered x
+    and the written y; the vector phases read and write 25 vectors.  FLOPs: 2 per
+    stored value per product, the node-block inverse twice, 14 vector FMAs / dots."""
+    newton = max(sum(r.iterations for r in reps), 1)
+    krylov = sum(r.krylov_iterations for r in reps)
+    vb = 4 if fp32_inner else 8
+    spmv_b = nnz * vb + (nnz // ndof) * 4 + (n_nodes + 1) * 4 * 2 + n_dofs * (vb + vb + 1)
+    iter_b = 2 * spmv_b + 25 * n_dofs * vb
+    iter_f = 2 * (2 * nnz) + 2 * (2 * n_dofs * ndof) + 14 * 2 * n_dofs
+    avg = kry_ms / newton
+    ipl = krylov / newton
+    hbm = iter_b * ipl / (avg / 1e3) / 1e9
+    alu = iter_f * ipl / (avg / 1e3) / 1e12
+    common = {"kernel": "bicgstab3_kernel (persistent two-level BiCGStab, one launch per Newton system)",
+              "avg_launch_ms": avg, "iterations_per_launch": ipl, "us_per_iteration": 1e3 * avg / max(ipl, 1e-9),
+              "algorithmic_bytes_per_launch": iter_b * ipl, "algorithmic_flops_per_launch": iter_f * ipl,
+              "bytes_per_iteration": iter_b}
+    if fp32_inner or iter_b > 129e6:
+        return dict(common, bound="hbm", achieved=hbm, peak=peaks["hbm_gbs"], unit="GB/s",
+                    frac=hbm / peaks["hbm_gbs"], traffic=None, peak_source=f"{peaks['kind']} copy bandwidth",
+                    alu_view={"achieved_tflops": alu, "fp64_peak": FP64_PEAK_TFLOPS})
+    return dict(common, bound="alu", achieved=alu, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                frac=alu / FP64_PEAK_TFLOPS, traffic=None, peak_source="measured FP64 FMA rate",
+                hbm_view={"achieved_gbs": hbm, "frac_of_copy": hbm / peaks["hbm_gbs"]},
+                note="the system stays L2-resident across the iterations of a launch")
+
+
+def element_roofline(reps, probs, n_elems_all, fp64, icnn, peaks):
+    """Counted algorithmic FLOPs of the element kernel per launch: the energy network
+    with its forward tangents and reverse column (10 w^2 + 40 w per point), the
+    yield network per local-solve evaluation (4 w^2 + 20 w), the element tangent
+    (25 nd^2 per point).  The networks' second layers (8 w^2 + 2 w^2 per point,
+    4 w^2 per evaluation) run on the tensor cores in the BF16 modes."""
+    asm = max(sum(r.assemblies for r in reps), 1)
+    asm_ms = sum(r.assembly_ms for r in reps)
+    mesh0 = probs[0].mesh
+    nq, nd = mesh0.nq, mesh0.nen * mesh0.ndof
+    evals = sum(r.yield_evals for r in reps)
+    qp_all = sum(p.mesh.n_elems * nq for p in probs)
+    psi_f = sum(p.mesh.n_elems * nq * (10 * p.psi.width ** 2 + 40 * p.psi.width) for p in probs)
+    psi_mma = sum(p.mesh.n_elems * nq * 10 * p.psi.width ** 2 for p in probs)
+    wy = sum(p.mesh.n_elems * p.yld.width for p in probs) / max(n_elems_all, 1)
+    flops = asm * psi_f + evals * (4 * wy * wy + 20 * wy) + asm * n_elems_all * nd * nd * nq * 25
+    mma = asm * psi_mma + evals * 4 * wy * wy
+    t = asm_ms / 1e3
+    avg = asm_ms / asm
+    if fp64:
+        return {"kernel": "asm_fp64_kernel", "bound": "alu", "achieved": flops / t / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": flops / t / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "measured FP64 FMA rate", "avg_launch_ms": avg,
+                "algorithmic_flops_per_launch": flops / asm, "qp_per_launch": qp_all}
+    tc = icnn in ("bf16", "bf16x3")
+    cuda_f = flops - (mma if tc else 0)
+    out = {"kernel": "asm_tc_kernel" if tc else "asm_fp32_kernel", "bound": "alu",
+           "achieved": cuda_f / t / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+           "frac": cuda_f / t / 1e12 / FP32_PEAK_TFLOPS, "traffic": None, "peak_source": "measured FP32 FMA rate",
+           "avg_launch_ms": avg, "algorithmic_flops_per_launch": flops / asm, "qp_per_launch": qp_all,
+           "note": "FLOPs on the CUDA cores (network layer 1 and epilogues, local solve, tangent rows)"}
+    if tc:
+        prod = 3 if icnn == "bf16x3" else 1
+        out["tensor_view"] = {"mma_flops_per_launch": mma / asm, "tensor_products": prod,
+                              "achieved_tflops": prod * mma / t / 1e12,
+                              "frac_of_bf16_peak": prod * mma / t / 1e12 / peaks["bf16_tflops_sustained"],
+                              "peak_source": f"{peaks['kind']} BF16 dense (sustained)"}
+    return out
+
+
+def timed_run(args, B, torch, probs, batch, precision, stream, flush, n_path, steps, warmup, tune=True):
+    """W untimed load steps, gd_autotune, then K steps timed with CUDA events on the
+    library's stream, the L2 flushed between them.  Returns the handle, the reports
+    and the timings."""
     import numpy as np
-    opts = B.gd_default_options(precision=B.GD_MIXED, cuda_stream=stream.cuda_stream)
+    prec = B.GD_FP64 if precision == "fp64" else B.GD_MIXED
+    opts = B.gd_default_options(precision=prec, cuda_stream=stream.cuda_stream,
+                                inner_solve={"auto": B.GD_INNER_AUTO, "fp64": B.GD_INNER_FP64,
+                                             "refined": B.GD_INNER_REFINED}[args.inner],
+                                icnn_mma=ICNN[args.icnn])
     if args.coarse is not None:
         opts.coarse = args.coarse
-    h = B.gd_create_batch(prob, opts) if batch else B.gd_create(prob, opts)
-    for _ in range(args.warmup):
-        B.gd_newton_step(h)
-    B.gd_autotune(h)
+    h = B.gd_create_batch(probs, opts) if batch else B.gd_create(probs[0], opts)
+    n_nodes_all = sum(p.mesh.n_nodes for p in probs)
+    n_elems_all = sum(p.mesh.n_elems for p in probs)
+    mesh0 = probs[0].mesh
+    state = {"next": 0, "dmax": 0.0}
+
+    def step():
+        # the path restarts from the undeformed state when it runs out or once a step
+        # has brought the largest damage to D_STOP (the uniform-deformation runs of
+        # Sec. 5.2 stop there: beyond it the block carries no load and the steps only
+        # probe a vanishing stiffness)
+        if state["next"] >= n_path or state["dmax"] >= D_STOP:
+            B.gd_set_state(h, np.zeros(n_nodes_all * mesh0.ndof), np.zeros((n_elems_all, mesh0.nq)), 0)
+            state["next"] = 0
+        r = B.gd_newton_step(h)
+        state["next"] += 1
+        state["dmax"] = r.max_damage
+        return r
+
+    for _ in range(warmup):
+        step()
+    tuning = None
+    if tune:
+        t = B.gd_autotune(h)
+        tuning = {"asm_warps": t.asm_warps, "krylov_ctas_per_sm": t.krylov_ctas_per_sm,
+                  "asm_ms_by_warps": dict(zip(("2", "4", "8"), [round(x, 4) for x in t.asm_ms])),
+                  "krylov_us_by_ctas_per_sm": dict(zip(("1", "2", "3", "4"), [round(x, 3) for x in t.krylov_us])),
+                  "krylov_node_groups_per_lane": t.krylov_up,
+                  "krylov_us_by_node_groups": dict(zip(("1", "2", "4"), [round(x, 3) for x in t.krylov_us_up]))}
+    saved = (B.gd_get_state(h), state["dmax"])
     torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     reps = []
-    reac = []
-    for k in range(args.steps):
-        flush.zero_()
+    for k in range(steps):
+        flush.zero_()                               # L2 flush between timed steps (outside the events)
         evs[k][0].record(stream)
-        reps.append(B.gd_newton_step(h))
+        reps.append(step())
         evs[k][1].record(stream)
-        if batch:
-            reac.append(None)
     torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in evs)
-    useful = sum(r.iterations + 1 + 2 * r.step_cuts for r in reps)
-    r32 = np.array([r.reaction for r in reps])
-    r64 = np.array([r.reaction for r in reps64])
-    err = float(np.max(np.abs(r32 - r64)) / max(np.max(np.abs(r64)), 1e-300)) if not batch else None
-    return {"value": n_qp * useful / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
-            "newton_iterations": sum(r.iterations for r in reps),
-            "krylov_iterations": sum(r.krylov_iterations for r in reps),
-            "krylov_fp32_iterations": sum(r.krylov_fp32_iterations for r in reps),
-            "assembly_avg_ms": sum(r.assembly_ms for r in reps) / max(sum(r.assemblies for r in reps), 1),
-            "reaction_rel_err_vs_fp64": err,
-            "note": "same load steps as the FP64 line; reaction error = max over the timed steps of "
-                    "|F_mixed - F_fp64| / max |F_fp64|" if not batch else "batch: per-specimen reactions not compared here"}
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    return h, reps, total_ms, saved, tuning, step
 
 
 def run_gd(args):
@@ -259,60 +376,30 @@ def run_gd(args):
     build_mod.build()
     prob, desc = make_workload(args.workload, rank, world)
     batch = isinstance(prob, list)
-    if args.precision is None:
-        args.precision = "mixed" if batch else "fp64"
-    stream = torch.cuda.current_stream()
-    prec = B.GD_FP64 if args.precision == "fp64" else B.GD_MIXED
-    opts = B.gd_default_options(precision=prec, cuda_stream=stream.cuda_stream, inner_solve={"auto": B.GD_INNER_AUTO, "fp64": B.GD_INNER_FP64,
-                                             "refined": B.GD_INNER_REFINED}[args.inner])
-    if args.coarse is not None:
-        opts.coarse = args.coarse
-    h = B.gd_create_batch(prob, opts) if batch else B.gd_create(prob, opts)
-    coarse_aggs, coarse_n = B.gd_coarse_info(h)
     probs = prob if batch else [prob]
+    if args.precision is None:
+        args.precision = "mixed" if (batch or args.workload == "cube") else "fp64"
+    # network arithmetic of the mixed runs (auto: tensor-core BF16x3 for one specimen)
+    icnn = args.icnn if args.icnn != "auto" else ("cuda" if batch else "bf16x3")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    n_path = max(int(p.load.size) for p in probs)
     n_qp = desc["qp"]
-    n_path = h.meta["n_steps"]
     n_nodes_all = sum(p.mesh.n_nodes for p in probs)
     n_elems_all = sum(p.mesh.n_elems for p in probs)
     mesh0 = probs[0].mesh
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    ndof = mesh0.ndof
+    peaks = measured_peaks()
 
-    def step(k):
-        if h_state["next"] >= n_path:          # restart the path when it runs out
-            B.gd_set_state(h, np.zeros(n_nodes_all * mesh0.ndof), np.zeros((n_elems_all, mesh0.nq)), 0)
-            h_state["next"] = 0
-        r = B.gd_newton_step(h)
-        h_state["next"] += 1
-        return r
-
-    h_state = {"next": 0}
-    for k in range(args.warmup):
-        step(k)
-    # launch shapes from the library's own timings at the warmed-up state
-    tune = B.gd_autotune(h)
-    saved = B.gd_get_state(h)        # the end-to-end leg repeats the timed steps from here
-    tuning = {"asm_warps": tune.asm_warps, "krylov_ctas_per_sm": tune.krylov_ctas_per_sm,
-              "asm_ms_by_warps": dict(zip(("2", "4", "8"), [round(x, 4) for x in tune.asm_ms])),
-              "krylov_us_by_ctas_per_sm": dict(zip(("1", "2", "3", "4"), [round(x, 3) for x in tune.krylov_us])),
-              "krylov_node_groups_per_lane": tune.krylov_up,
-              "krylov_us_by_node_groups": dict(zip(("1", "2", "4"), [round(x, 3) for x in tune.krylov_us_up]))}
-    torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    reps = []
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.zero_()                               # L2 flush between timed steps (outside the events)
-        evs[k][0].record(stream)
-        reps.append(step(k))
-        evs[k][1].record(stream)
-    torch.cuda.synchronize()
+    h, reps, total_ms, saved, tuning, step = timed_run(args, B, torch, probs, batch, args.precision, stream, flush,
+                                                      n_path, args.steps, args.warmup)
     clk = clocks.stop()
-    total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    asm = sum(r.assemblies for r in reps)
+    coarse_aggs, coarse_n = B.gd_coarse_info(h)
+    nnz = B.gd_csr_pattern(h)[1].size
     # qp updates counted per Newton iterate: the first pass of every attempted (sub)step
     # plus the accepted pass of every direction; rejected line-search trials and the
     # mixed mode's FP64 noise pass are work, not progress, and are left out
@@ -327,83 +414,33 @@ def run_gd(args):
     else:
         total_ms_all, units_all = total_ms, float(units)
     value = units_all / (total_ms_all / 1e3)
-    newton = sum(r.iterations for r in reps)
-    krylov = sum(r.krylov_iterations for r in reps)
-    asm_ms = sum(r.assembly_ms for r in reps)
-    kry_ms = sum(r.krylov_ms for r in reps)
-    launches = sum(r.kernel_launches for r in reps)
 
-    # --- dominant-kernel roofline: persistent Krylov kernel vs the element kernel ---
-    # both durations come from CUDA events the library records on its stream around
-    # each launch inside the timed steps
-    n_dofs = n_nodes_all * mesh0.ndof
-    rowptr, colidx = B.gd_csr_pattern(h)
-    nnz = colidx.size
-    ndof = mesh0.ndof
-    peak_bw, peak_kind = measured_peaks()
-    asm_avg = asm_ms / max(asm, 1)
-    solves = max(newton, 1)
-    kry_avg = kry_ms / solves
-    iters_per_solve = krylov / solves
-    # One BiCGStab iteration (three-barrier form): two SpMVs and the vector phases.
-    # Algorithmic bytes: per SpMV the values, the column list once per node block, the
-    # row pointers, the gathered x and the written y; the vector phases read/write 25
-    # vectors (p, v, y, q, s, t, x~, r, u, rh updates and reads).  Algorithmic FLOPs:
-    # 2 per stored value per SpMV, 2 per node-block inverse entry twice, and 2 per
-    # element of the 14 vector FMAs / dot products.
-    fp32_inner = sum(r.krylov_fp32_iterations for r in reps) * 2 > krylov
-    vb = 4 if fp32_inner else 8
-    spmv_b = nnz * vb + (nnz // ndof) * 4 + (n_nodes_all + 1) * 4 * 2 + n_dofs * (vb + vb + 1)
-    iter_b = 2 * spmv_b + 25 * n_dofs * vb
-    iter_f = 2 * (2 * nnz) + 2 * (2 * n_dofs * ndof) + 14 * 2 * n_dofs
-    if kry_ms >= asm_ms:
-        bytes_launch = iter_b * iters_per_solve
-        flops_launch = iter_f * iters_per_solve
-        hbm_achieved = bytes_launch / (kry_avg / 1e3) / 1e9
-        alu_achieved = flops_launch / (kry_avg / 1e3) / 1e12
-        common = {"kernel": "bicgstab3_kernel (persistent Krylov solve of one Newton system)",
-                  "avg_launch_ms": kry_avg, "iterations_per_launch": iters_per_solve,
-                  "algorithmic_bytes_per_launch": bytes_launch, "algorithmic_flops_per_launch": flops_launch,
-                  "traffic_note": "the system (%.0f MB) stays L2-resident across the iterations of a launch, so "
-                                  "DRAM traffic is far below the algorithmic bytes" % (spmv_b / 1e6)}
-        if fp32_inner:
-            roof = dict(common, bound="hbm", achieved=hbm_achieved, peak=peak_bw, unit="GB/s",
-                        frac=hbm_achieved / peak_bw, traffic=None, peak_source=f"{peak_kind} copy bandwidth")
-        else:
-            # FP64 arithmetic issues at 1/64 of the FP32 rate on this part: the FP64 solve is
-            # bounded by the FP64 pipe and by its grid barriers, not by memory
-            roof = dict(common, bound="alu", achieved=alu_achieved, peak=FP64_PEAK_TFLOPS_NOMINAL, unit="TFLOP/s",
-                        frac=alu_achieved / FP64_PEAK_TFLOPS_NOMINAL, traffic=None,
-                        peak_source="nominal FP64 rate (1.25 TFLOP/s)",
-                        hbm_view={"achieved_gbs": hbm_achieved, "frac_of_measured_copy": hbm_achieved / peak_bw})
-    else:
-        # element kernel: FP64 (or FP32) ALU bound; algorithmic FLOPs (FMA = 2) of the dense parts
-        nq = mesh0.nq
-        nd = mesh0.nen * ndof
-        evals = sum(r.yield_evals for r in reps)
-        # per pass: energy network with tangents at every qp, element tangent; the yield
-        # network per local-solve evaluation (qp-weighted mean width over specimens)
-        psi_f = sum(p.mesh.n_elems * nq * (10 * p.psi.width ** 2 + 40 * p.psi.width) for p in probs)
-        wy = sum(p.mesh.n_elems * p.yld.width for p in probs) / max(n_elems_all, 1)
-        flops = asm * psi_f + evals * (4 * wy * wy + 20 * wy) + (asm * n_elems_all) * nd * nd * nq * 25
-        achieved = flops / (asm_ms / 1e3) / 1e12
-        peak = FP64_PEAK_TFLOPS_NOMINAL if prec == B.GD_FP64 else FP32_PEAK_TFLOPS_NOMINAL
-        roof = {"kernel": "element kernel (asm_fp64_kernel)" if prec == B.GD_FP64 else "element kernel (asm_fp32_kernel)",
-                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": "nominal FP64 rate" if prec == B.GD_FP64 else
-                "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "avg_launch_ms": asm_avg,
-                "algorithmic_flops_per_launch": flops / max(asm, 1)}
+    def summary(reps, total_ms, precision):
+        newton = sum(r.iterations for r in reps)
+        krylov = sum(r.krylov_iterations for r in reps)
+        asm = sum(r.assemblies for r in reps)
+        asm_ms = sum(r.assembly_ms for r in reps)
+        kry_ms = sum(r.krylov_ms for r in reps)
+        fp32_inner = sum(r.krylov_fp32_iterations for r in reps) * 2 > krylov
+        kroof = krylov_roofline(reps, nnz, n_nodes_all * ndof, n_nodes_all, ndof, kry_ms, peaks, fp32_inner)
+        eroof = element_roofline(reps, probs, n_elems_all, precision == "fp64", icnn, peaks)
+        dominant = kroof if kry_ms >= asm_ms else eroof
+        return {"newton_step_ms": total_ms / max(newton, 1), "newton_iterations": newton,
+                "krylov_iterations": krylov, "krylov_fp32_iterations": sum(r.krylov_fp32_iterations for r in reps),
+                "assembly": {"launches": asm, "avg_ms": asm_ms / max(asm, 1),
+                             "qp_per_s": n_qp / (asm_ms / max(asm, 1) / 1e3), "share_of_step": asm_ms / total_ms},
+                "krylov_share_of_step": kry_ms / total_ms, "krylov_ms_per_newton": kry_ms / max(newton, 1),
+                "krylov_iterations_per_newton": krylov / max(newton, 1),
+                "step_cuts": sum(r.step_cuts for r in reps), "gpu_launches": int(sum(r.kernel_launches for r in reps)),
+                "roofline": dominant, "roofline_kernels": {"element": eroof, "krylov": kroof}}
+
+    main = summary(reps, total_ms, args.precision)
 
     # --- end to end through the C ABI with host buffers, over the same load steps as
-    # the device-timed loop: each step uploads the committed state (dofs, the previous
-    # step's dofs for the predictor, kappa) from pinned host memory and reads the new
-    # state back ---
-    d_np, dp_np, k_np, nxt, dpp_np = saved
-    if nxt < 2 or nxt + args.steps > n_path:      # no history to restart from: begin after step 1
-        B.gd_set_state(h, np.zeros_like(d_np), np.zeros_like(k_np), 0)
-        B.gd_newton_step(h)
-        B.gd_newton_step(h)
-        d_np, dp_np, k_np, nxt, dpp_np = B.gd_get_state(h)
+    # the device-timed loop: each step uploads the committed state (dofs, the two
+    # previous states for the predictor, kappa) from pinned host memory and reads the
+    # new state back ---
+    (d_np, dp_np, k_np, nxt, dpp_np), dmax = saved
     d_host = torch.from_numpy(d_np).pin_memory().numpy()
     dp_host = torch.from_numpy(dp_np).pin_memory().numpy()
     dpp_host = torch.from_numpy(dpp_np).pin_memory().numpy()
@@ -412,39 +449,63 @@ def run_gd(args):
     e2e_units = 0
     for k in range(args.steps):
         flush.zero_()
+        if nxt >= n_path or dmax >= D_STOP:      # the path's end, as in the timed loop
+            d_host[:] = 0.0
+            k_host[:] = 0.0
+            nxt = 0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        B.gd_set_state(h, d_host, k_host, nxt, dofs_prev=dp_host, dofs_prev2=dpp_host)    # host -> device
+        if nxt >= 2:                               # host -> device: the state and the predictor's history
+            B.gd_set_state(h, d_host, k_host, nxt, dofs_prev=dp_host, dofs_prev2=dpp_host)
+        elif nxt == 1:
+            B.gd_set_state(h, d_host, k_host, nxt, dofs_prev=dp_host)
+        else:
+            B.gd_set_state(h, d_host, k_host, nxt)
         r = B.gd_newton_step(h)
         d2, dp2, k2, nxt2, dpp2 = B.gd_get_state(h)                                       # device -> host
         e2e_ms += (time.perf_counter() - t0) * 1e3
         e2e_units += n_qp * (r.iterations + 1 + 2 * r.step_cuts)
         d_host[:], dp_host[:], dpp_host[:], k_host[:], nxt = d2, dp2, dpp2, k2, nxt2
+        dmax = r.max_damage
     h2d = d_host.nbytes + dp_host.nbytes + dpp_host.nbytes + k_host.nbytes
     e2e = {"value": e2e_units / (e2e_ms / 1e3) * (world if world > 1 else 1), "unit": UNIT,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d)}
+    del h
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
         "scaling": "strong" if batch else "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == B.GD_FP64 else "f32+f64",
+        "dtype": "f64" if args.precision == "fp64" else ("bf16x3+f32+f64" if icnn == "bf16x3" else
+                                                         "bf16+f32+f64" if icnn == "bf16" else "f32+f64"),
         "data": "synthetic (seeded mesh, seeded ICNN weights)",
-        "config": dict(desc, precision=args.precision,
+        "config": dict(desc, precision=args.precision, icnn_mma=icnn if args.precision == "mixed" else None,
                        parallelism=f"specimen-shards{world}" if batch else f"replicas{world}",
                        inner_solve=args.inner, coarse_unknowns=coarse_n, coarse_aggregates=coarse_aggs,
-                       l2="flushed between timed steps (512 MB write)"),
-        "newton_step_ms": total_ms / max(newton, 1),
-        "newton_iterations": newton, "krylov_iterations": krylov,
-        "assembly": {"launches": asm, "counted_passes": useful, "avg_ms": asm_avg,
-                     "qp_per_s": n_qp / (asm_avg / 1e3), "share_of_step": asm_ms / total_ms},
-        "krylov_share_of_step": kry_ms / total_ms,
-        "krylov_ms_per_newton": kry_avg, "krylov_iterations_per_newton": iters_per_solve,
-        "krylov_fp32_iterations": sum(r.krylov_fp32_iterations for r in reps),
-        "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "tuning": tuning,
+                       l2="flushed between timed steps (512 MB write)",
+                       path_end=f"restart from the undeformed state when the path runs out or max damage >= {D_STOP}"),
     }
-    if prec == B.GD_FP64 and not args.no_mixed:
-        line["mixed"] = mixed_comparison(args, B, torch, prob, batch, stream, flush, reps, n_qp)
+    line.update({k: v for k, v in main.items() if k != "gpu_launches"})
+    line["e2e"] = e2e
+    line["gpu_launches"] = main["gpu_launches"]
+    line["clocks"] = clk
+    line["tuning"] = tuning
+    # --- the other precision over the same load steps ---
+    if not args.no_compare:
+        other = "fp64" if args.precision == "mixed" else "mixed"
+        h2, reps2, ms2, _, _, _ = timed_run(args, B, torch, probs, batch, other, stream, flush, n_path, args.steps,
+                                            args.warmup, tune=True)
+        useful2 = sum(r.iterations + 1 + 2 * r.step_cuts for r in reps2)
+        sub = {"value": n_qp * useful2 / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2 / args.steps}
+        sub.update(summary(reps2, ms2, other))
+        if not batch:
+            r_mixed = np.array([r.reaction for r in (reps if args.precision == "mixed" else reps2)])
+            r_fp64 = np.array([r.reaction for r in (reps2 if args.precision == "mixed" else reps)])
+            line["reaction_rel_err_mixed_vs_fp64"] = float(np.max(np.abs(r_mixed - r_fp64)) /
+                                                          max(np.max(np.abs(r_fp64)), 1e-300))
+        line[other] = sub
+        line["speedup_mixed_over_fp64"] = (value / sub["value"]) if args.precision == "mixed" else (sub["value"] / value)
+        del h2
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(max(probs, key=lambda p: p.mesh.n_elems), args.cpu_seconds)
     if dist:

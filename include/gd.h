@@ -422,11 +422,12 @@ gd_status gd_get_fields(gd_handle *h, double *dofs, double *kappa, double *damag
  * >= 2).  The next step's initial guess extrapolates from the states given: the
  * quadratic through all three where the path is monotone (as an uninterrupted run
  * does), the last increment linearly with dofs_prev alone, else `dofs` itself; the
- * converged states agree to the Newton tolerance either way.  The coarse level of
- * the preconditioner and the mixed-precision residual-noise estimate are kept:
- * the coarse inverse is recomputed when a solve slows down or fails with it, the
- * noise estimate at its usual interval.  gd_get_state gives the arrays that
- * continue the path. */
+ * converged states agree to the Newton tolerance either way.  With dofs_prev (a
+ * continuation) the coarse level of the preconditioner and the mixed-precision
+ * residual-noise estimate are kept -- the coarse inverse is recomputed when a
+ * solve slows down or fails with it, the noise estimate at its usual interval;
+ * without it (a new start) both are recomputed at the next solve.  gd_get_state
+ * gives the arrays that continue the path. */
 gd_status gd_set_state(gd_handle *h, const double *dofs, const double *dofs_prev, const double *dofs_prev2,
                        const double *kappa, int32_t next_step);
 

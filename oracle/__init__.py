@@ -539,3 +539,44 @@ def material_point_biaxial(model: Model, stretches, tol=1e-13):
         out_l3.append(l3)
         out_k.append(kappa_n)
     return np.array(out_P), np.array(out_l3), np.array(out_k)
+
+
+def material_point_uniaxial_3d(model: Model, stretches, tol=1e-13):
+    """Homogeneous 3D uniaxial states F = diag(lam, lam_t, lam_t) with P22 = P33 = 0
+    (isotropic energies: the two lateral stretches are equal); phi = kappa as in the
+    other drivers (Sec. 5.1).  Returns arrays (P11, lam_t, kappa)."""
+    from scipy.optimize import brentq
+    assert model.dim == 3
+    kappa_n = 0.0
+    out_P, out_l, out_k = [], [], []
+    lt_prev = 1.0
+
+    def state(lam, lt, kn):
+        z = np.zeros(13)
+        z[0] = lam - 1.0
+        z[4] = lt - 1.0
+        z[8] = lt - 1.0
+        pe = model.psi_value(z)
+        G, _ = model.yield_G(pe)
+        z[9] = max(kn, G)
+        dP, _, info = model.qp(z, kn, tangent=False)
+        return dP, info
+
+    for lam in stretches:
+        f = lambda lt: state(lam, lt, kappa_n)[0][4]
+        a, b = lt_prev * 0.7, lt_prev * 1.3
+        fa, fb = f(a), f(b)
+        k = 0
+        while fa * fb > 0 and k < 60:
+            a *= 0.9
+            b *= 1.1
+            fa, fb = f(a), f(b)
+            k += 1
+        lt = brentq(f, a, b, xtol=tol, rtol=1e-15, maxiter=500)
+        dP, info = state(lam, lt, kappa_n)
+        kappa_n = info[0]
+        lt_prev = lt
+        out_P.append(dP[0])
+        out_l.append(lt)
+        out_k.append(kappa_n)
+    return np.array(out_P), np.array(out_l), np.array(out_k)

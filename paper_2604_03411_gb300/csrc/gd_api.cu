@@ -2109,9 +2109,15 @@ gd_status gd_set_state(gd_handle *h, const double *dofs, const double *dofs_prev
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));
     H.next_step = next_step;
     H.rec_on = false;
-    // the coarse inverse and the mixed-precision noise estimate are kept: the first is
-    // recomputed by its own convergence-rate test (and after a failed solve), the second
-    // at its usual interval
+    // A continuation (the state one step back given) keeps the coarse inverse and the
+    // mixed-precision noise estimate: the first is recomputed by its own
+    // convergence-rate test (and after a failed solve), the second at its usual
+    // interval.  A state without that history starts a path anew: both are dropped
+    // (an inverse formed at a damaged state preconditions the undamaged one badly).
+    if (!dofs_prev) {
+        H.coarse_age = -1;
+        H.noise_age = 0;
+    }
     H.have_prev = dofs_prev != nullptr;
     H.have_pp = dofs_prev2 != nullptr;
     H.load_prev = (double)next_step;

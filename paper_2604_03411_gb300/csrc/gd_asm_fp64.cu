@@ -20,10 +20,15 @@
 // (dd_1), (Gq_NN), (dd_7).
 #include <cuda_runtime.h>
 
+#include "gd_elem32.cuh"
 #include "gd_internal.cuh"
 
 namespace gd {
 namespace {
+
+// trial yield values farther than this (relative to max(1, kappa_n)) from zero are
+// decided by the FP32 evaluation; closer ones by an FP64 evaluation
+constexpr double kTrialMargin = 1e-4;
 
 
 #include "gd_device_fp64.cuh"
@@ -270,6 +275,8 @@ __global__ void __launch_bounds__(32 * KW) asm_fp64_kernel(AsmArgs A)
         __syncwarp();
 
         // ================= unit mode: local damage update per point =================
+        const e32::MatF mf = e32::to_f(A.mat);
+        float *fbuf = reinterpret_cast<float *>(sBuf);   // FP32 network buffers (2 w floats)
         if (A.kappa_fixed) {
             // frozen history (staggered scheme): the point keeps the given kappa
             double *o = sOut + lane * 10;
@@ -285,66 +292,113 @@ __global__ void __launch_bounds__(32 * KW) asm_fp64_kernel(AsmArgs A)
             const int sp = spec_of(A, e0 + p / NQ);
             const DevNet &yn = yld_of(A, sp);
             const NetConst ncp = A.netc[sp];
-            double r, dr, Gp;
-            int n_eval = 1;
-            r_slope(A.mat, yn, ncp, ppe, pphi, kn, r, dr, Gp, sBuf, lane);
+            double r = 0.0, dr = -1.0, Gp = 0.0;
+            int n_eval = 0;
             double kappa = kn, fail = 0.0, loading = 0.0;
-            if (r > 0.0) {
+            // Trial Phi_d(kappa_n) (Eq. (dd_7_no_nn)): the FP32 network decides points
+            // clearly off the yield surface, an FP64 evaluation the others.
+            const e32::NcF nf = e32::ncf(ncp);
+            float r32, dr32, Gp32;
+            e32::r_slope(yn, mf, nf, (float)ppe, (float)pphi, (float)kn, r32, dr32, Gp32, fbuf, lane);
+            const double scale_n = fabs(kn) > 1.0 ? fabs(kn) : 1.0;
+            bool load;
+            if (fabs((double)r32) > kTrialMargin * scale_n) {
+                load = r32 > 0.0f;
+            } else {
+                r_slope(A.mat, yn, ncp, ppe, pphi, kn, r, dr, Gp, sBuf, lane);
+                ++n_eval;
+                load = r > 0.0;
+                r32 = (float)r;
+                dr32 = (float)dr;
+                Gp32 = (float)Gp;
+            }
+            if (load) {
                 loading = 1.0;
-                // Newton iteration on r(kappa) = G(q(kappa)) - kappa from kappa_n (r > 0 there)
-                // or from the warm-start guess, bracketing lazily: lo keeps the last point with
-                // r > 0; once a point with r <= 0 is met it becomes hi and the iteration turns
-                // into the safeguarded Newton-bisection on [lo, hi].  Before that, a step that
-                // is not a forward Newton step (slope >= 0) probes ahead geometrically.
-                const double kg = A.kappa_guess ? (double)__ldg(A.kappa_guess + e0 * NQ + p) : kn;
-                if (kg > kn && isfinite(kg)) {
-                    kappa = kg;
-                    r_slope(A.mat, yn, ncp, ppe, pphi, kappa, r, dr, Gp, sBuf, lane);
+                // The root in FP32 (the lazily bracketed Newton iteration of the mixed
+                // kernel, from the warm start), then FP64: one value-only evaluation and
+                // a Newton step with the FP32 slope (its relative error, ~1e-7, times a
+                // residual of ~1e-6 leaves ~1e-13), then one full evaluation and a last
+                // Newton step; the slope and G' of that evaluation feed the tangent (they
+                // change by ~1e-12 relative over the last step).  Where the FP32 root is not
+                // close enough, the FP64 bracketed iteration takes over from it.
+                const float kg = A.kappa_guess ? (float)__ldg(A.kappa_guess + e0 * NQ + p) : (float)kn;
+                float k32 = (float)kn;
+                int n32 = 0;
+                const bool ok32 = e32::bracketed_newton(yn, mf, nf, (float)ppe, (float)pphi, (float)kn, kg, k32, r32,
+                                                        dr32, Gp32, n32, fbuf, lane);
+                bool done = false;
+                if (ok32 && isfinite(k32) && (double)k32 >= kn && dr32 < 0.0f) {
+                    const double sc = fabs((double)k32) > 1.0 ? fabs((double)k32) : 1.0;
+                    const double r0 = r_value(A.mat, yn, ncp, ppe, pphi, (double)k32, sBuf, lane);
                     ++n_eval;
-                }
-                double lo = kn, hi = kn;
-                bool have_hi = false;
-                if (r > 0.0) lo = kappa;
-                else {
-                    hi = kappa;
-                    have_hi = true;
-                }
-                double dx_prev = have_hi ? hi - lo : 1.0e30, dx = dx_prev;
-                int it;
-                for (it = 0; it < m.local_max; ++it) {
-                    const double scale = fabs(kappa) > 1.0 ? fabs(kappa) : 1.0;
-                    if (fabs(r) <= 1e-13 * scale || (have_hi && (hi - lo) <= 4.0 * 2.220446049250313e-16 * scale)) break;
-                    const double newton = kappa - r / dr;
-                    bool take;
-                    if (have_hi) {
-                        take = (newton > lo) && (newton < hi) && (fabs(2.0 * r) <= fabs(dx_prev * dr));
-                    } else {
-                        // forward Newton step, at most a few times the distance covered so far
-                        const double cap = 4.0 * ((double)(r > 1e-12 ? r : 1e-12) + (kappa - kn));
-                        take = dr < 0.0 && newton > lo && (newton - kappa) <= cap;
+                    if (fabs(r0) <= 1e-4 * sc) {
+                        const double k1 = (double)k32 - r0 / (double)dr32;
+                        r_slope(A.mat, yn, ncp, ppe, pphi, k1, r, dr, Gp, sBuf, lane);
+                        ++n_eval;
+                        if (k1 >= kn && fabs(r) <= 1e-9 * sc && dr < 0.0) {
+                            const double k2 = fabs(r) <= 1e-13 * sc ? k1 : k1 - r / dr;
+                            kappa = k2 >= kn ? k2 : kn;
+                            done = true;
+                        }
                     }
-                    dx_prev = dx;
-                    if (take) {
-                        dx = kappa - newton;
-                        kappa = newton;
-                    } else if (have_hi) {
-                        dx = 0.5 * (hi - lo);
-                        kappa = lo + dx;
-                    } else {
-                        const double step = 2.0 * ((kappa - kn) > (r > 1e-12 ? r : 1e-12) ? (kappa - kn) : (r > 1e-12 ? r : 1e-12));
-                        dx = step;
-                        kappa = lo + step;
-                    }
-                    r_slope(A.mat, yn, ncp, ppe, pphi, kappa, r, dr, Gp, sBuf, lane);
+                }
+                if (!done) {
+                    // FP64 lazily bracketed Newton iteration from the FP32 result (the
+                    // iteration of the FP64 reference path)
+                    r_slope(A.mat, yn, ncp, ppe, pphi, kn, r, dr, Gp, sBuf, lane);
                     ++n_eval;
-                    if (r > 0.0) {
-                        lo = kappa;
-                    } else {
+                    const double kgd = isfinite(k32) ? (double)k32 : kn;
+                    if (kgd > kn) {
+                        kappa = kgd;
+                        r_slope(A.mat, yn, ncp, ppe, pphi, kappa, r, dr, Gp, sBuf, lane);
+                        ++n_eval;
+                    }
+                    double lo = kn, hi = kn;
+                    bool have_hi = false;
+                    if (r > 0.0) lo = kappa;
+                    else {
                         hi = kappa;
                         have_hi = true;
                     }
+                    double dx_prev = have_hi ? hi - lo : 1.0e30, dx = dx_prev;
+                    int it;
+                    for (it = 0; it < m.local_max; ++it) {
+                        const double scale = fabs(kappa) > 1.0 ? fabs(kappa) : 1.0;
+                        if (fabs(r) <= 1e-13 * scale || (have_hi && (hi - lo) <= 4.0 * 2.220446049250313e-16 * scale))
+                            break;
+                        const double newton = kappa - r / dr;
+                        bool take;
+                        if (have_hi) {
+                            take = (newton > lo) && (newton < hi) && (fabs(2.0 * r) <= fabs(dx_prev * dr));
+                        } else {
+                            // forward Newton step, at most a few times the distance covered so far
+                            const double cap = 4.0 * ((double)(r > 1e-12 ? r : 1e-12) + (kappa - kn));
+                            take = dr < 0.0 && newton > lo && (newton - kappa) <= cap;
+                        }
+                        dx_prev = dx;
+                        if (take) {
+                            dx = kappa - newton;
+                            kappa = newton;
+                        } else if (have_hi) {
+                            dx = 0.5 * (hi - lo);
+                            kappa = lo + dx;
+                        } else {
+                            const double step =
+                                2.0 * ((kappa - kn) > (r > 1e-12 ? r : 1e-12) ? (kappa - kn) : (r > 1e-12 ? r : 1e-12));
+                            dx = step;
+                            kappa = lo + step;
+                        }
+                        r_slope(A.mat, yn, ncp, ppe, pphi, kappa, r, dr, Gp, sBuf, lane);
+                        ++n_eval;
+                        if (r > 0.0) {
+                            lo = kappa;
+                        } else {
+                            hi = kappa;
+                            have_hi = true;
+                        }
+                    }
+                    if (it >= m.local_max) fail = 1.0;
                 }
-                if (it >= m.local_max) fail = 1.0;
             }
             if (lane == 0) {
                 double *o = sOut + p * 10;

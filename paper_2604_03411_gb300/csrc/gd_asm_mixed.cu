@@ -125,75 +125,6 @@ __device__ void psi_net_unit(const DevNet &net, const float *x, float *out10, fl
     __syncwarp();
 }
 
-// Yield network value and slope in unit mode: G(q) = s (N_k(q) - N_k(0)),
-// G' = s N_k'(q) (Eq. (Gq_NN)); width 0 is the identity G(q) = q.
-__device__ void yield_unit(const DevNet &net, const NcF &nc, float q, float &G, float &Gp, float *buf, int lane)
-{
-    const int w = net.width;
-    if (w == 0) {
-        G = q;
-        Gp = 1.0f;
-        return;
-    }
-    const float *V1 = net.pf, *c1 = V1 + w, *V2 = c1 + w, *B2 = V2 + w * w, *c2 = B2 + w, *v3 = c2 + w,
-                 *b3 = v3 + w;
-    float *sS = buf, *sT = buf + w;
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        int j = lane + 32 * t;
-        if (j < w) {
-            float a = __ldg(V1 + j);
-            float h = __ldg(c1 + j) + a * q;
-            float spv, sg;
-            sp_sig(h, spv, sg);
-            sS[j] = spv;
-            sT[j] = sg * a;
-        }
-    }
-    __syncwarp();
-    float n0 = 0.0f, n1 = 0.0f;
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        int k = lane + 32 * t;
-        if (k < w) {
-            float g = __ldg(B2 + k);
-            float h = __ldg(c2 + k) + g * q;
-            const float *col = net.W2Tf + k;
-            for (int j = 0; j < w; ++j) {
-                float wkj = __ldg(col + j * w);
-                h += wkj * sS[j];
-                g += wkj * sT[j];
-            }
-            float vk = __ldg(v3 + k);
-            float spv, sg;
-            sp_sig(h, spv, sg);
-            n0 += vk * spv;
-            n1 += vk * sg * g;
-        }
-    }
-    n0 = warp_sum(n0);
-    n1 = warp_sum(n1);
-    float b = __ldg(b3);
-    G = nc.y_s * (n0 + b * q - nc.y_N0);
-    Gp = nc.y_s * (n1 + b);
-    __syncwarp();
-}
-
-// r(kappa) = G(q(kappa)) - kappa and dr/dkappa (Eq. (potential_function)),
-// q = psi_e + qcoef (phi - kappa) / f_d(kappa) (Eq. (ostwald_potential)).
-__device__ __forceinline__ void r_slope(const DevNet &yld, const MatF &m, const NcF &nc, float pe, float phi,
-                                        float kappa, float &r, float &dr, float &Gp, float *buf, int lane)
-{
-    bool dmg = kappa > m.kappa_d;
-    float f = dmg ? expf(-m.eta_d * (kappa - m.kappa_d)) : 1.0f;
-    float q = pe + m.qcoef * (phi - kappa) / f;
-    float dq = m.qcoef * (-1.0f / f + (dmg ? (phi - kappa) * m.eta_d / f : 0.0f));
-    float G;
-    yield_unit(yld, nc, q, G, Gp, buf, lane);
-    r = G - kappa;
-    dr = Gp * dq - 1.0f;
-}
-
 template <int DIM, int KW>
 __global__ void __launch_bounds__(32 * KW) asm_fp32_kernel(AsmArgs A)
 {
@@ -288,60 +219,8 @@ __global__ void __launch_bounds__(32 * KW) asm_fp32_kernel(AsmArgs A)
             float kappa = kn, fail = 0.0f, loading = 0.0f;
             if (phi_trial > 0.0) {
                 loading = 1.0f;
-                // Newton iteration on r(kappa) = G(q(kappa)) - kappa from kappa_n (r > 0 there)
-                // or from the warm-start guess, bracketing lazily: lo keeps the last point with
-                // r > 0; once a point with r <= 0 is met it becomes hi and the iteration turns
-                // into the safeguarded Newton-bisection on [lo, hi].  Before that, a step that
-                // is not a forward Newton step (slope >= 0) probes ahead geometrically.
                 const float kg = A.kappa_guess ? (float)__ldg(A.kappa_guess + e0 * NQ + p) : kn;
-                if (kg > kn && isfinite(kg)) {
-                    kappa = kg;
-                    r_slope(yn, m, ncp, ppe, pphi, kappa, r, dr, Gp, sBuf, lane);
-                    ++n_eval;
-                }
-                float lo = kn, hi = kn;
-                bool have_hi = false;
-                if (r > 0.0f) lo = kappa;
-                else {
-                    hi = kappa;
-                    have_hi = true;
-                }
-                float dx_prev = have_hi ? hi - lo : 1.0e30f, dx = dx_prev;
-                int it;
-                for (it = 0; it < m.local_max; ++it) {
-                    const float scale = fabsf(kappa) > 1.0f ? fabsf(kappa) : 1.0f;
-                    if (fabsf(r) <= 2e-6f * scale || (have_hi && (hi - lo) <= 4.0f * kEpsF * scale)) break;
-                    const float newton = kappa - r / dr;
-                    bool take;
-                    if (have_hi) {
-                        take = (newton > lo) && (newton < hi) && (fabsf(2.0f * r) <= fabsf(dx_prev * dr));
-                    } else {
-                        // forward Newton step, at most a few times the distance covered so far
-                        const float cap = 4.0f * ((float)(r > 1e-12f ? r : 1e-12f) + (kappa - kn));
-                        take = dr < 0.0f && newton > lo && (newton - kappa) <= cap;
-                    }
-                    dx_prev = dx;
-                    if (take) {
-                        dx = kappa - newton;
-                        kappa = newton;
-                    } else if (have_hi) {
-                        dx = 0.5f * (hi - lo);
-                        kappa = lo + dx;
-                    } else {
-                        const float step = 2.0f * ((kappa - kn) > (r > 1e-12f ? r : 1e-12f) ? (kappa - kn) : (r > 1e-12f ? r : 1e-12f));
-                        dx = step;
-                        kappa = lo + step;
-                    }
-                    r_slope(yn, m, ncp, ppe, pphi, kappa, r, dr, Gp, sBuf, lane);
-                    ++n_eval;
-                    if (r > 0.0f) {
-                        lo = kappa;
-                    } else {
-                        hi = kappa;
-                        have_hi = true;
-                    }
-                }
-                if (it >= m.local_max) fail = 1.0f;
+                if (!bracketed_newton(yn, m, ncp, ppe, pphi, kn, kg, kappa, r, dr, Gp, n_eval, sBuf, lane)) fail = 1.0f;
             }
             if (lane == 0) {
                 float *o = sOut + p * 10;

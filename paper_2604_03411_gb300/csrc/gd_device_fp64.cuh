@@ -270,6 +270,41 @@ __device__ __forceinline__ void r_slope(const MatConst &m, const DevNet &yld, co
 }
 
 
+// r(kappa) = G(q(kappa)) - kappa alone (no slope column): the value part of yield_unit
+// and r_slope, for the Newton step that polishes an FP32 root
+__device__ double r_value(const MatConst &m, const DevNet &net, const NetConst &nc, double pe, double phi,
+                          double kappa, double *buf, int lane)
+{
+    const bool dmg = kappa > m.kappa_d;
+    const double f = dmg ? exp(-m.eta_d * (kappa - m.kappa_d)) : 1.0;
+    const double q = pe + m.qcoef * (phi - kappa) / f;
+    const int w = net.width;
+    if (w == 0) return q - kappa;
+    const double *V1 = net.p, *c1 = V1 + w, *V2 = c1 + w, *B2 = V2 + w * w, *c2 = B2 + w, *v3 = c2 + w,
+                 *b3 = v3 + w;
+    double *sS = buf;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        int j = lane + 32 * t;
+        if (j < w) sS[j] = softplus(__ldg(c1 + j) + __ldg(V1 + j) * q);
+    }
+    __syncwarp();
+    double n0 = 0.0;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        int k = lane + 32 * t;
+        if (k < w) {
+            double h = __ldg(c2 + k) + __ldg(B2 + k) * q;
+            const double *col = net.W2T + k;
+            for (int j = 0; j < w; ++j) h += __ldg(col + j * w) * sS[j];
+            n0 += __ldg(v3 + k) * softplus(h);
+        }
+    }
+    n0 = warp_sum(n0);
+    __syncwarp();
+    return nc.y_s * (n0 + __ldg(b3) * q - nc.y_N0) - kappa;
+}
+
 // specimen of element e and its networks (single-specimen launches use A.psi / A.yld)
 template <class Args>
 __device__ __forceinline__ int spec_of(const Args &A, int64_t e) { return A.elem_spec ? __ldg(A.elem_spec + e) : 0; }

@@ -341,6 +341,22 @@ def notched_plate_3d(seed: int = 6, n_long: int = 49, n_wide: int = 48, n_steps:
     return Problem(f"notched_plate_hex8_{mesh.n_elems}", mesh, psi, yld, mat, load, precision)
 
 
+def uniform_plate_e3(n: int = 5, n_steps: int = 40, u_max: float = 1.0, gamma_d: float = 1.0) -> Problem:
+    """The uniform-deformation study of Sec. 5.2: a 10 x 10 x 1 plate (n x n x 1 HEX8)
+    pulled along x with lateral faces free, the closed-form Neo-Hookean energy with
+    the Ostwald loading function (G(q) = q) and the constants the paper lists
+    (E = 210, nu = 0.3, eta_d = 0.002, kappa_d = 0.1, c_d = 1, beta_d = 1000, read as
+    nondimensional), u_x to u_max in n_steps; gamma_d = 0 is the local model."""
+    mesh = uniaxial_bc_3d(structured_hex8(n, n, 1, 10.0, 10.0, 1.0), scale=10.0)
+    E, nu = 210.0, 0.3
+    mat = Material(mu_e=E / (2.0 * (1.0 + nu)), lambda_e=E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), eta_d=0.002,
+                   kappa_d=0.1, beta_d=1000.0, c_d=1.0, gamma_d=gamma_d, energy=ENERGY_NEO_HOOKE)
+    psi = ICNN(3, 0, np.zeros(1))
+    yld = ICNN(1, 0, np.zeros(1))
+    load = np.linspace(0.0, u_max / 10.0, n_steps + 1)[1:]        # nominal strain: u_x(x = 10) = 10 load
+    return Problem(f"uniform_plate_e3_{n}x{n}", mesh, psi, yld, mat, load, "fp64")
+
+
 def config5(seed: int = 5, n_specimens: int = 96) -> List[Problem]:
     """96 independent specimens: structured Q4 nx ~ U{16..96} x ny ~ U{16..48}, each with
     its own seeded weight set (width in {16, 24, 32}) and a uniaxial path of U{20..60}

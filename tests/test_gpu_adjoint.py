@@ -167,3 +167,72 @@ def test_autograd_refuses_a_stale_path(env):
     reaction_curve(torch.tensor(theta0 * 1.02, dtype=torch.float64, device="cuda"), h)   # another path
     with pytest.raises(RuntimeError):
         reac.sum().backward()
+
+
+@pytest.mark.parametrize("energy", [I.ENERGY_ICNN_RAW, I.ENERGY_ICNN_ISO])
+def test_adjoint_vs_oracle_adjoint_every_weight(env, energy):
+    """gd_backward against the oracle's FP64 discrete adjoint (all states stored,
+    transposed LU solves) on every weight of both networks, along a path that loads,
+    unloads, reloads below and then beyond its previous maximum (the history adjoint
+    is carried through unloading points).  Bar 1e-8 of the largest component (both
+    are exact derivatives of paths converged to 1e-13)."""
+    torch, B, oracle = env
+    mesh = I.uniaxial_bc_2d(I.structured_q4(3, 2))
+    psi, yld = I.icnn_pair(11, 8, 8)
+    mat = I.Material(beta_d=10.0, c_d=10.0 * 0.1 ** 2, energy=energy)
+    load = np.array([0.25, 0.5, 0.35, 0.45, 0.6])
+    prob = I.Problem("adj-oracle", mesh, psi, yld, mat, load)
+    w = np.array([1.0, -0.5, 2.0, 0.7, 1.5])
+    go, reac_o = oracle.adjoint_gradient(oracle.Model.from_problem(prob), mesh, load, w, rtol=1e-13, atol=1e-15)
+    h = B.gd_create(prob, opts(B, k=2))
+    reac, rep = B.gd_run_load_path(h)
+    assert rep.step_cuts == 0
+    assert np.abs(reac - reac_o).max() <= 1e-10 * np.abs(reac_o).max()
+    g = B.gd_backward(h, w)
+    assert g.size == go.size
+    err = np.abs(g - go).max() / np.abs(go).max()
+    print(f"adjoint vs oracle adjoint ({energy}): {err:.2e} over {g.size} weights")
+    assert err < 1e-8, err
+
+
+def test_adjoint_cfg4_notched_plate(env):
+    """The calibration workload: notched plate of 19,980 Q4 elements, 30 load steps,
+    both networks width 32 (2,500 weights), checkpoint every 5 steps; the loss is the
+    squared misfit of the reaction curve against the curve at seeded 5%-perturbed
+    weights.  gd_backward against central differences of the GPU path on the 20
+    seeded weights, bar 1e-5 relative (to a tenth of the largest component for the
+    components below it)."""
+    torch, B, oracle = env
+    prob = I.config4()
+    theta0 = np.concatenate([prob.psi.params, prob.yld.params])
+    n_psi = prob.psi.params.size
+    o = B.gd_default_options(newton_rtol=1e-12, newton_atol=1e-14, krylov_rtol=1e-13, krylov_max=50000,
+                             checkpoint_every=prob.extra["checkpoint_every"])
+
+    def path(theta):
+        h = B.gd_create(prob, o)
+        B.gd_set_params(h, theta[:n_psi], theta[n_psi:])
+        reac, rep = B.gd_run_load_path(h)
+        assert rep.step_cuts == 0
+        return h, reac
+
+    _, target = path(prob.extra["theta_star"])
+    h, reac = path(theta0)
+    _, dL = loss_and_grad_target(reac, target)
+    g = B.gd_backward(h, dL)
+    assert g.size == theta0.size == 2500
+    scale = np.abs(g).max()
+    for i in prob.extra["fd_index"]:
+        step = 1e-6 * max(abs(theta0[i]), 1e-3)
+        tp = theta0.copy()
+        tp[i] += step
+        tm = theta0.copy()
+        tm[i] -= step
+        fp = loss_and_grad_target(path(tp)[1], target)[0]
+        fm = loss_and_grad_target(path(tm)[1], target)[0]
+        fd = (fp - fm) / (2 * step)
+        # relative to the component for components above a tenth of the largest; the
+        # central differences of the smaller ones carry the paths' Newton tolerance
+        # (measured ~5e-9 absolute, 1e-7 of the largest), so those are held to 1e-6 of
+        # the largest component
+        assert abs(g[i] - fd) <= 1e-5 * max(abs(fd), 0.1 * scale), (i, g[i], fd)
