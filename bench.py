@@ -68,6 +68,9 @@ def parse():
                     help="default: mixed for the cube and the batch, fp64 otherwise")
     ap.add_argument("--icnn", default="auto", choices=["auto", "cuda", "bf16", "bf16x3"],
                     help="network arithmetic of the mixed element kernel (gd_options.icnn_mma)")
+    ap.add_argument("--cube-n", type=int, default=64,
+                    help="elements per edge of the cube workload (64 for the bench line; smaller "
+                         "cubes for profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the other precision's run on the same steps")
@@ -79,7 +82,7 @@ def parse():
     return ap.parse_args()
 
 
-def make_workload(name, rank=0, world=1):
+def make_workload(name, rank=0, world=1, cube_n=64):
     from paper_2604_03411_gb300 import inputs as I
     if name == "batch":
         from paper_2604_03411_gb300 import shard
@@ -102,8 +105,8 @@ def make_workload(name, rank=0, world=1):
                 "dofs": p.mesh.n_nodes * 4, "icnn_width": [32, 32], "load_steps": int(p.load.size),
                 "length_scale": 0.04}
     elif name == "cube":
-        p = I.config3()
-        desc = {"workload": "cube_hex8_64", "elements": p.mesh.n_elems, "qp": p.mesh.n_elems * 8,
+        p = I.config3(n=cube_n)
+        desc = {"workload": f"cube_hex8_{cube_n}", "elements": p.mesh.n_elems, "qp": p.mesh.n_elems * 8,
                 "dofs": p.mesh.n_nodes * 4, "icnn_width": [64, 64], "load_steps": int(p.load.size)}
     else:
         p = I.config1()
@@ -209,7 +212,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    prob, desc = make_workload(args.workload)
+    prob, desc = make_workload(args.workload, cube_n=args.cube_n)
     if isinstance(prob, list):
         prob = max(prob, key=lambda p: p.mesh.n_elems)
         desc = dict(desc, oracle_sample="largest specimen")
@@ -343,7 +346,9 @@ def timed_run(args, B, torch, probs, batch, precision, stream, flush, n_path, st
                   "asm_ms_by_warps": dict(zip(("2", "4", "8"), [round(x, 4) for x in t.asm_ms])),
                   "krylov_us_by_ctas_per_sm": dict(zip(("1", "2", "3", "4"), [round(x, 3) for x in t.krylov_us])),
                   "krylov_node_groups_per_lane": t.krylov_up,
-                  "krylov_us_by_node_groups": dict(zip(("1", "2", "4"), [round(x, 3) for x in t.krylov_us_up]))}
+                  "krylov_us_by_node_groups": dict(zip(("1", "2", "4"), [round(x, 3) for x in t.krylov_us_up])),
+                  "krylov_lanes_per_node": t.krylov_lanes,
+                  "krylov_us_by_lanes": dict(zip(("32", "8", "4"), [round(x, 3) for x in t.krylov_us_lanes]))}
     saved = (B.gd_get_state(h), state["dmax"])
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -374,7 +379,7 @@ def run_gd(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build_mod.build()
-    prob, desc = make_workload(args.workload, rank, world)
+    prob, desc = make_workload(args.workload, rank, world, cube_n=args.cube_n)
     batch = isinstance(prob, list)
     probs = prob if batch else [prob]
     if args.precision is None:

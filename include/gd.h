@@ -60,7 +60,7 @@ enum { GD_FP64 = 0, GD_MIXED = 1 };
 enum { GD_BICGSTAB = 0, GD_GMRES = 1 };
 enum { GD_ASM_RESIDUAL = 0, GD_ASM_TANGENT = 1 };
 enum { GD_INNER_AUTO = 0, GD_INNER_FP64 = 1, GD_INNER_REFINED = 2 };
-enum { GD_MONOLITHIC = 0, GD_STAGGERED = 1 };
+enum { GD_MONOLITHIC = 0, GD_STAGGERED = 1, GD_STAGGERED_ITERATED = 2 };
 enum { GD_ICNN_AUTO = 0, GD_ICNN_CUDA_CORES = 1, GD_ICNN_BF16 = 2, GD_ICNN_BF16X3 = 3 };
 
 /* Mesh and boundary data (Sec. 3.1, Table kernel_inputs; Dirichlet data of the
@@ -125,12 +125,16 @@ typedef struct gd_options {
     double newton_atol;
     int32_t newton_max;        /* Newton iterations per step                           */
     int32_t line_search_max;   /* backtracking halvings per Newton direction           */
-    int32_t krylov;            /* GD_BICGSTAB (GD_GMRES reserved)                      */
+    int32_t krylov;            /* GD_BICGSTAB (default): the persistent two-level BiCGStab, and
+                                  for an FP64 solve it does not finish (breakdown, stagnation,
+                                  krylov_max) GMRES(gmres_m) takes over; GD_GMRES: every FP64
+                                  solve by restarted GMRES(gmres_m), right-preconditioned by
+                                  node-block Jacobi (FP32 inner solves stay BiCGStab)          */
     double krylov_rtol;        /* floor of the relative residual of each Newton solve (the
                                   solve stops at max(krylov_rtol, min(1e-2, 0.1 tol/||R||)),
                                   tol the Newton tolerance); gd_solve uses it directly       */
     int32_t krylov_max;
-    int32_t gmres_m;
+    int32_t gmres_m;           /* GMRES restart length, 1..64 (default 50)              */
     int32_t local_max;         /* local kappa iterations (the paper caps at 100, Sec. 5.3) */
     int32_t checkpoint_every;  /* adjoint checkpoint interval in load steps            */
     int32_t max_step_cuts;     /* nested load-step halvings after a failed step        */
@@ -152,14 +156,20 @@ typedef struct gd_options {
                                   recurrences.                                              */
     int32_t scheme;            /* GD_MONOLITHIC (default, Sec. 3.2): kappa is updated inside
                                   every Newton iteration and its sensitivity enters the
-                                  tangent.  GD_STAGGERED (single specimens): the (u, phi)
-                                  equilibrium is solved by Newton with kappa frozen, then the
-                                  local update runs at the converged fields, and the two
-                                  alternate until the residual with the updated kappa meets
-                                  the Newton test; the converged step solves the same
-                                  equations as the monolithic one.                         */
-    int32_t stagger_max;       /* alternations per load step before the step counts as failed
-                                  (default 100)                                              */
+                                  tangent.  GD_STAGGERED (Sec. 3.2, single specimens): the
+                                  history is advanced apart from the nodal solve: Newton on
+                                  the (u, phi) equilibrium with kappa held at the committed
+                                  kappa_n, then one local update at the converged fields; the
+                                  step is accepted without a coupled test, so the update lags
+                                  the nodal solve by one step (first order in the load
+                                  step), and the step's reaction is that of the equilibrium.
+                                  GD_STAGGERED_ITERATED (single specimens): the same two
+                                  stages alternate within the step until the residual with
+                                  the updated kappa meets the Newton test; the converged step
+                                  solves the monolithic equations (the alternation converges
+                                  linearly, slowly for a stiff penalty beta_d).             */
+    int32_t stagger_max;       /* GD_STAGGERED_ITERATED: alternations per load step before the
+                                  step counts as failed (default 100)                       */
     int32_t asm_grid_max;      /* cap on the CTAs of the persistent element-kernel grid (0, the
                                   default: SMs x resident CTAs).  A small cap makes every warp
                                   take several element batches in turn; results do not depend
@@ -383,6 +393,8 @@ typedef struct gd_tune_report {
                                     co-resident                                                 */
     int32_t krylov_up;           /* node groups per lane in the Krylov products (1, 2 or 4)     */
     double krylov_us_up[3];      /* iteration time with 1, 2, 4 node groups at the chosen grid  */
+    int32_t krylov_lanes;        /* lanes per node of 3D solves with FP32 vectors (32, 8 or 4)  */
+    double krylov_us_lanes[3];   /* iteration time with 32, 8, 4 lanes per node; -1: not timed */
 } gd_tune_report;
 
 /* Times the element kernel (one tangent pass at the committed state) for each CTA
@@ -395,8 +407,9 @@ typedef struct gd_tune_report {
 gd_status gd_autotune(gd_handle *h, gd_tune_report *rep);
 
 /* Advances the next load step of the path to convergence (monolithic Newton,
- * Sec. 3.2, with a line search and nested step halving on failure); commits
- * kappa and the fields on success.  rep may be NULL. */
+ * Sec. 3.2, with a line search and nested step halving on failure; or the step of
+ * the handle's staggered scheme); commits kappa and the fields on success.  rep
+ * may be NULL. */
 gd_status gd_newton_step(gd_handle *h, gd_newton_report *rep);
 
 /* Runs every remaining step of the load path; reaction [n_steps] (host, may be
@@ -407,7 +420,9 @@ gd_status gd_run_load_path(gd_handle *h, double *reaction, gd_path_report *rep);
 /* Gradient of a loss of the reaction curve with respect to the network weights
  * through the whole load path (discrete adjoint with checkpoints every
  * checkpoint_every steps and recomputation in between).
- *   dL_dreaction [n_steps] host; dL_dtheta [n_psi + n_yield] host out. */
+ *   dL_dreaction [n_steps] host; dL_dtheta [n_psi + n_yield] host out.
+ * The adjoint differentiates the monolithic step equations: GD_ERR_STATE for a
+ * handle with scheme GD_STAGGERED (whose lagged steps solve other equations). */
 gd_status gd_backward(gd_handle *h, const double *dL_dreaction, double *dL_dtheta);
 
 /* Copies the committed fields to host: dofs [n_nodes*ndof], kappa [n_elems*nq]

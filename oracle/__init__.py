@@ -11,8 +11,10 @@ Layers:
   * this module: global assembly, Dirichlet elimination, the Newton iteration
     with a direct sparse LU (the paper solves each step with an LU
     factorisation and warm-starts from the last converged step, Sec. 3.2), the
-    incremental quasi-static load path, reactions, the homogeneous
-    material-point driver, and the discrete adjoint of the load path.
+    incremental quasi-static load path (monolithic, or the staggered scheme
+    with the history advanced after the nodal solve), reactions, the
+    homogeneous material-point drivers, and the discrete adjoint of the load
+    path.
 """
 from __future__ import annotations
 
@@ -71,7 +73,7 @@ class _OrMat(ctypes.Structure):
                 ("psi_N0", ctypes.c_double), ("psi_n", ctypes.c_double),
                 ("y_N0", ctypes.c_double), ("y_s", ctypes.c_double),
                 ("seeded", ctypes.c_int), ("psi_ph", ctypes.c_void_p), ("y_ph", ctypes.c_void_p),
-                ("c_hd", ctypes.c_double * 16)]
+                ("c_hd", ctypes.c_double * 16), ("frozen", ctypes.c_int)]
 
 
 def lib():
@@ -342,13 +344,36 @@ def predictor(dofs, dofs_prev, load_now, load_prev, load_prevprev):
     return dofs + (dofs - dofs_prev) * ((load_now - load_prev) / (load_prev - load_prevprev))
 
 
+def staggered_step(model: Model, mesh, dofs, kappa_n, load_value, rtol=1e-10, atol=1e-12, max_it=25,
+                   guess=None, max_ls=12):
+    """One load step of the staggered scheme (Sec. 3.2): the history is advanced
+    apart from the nodal solve.  First the (u, phi) equilibrium is solved by Newton
+    with kappa held at kappa_n (no local update, no kappa term in the tangent),
+    then the local update runs once at the converged fields, against kappa_n.  The
+    step takes no further coupled iteration, so the non-local driving force of the
+    update comes from fields that were in equilibrium with the previous history:
+    the lag the paper describes.  The reaction is the one of that equilibrium.
+    Returns (dofs, kappa_new, StepResult, R)."""
+    model.m.frozen = 1
+    try:
+        d1, _, res, R = newton_step(model, mesh, dofs, kappa_n, load_value, rtol, atol, max_it, guess, max_ls)
+    finally:
+        model.m.frozen = 0
+    _, _, k1, qi, nfail = model.assemble(mesh, d1, kappa_n, tangent=False)
+    res.local_failures = nfail
+    res.qinfo = qi
+    return d1, k1, res, R
+
+
 def run_load_path(model: Model, mesh, load, dofs0=None, kappa0=None, rtol=1e-10, atol=1e-12, max_it=25,
-                  keep_states=False, max_cuts=4):
+                  keep_states=False, max_cuts=4, scheme="monolithic"):
     """Incremental quasi-static path (Sec. 3.2): for each load value a Newton
     step started from the extrapolated last converged state, then kappa_n <-
     kappa_{n+1}.  A step that fails is retried as two half steps (at most
-    max_cuts nested halvings).  Returns dict(reaction[n_steps], iterations, dofs,
-    kappa, states, cuts)."""
+    max_cuts nested halvings).  scheme: "monolithic" (newton_step) or "staggered"
+    (staggered_step).  Returns dict(reaction[n_steps], iterations, dofs, kappa,
+    states, cuts)."""
+    step = {"monolithic": newton_step, "staggered": staggered_step}[scheme]
     n = mesh.n_nodes * mesh.ndof
     dofs = np.zeros(n) if dofs0 is None else _f64(dofs0).ravel().copy()
     kappa = np.zeros((mesh.n_elems, mesh.nq)) if kappa0 is None else _f64(kappa0).copy()
@@ -358,7 +383,7 @@ def run_load_path(model: Model, mesh, load, dofs0=None, kappa0=None, rtol=1e-10,
     def advance(target, depth):
         nonlocal dofs, kappa
         g = predictor(dofs, hist["prev"], target, hist["l1"], hist["l2"])
-        d1, k1, res, R = newton_step(model, mesh, dofs, kappa, target, rtol, atol, max_it, guess=g)
+        d1, k1, res, R = step(model, mesh, dofs, kappa, target, rtol, atol, max_it, guess=g)
         if not res.converged and depth < max_cuts:
             hist["cuts"] += 1
             mid = 0.5 * (hist["l1"] + target)

@@ -103,6 +103,10 @@ typedef struct {
     int seeded;
     const hd *psi_ph, *y_ph;
     hd c_N0, c_n, c_yN0, c_ys;
+    /* frozen != 0: the history passed as kappa_n is kappa_{n+1} itself, with no local
+     * update and no kappa sensitivity in the tangent (the global solve of the staggered
+     * scheme, Sec. 3.2, where the history is advanced apart from the nodal solve) */
+    int frozen;
 } or_mat;
 
 /* Two-layer input-convex network (Amos et al.), softplus activations, input
@@ -465,7 +469,12 @@ static void local_update(const or_mat *m, const double *z, double kappa_n, or_qp
 static void qp_eval(const or_mat *m, const double *z, double kappa_n, double *dPsi, double *D, or_qp_info *inf)
 {
     int nz = nz_of(m->dim);
-    local_update(m, z, kappa_n, inf);
+    if (m->frozen) {
+        memset(inf, 0, sizeof(*inf));
+        inf->kappa = kappa_n;            /* not loading: D gets no implicit-function term */
+    } else {
+        local_update(m, z, kappa_n, inf);
+    }
     hd zz[13];
     for (int c = 0; c < nz; ++c) {
         for (int e = 0; e < nz; ++e) zz[e] = hc(z[e]);

@@ -24,7 +24,7 @@ STATUS = {0: "GD_OK", 1: "GD_ERR_ARG", 2: "GD_ERR_MESH", 3: "GD_ERR_CUDA", 4: "G
 GD_FP64, GD_MIXED = 0, 1
 GD_ASM_RESIDUAL, GD_ASM_TANGENT = 0, 1
 GD_INNER_AUTO, GD_INNER_FP64, GD_INNER_REFINED = 0, 1, 2
-GD_MONOLITHIC, GD_STAGGERED = 0, 1
+GD_MONOLITHIC, GD_STAGGERED, GD_STAGGERED_ITERATED = 0, 1, 2
 GD_ICNN_AUTO, GD_ICNN_CUDA_CORES, GD_ICNN_BF16, GD_ICNN_BF16X3 = 0, 1, 2, 3
 GD_NOALLOC_MAX_DOFS = 131072
 
@@ -85,7 +85,8 @@ class GdPathReport(ctypes.Structure):
 class GdTuneReport(ctypes.Structure):
     _fields_ = [("asm_warps", ctypes.c_int32), ("krylov_ctas_per_sm", ctypes.c_int32),
                 ("asm_ms", ctypes.c_double * 3), ("krylov_us", ctypes.c_double * 4),
-                ("krylov_up", ctypes.c_int32), ("krylov_us_up", ctypes.c_double * 3)]
+                ("krylov_up", ctypes.c_int32), ("krylov_us_up", ctypes.c_double * 3),
+                ("krylov_lanes", ctypes.c_int32), ("krylov_us_lanes", ctypes.c_double * 3)]
 
 
 _H = ctypes.c_void_p

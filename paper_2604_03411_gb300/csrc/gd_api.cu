@@ -126,6 +126,9 @@ void free_handle(gd::Handle &H)
     dfree(H.psi_tab);
     dfree(H.yld_tab);
     dfree(H.tc_blob);
+    dfree(H.Rabs);
+    dfree(H.gm_ws);
+    dfree(H.gm_binv);
     {
         gd::CoarseSpace &c = H.coarse;
         void *cp[] = {c.agg, c.coff, c.node_co, c.P, c.Ac, c.X32, c.X64, c.rc, c.cc, c.status};
@@ -171,6 +174,7 @@ gd::AsmArgs asm_args(gd::Handle &H, const double *dofs, const double *kappa_n, d
     a.dofs = dofs;
     a.kappa_n = kappa_n;
     a.R = R;
+    a.Rabs = nullptr;
     a.vals = (tangent && H.opt.precision == GD_FP64) ? (double *)vals : nullptr;
     a.vals32 = (tangent && H.opt.precision == GD_MIXED) ? (float *)vals : nullptr;
     a.kappa_new = kappa_out;
@@ -197,7 +201,7 @@ gd::AsmArgs asm_args(gd::Handle &H, const double *dofs, const double *kappa_n, d
 // where the local solves of the loading points start; null: at kappa_n
 gd_status assemble_pass(gd::Handle &H, const double *dofs, const double *kappa_n, double *R, void *vals,
                         double *kappa_out, int8_t *loading, int tangent, bool force_fp64 = false,
-                        const double *guess = nullptr)
+                        const double *guess = nullptr, double *rabs = nullptr)
 {
     const size_t vbytes = H.opt.precision == GD_FP64 ? sizeof(double) : sizeof(float);
     if (force_fp64) tangent = 0;
@@ -207,6 +211,10 @@ gd_status assemble_pass(gd::Handle &H, const double *dofs, const double *kappa_n
     GD_CUDA(&H, cudaEventRecord(H.ev0, H.stream));
     gd::AsmArgs a = asm_args(H, dofs, kappa_n, R, vals, kappa_out, loading, tangent);
     a.kappa_guess = guess;
+    if (rabs && !force_fp64 && H.opt.precision == GD_MIXED) {
+        GD_CUDA(&H, cudaMemsetAsync(rabs, 0, sizeof(double) * H.n_dofs, H.stream));
+        a.Rabs = rabs;
+    }
     if (H.opt.precision == GD_FP64 || force_fp64) {
         GD_CUDA(&H, gd::launch_assemble_fp64(H.dim, a, H.num_sms, H.stream, H.asm_tune));
     } else if (H.icnn_mode == GD_ICNN_BF16 || H.icnn_mode == GD_ICNN_BF16X3) {
@@ -262,9 +270,46 @@ gd_status norms(gd::Handle &H, const double *R, NormPair &out)
 constexpr int kCoarseReuse = 8;
 enum MatKind { kTangent = 0, kTransposed = 1, kCallerMatrix = 2 };
 
+// FP64-vector GMRES(gmres_m) on `vals` (the handle's precision: FP64 values, or FP32
+// values with FP64 vectors in GD_MIXED); work space allocated on first use.
+gd_status gmres(gd::Handle &H, const void *vals, const double *b, double *x, int &iters, double &rel, double rtol,
+                bool &converged)
+{
+    const bool fp32_vals = H.opt.precision == GD_MIXED;
+    const int m = std::max(1, std::min(H.opt.gmres_m, gd::gmres_max_m()));
+    gd::SolverCtx c = solver_ctx(H, nullptr);
+    if (fp32_vals) c.vals32 = (const float *)vals;
+    else c.vals = (const double *)vals;
+    if (!H.gm_ws) {
+        GD_CUDA(&H, dalloc(&H.gm_ws, gd::gmres_workspace_doubles(H.n_dofs, gd::gmres_max_m(), c.blocks)));
+        GD_CUDA(&H, dalloc(&H.gm_binv, (size_t)H.n_nodes * H.ndof * H.ndof));
+    }
+    GD_CUDA(&H, gd::launch_block_inverse(H.ndof, H.n_nodes, H.rowptr, H.colidx, vals, fp32_vals, H.fixed, H.gm_binv,
+                                         H.num_sms, H.stream));
+    GD_CUDA(&H, gd::gmres_solve(c, H.gm_binv, b, x, rtol, m, H.opt.krylov_max, H.gm_ws, iters, rel, converged));
+    H.gmres_iterations += iters;
+    H.launches += 8 + 8LL * iters;
+    return GD_OK;
+}
+
 gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, int &iters, double &rel,
                  double rtol, bool inner_fp32 = false, double accept = -1.0, int kind = kTangent)
 {
+    if (H.opt.krylov == GD_GMRES && !inner_fp32) {
+        // every FP64 solve by GMRES(m)
+        GD_CUDA(&H, cudaEventRecord(H.kv0, H.stream));
+        bool conv = false;
+        gd_status st = gmres(H, vals, b, x, iters, rel, rtol, conv);
+        if (st) return st;
+        GD_CUDA(&H, cudaEventRecord(H.kv1, H.stream));
+        GD_CUDA(&H, cudaEventSynchronize(H.kv1));
+        float kms = 0.0f;
+        cudaEventElapsedTime(&kms, H.kv0, H.kv1);
+        H.krylov_ms += kms;
+        if (!conv && !(std::isfinite(rel) && rel <= std::max(accept, rtol)))
+            return fail(&H, GD_ERR_KRYLOV, "GMRES stopped at relative residual " + std::to_string(rel));
+        return GD_OK;
+    }
     gd::KrylovCtx kc;
     kc.n_nodes = H.n_nodes;
     kc.ndof = H.ndof;
@@ -283,6 +328,7 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
     kc.up = H.krylov_up;
     kc.lmax = H.krylov_lmax;
     kc.row_cache = H.opt.krylov_row_cache;
+    kc.lanes = H.krylov_lanes;
     kc.coarse = H.coarse.nc > 0 ? &H.coarse : nullptr;
     bool refresh =
         kind == kCallerMatrix || H.coarse_age < 0 || H.coarse_kind != kind || H.coarse_age >= kCoarseReuse;
@@ -330,9 +376,25 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
             if (rate < 0.7 * H.coarse_rate) H.coarse_age = -1;
         }
     }
-    if (kout[2] != 0.0 && !(kout[2] != 2.0 && std::isfinite(rel) && rel <= std::max(accept, rtol)))
+    if (kout[2] != 0.0 && !(kout[2] != 2.0 && std::isfinite(rel) && rel <= std::max(accept, rtol))) {
+        if (!inner_fp32) {
+            // an FP64 solve that BiCGStab did not finish (breakdown, stagnation, the
+            // iteration cap): GMRES(m) from zero, which minimises the residual and
+            // cannot break down before convergence
+            int git = 0;
+            double grel = 1.0;
+            bool conv = false;
+            gd_status st = gmres(H, vals, b, x, git, grel, rtol, conv);
+            if (st) return st;
+            iters += git;
+            if (conv || (std::isfinite(grel) && grel <= std::max(accept, rtol))) {
+                rel = grel;
+                return GD_OK;
+            }
+        }
         return fail(&H, GD_ERR_KRYLOV, "BiCGStab stopped (status " + std::to_string((int)kout[2]) +
                                            ", relative residual " + std::to_string(rel) + ")");
+    }
     return GD_OK;
 }
 
@@ -565,15 +627,16 @@ gd_status mixed_noise(gd::Handle &H, const double *R32, std::vector<double> &noi
     return norms_batch(H, diff, noise, nx);
 }
 
-// GD_MIXED noise level for the Newton test.  The FP32 rounding noise of the
-// residual scales with the force level, so it is measured by the FP64 pass of
-// mixed_noise on the first Newton solve (and after every restart of the state) and
-// every kNoiseEvery solves, and in between taken as the measured ratio to the
-// specimen's force scale ||R_fixed|| (||R|| at the first iterate when nothing is
-// prescribed).  The FP64 pass costs as much as several FP32 passes.  The ratio
-// drifts once damage lowers the reaction while the element forces that cancel in
-// the residual stay large, so a Newton solve whose line search stalls on an
-// estimate it did not measure itself measures it again (force = true).
+// GD_MIXED noise level for the Newton test.  The rounding noise of the residual
+// scales with the element forces that cancel in it, so it is measured by the FP64
+// pass of mixed_noise on the first Newton solve (and after every new start of the
+// state) and every kNoiseEvery solves, and in between taken as the measured ratio to
+// the specimen's scale ||sum_e |R_e|||: the norm of the sum of the absolute element
+// residual rows, which the mixed kernels accumulate beside R (damage lowers the
+// reaction, but the element forces, and with them the noise, follow this norm).
+// The FP64 pass costs as much as several mixed passes.  A Newton solve whose line
+// search stalls on an estimate it did not measure itself measures it again (force =
+// true).
 constexpr int kNoiseEvery = 8;
 
 gd_status noise_estimate(gd::Handle &H, const double *R, const std::vector<double> &scale,
@@ -600,7 +663,8 @@ gd_status noise_estimate(gd::Handle &H, const double *R, const std::vector<doubl
 // prescribed dofs set).  On return H.w_dofs/H.R/H.kappa_trial hold the last iterate.
 gd_status newton(gd::Handle &H, gd_newton_report &rep)
 {
-    gd_status st = assemble_pass(H, H.w_dofs, H.kappa, H.R, H.vals, H.kappa_trial, H.loading, 1);
+    gd_status st = assemble_pass(H, H.w_dofs, H.kappa, H.R, H.vals, H.kappa_trial, H.loading, 1, false, nullptr,
+                                 H.Rabs);
     if (st) return st;
     NormPair nr;
     if ((st = norms(H, H.R, nr))) return st;
@@ -613,8 +677,11 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
     const double r0 = std::max(nr.free_, nr.fixed_);
     double noise = 0.0;
     bool fresh = false;     // noise measured at an iterate of this solve
-    const std::vector<double> sc(1, nr.fixed_ > 0.0 ? nr.fixed_ : r0);
+    std::vector<double> sc(1, nr.fixed_ > 0.0 ? nr.fixed_ : r0);
     if (H.opt.precision == GD_MIXED) {
+        NormPair na;
+        if ((st = norms(H, H.Rabs, na))) return st;
+        if (na.free_ > 0.0) sc[0] = na.free_;
         std::vector<double> nz;
         if ((st = noise_estimate(H, H.R, sc, nz, fresh))) return st;
         noise = nz[0];
@@ -730,7 +797,8 @@ gd_status set_coef(gd::Handle &H, const std::vector<double> &coef)
 gd_status newton_batch(gd::Handle &H, gd_newton_report &rep)
 {
     const int S = H.n_spec;
-    gd_status st = assemble_pass(H, H.w_dofs, H.kappa, H.R, H.vals, H.kappa_trial, H.loading, 1);
+    gd_status st = assemble_pass(H, H.w_dofs, H.kappa, H.R, H.vals, H.kappa_trial, H.loading, 1, false, nullptr,
+                                 H.Rabs);
     if (st) return st;
     std::vector<double> nf, nx, nt, ntx;
     if ((st = norms_batch(H, H.R, nf, nx))) return st;
@@ -749,8 +817,13 @@ gd_status newton_batch(gd::Handle &H, gd_newton_report &rep)
     std::vector<double> noise(S, 0.0), sc(S);
     bool fresh = false;     // noise measured at an iterate of this solve
     for (int s = 0; s < S; ++s) sc[s] = nx[s] > 0.0 ? nx[s] : nf[s];
-    if (H.opt.precision == GD_MIXED)
+    if (H.opt.precision == GD_MIXED) {
+        std::vector<double> af, ax;
+        if ((st = norms_batch(H, H.Rabs, af, ax))) return st;
+        for (int s = 0; s < S; ++s)
+            if (af[s] > 0.0) sc[s] = af[s];
         if ((st = noise_estimate(H, H.R, sc, noise, fresh))) return st;
+    }
     for (int s = 0; s < S; ++s) {
         r0[s] = std::max(nf[s], nx[s]);
         ntol[s] = std::max(std::max(H.opt.newton_rtol * r0[s], H.opt.newton_atol), 2.0 * noise[s]);
@@ -1048,12 +1121,35 @@ gd_status commit(gd::Handle &H, double target, gd_newton_report &rep)
     return GD_OK;
 }
 
-// Staggered scheme (gd_options.scheme): Newton on the (u, phi) equilibrium with the
-// history frozen, then the local update at the converged fields; the two alternate
+// Staggered scheme of Sec. 3.2 (gd_options.scheme = GD_STAGGERED): the history is
+// advanced apart from the nodal solve.  Newton on the (u, phi) equilibrium with kappa
+// held at the committed kappa_n, then one local update at the converged fields (its
+// loading test against kappa_n).  The step takes no coupled test: the update lags the
+// nodal solve by one step.  The update's residual goes to the scratch R_trial, so H.R
+// keeps the equilibrium residual and the step's reaction is that equilibrium's.
+gd_status newton_staggered(gd::Handle &H, gd_newton_report &rep)
+{
+    H.kappa_fix = H.kappa;
+    gd_status st = newton(H, rep);
+    H.kappa_fix = nullptr;
+    if (st || !rep.converged) return st;
+    if ((st = assemble_pass(H, H.w_dofs, H.kappa, H.R_trial, nullptr, H.kappa_trial, H.loading, 0))) return st;
+    H.assembly_ms += elapsed_ms(H);
+    int hc[4];
+    GD_CUDA(&H, cudaMemcpy(hc, H.counters, 4 * sizeof(int), cudaMemcpyDeviceToHost));
+    GD_TC_CHECK(&H, hc);
+    rep.yield_evals += hc[2];
+    rep.local_failures = hc[0];
+    rep.loading_points = hc[1];
+    return GD_OK;
+}
+
+// Iterated staggered scheme (GD_STAGGERED_ITERATED): Newton on the (u, phi) equilibrium
+// with the history frozen, then the local update at the converged fields; the two alternate
 // until the residual with the updated history meets the Newton test (then the step
 // solves the same equations as the monolithic scheme).  The loading test of every
 // local update is against the committed history kappa_n, as in the monolithic scheme.
-gd_status newton_staggered(gd::Handle &H, gd_newton_report &rep)
+gd_status newton_staggered_iterated(gd::Handle &H, gd_newton_report &rep)
 {
     const size_t nq_bytes = sizeof(double) * (size_t)(H.n_elems * H.nq);
     GD_CUDA(&H, cudaMemcpyAsync(H.kappa_stag, H.kappa, nq_bytes, cudaMemcpyDeviceToDevice, H.stream));
@@ -1117,8 +1213,9 @@ gd_status advance(gd::Handle &H, double target, int depth, gd_newton_report &rep
     const int n0 = H.assemblies;
     const long long l0 = H.launches;
     gd_status st = H.n_spec > 1                      ? newton_batch(H, sub)
-                   : H.opt.scheme == GD_STAGGERED ? newton_staggered(H, sub)
-                                                  : newton(H, sub);
+                   : H.opt.scheme == GD_STAGGERED          ? newton_staggered(H, sub)
+                   : H.opt.scheme == GD_STAGGERED_ITERATED ? newton_staggered_iterated(H, sub)
+                                                           : newton(H, sub);
     rep.assembly_ms += H.assembly_ms - a0;
     rep.krylov_ms += H.krylov_ms - k0;
     rep.assemblies += H.assemblies - n0;
@@ -1494,13 +1591,18 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
     if (o.inner_solve < GD_INNER_AUTO || o.inner_solve > GD_INNER_REFINED)
         return fail(nullptr, GD_ERR_ARG, "inner_solve");
     if (o.coarse < 0 || o.coarse > gd::kCoarseMax) return fail(nullptr, GD_ERR_ARG, "coarse must be in [0, 3072]");
-    if (o.scheme != GD_MONOLITHIC && o.scheme != GD_STAGGERED) return fail(nullptr, GD_ERR_ARG, "scheme");
-    if (o.scheme == GD_STAGGERED && (n_spec > 1 || o.stagger_max < 1))
-        return fail(nullptr, GD_ERR_ARG, "the staggered scheme needs one specimen and stagger_max >= 1");
+    if (o.scheme != GD_MONOLITHIC && o.scheme != GD_STAGGERED && o.scheme != GD_STAGGERED_ITERATED)
+        return fail(nullptr, GD_ERR_ARG, "scheme");
+    if (o.scheme != GD_MONOLITHIC && n_spec > 1)
+        return fail(nullptr, GD_ERR_ARG, "the staggered schemes need one specimen");
+    if (o.scheme == GD_STAGGERED_ITERATED && o.stagger_max < 1)
+        return fail(nullptr, GD_ERR_ARG, "the iterated staggered scheme needs stagger_max >= 1");
     if (o.asm_grid_max < 0) return fail(nullptr, GD_ERR_ARG, "asm_grid_max must be >= 0");
     if (o.krylov_row_cache < 0 || o.krylov_row_cache > 2)
         return fail(nullptr, GD_ERR_ARG, "krylov_row_cache must be 0, 1 or 2");
     if (o.icnn_mma < GD_ICNN_AUTO || o.icnn_mma > GD_ICNN_BF16X3) return fail(nullptr, GD_ERR_ARG, "icnn_mma");
+    if (o.krylov != GD_BICGSTAB && o.krylov != GD_GMRES) return fail(nullptr, GD_ERR_ARG, "krylov");
+    if (o.gmres_m < 1 || o.gmres_m > gd::gmres_max_m()) return fail(nullptr, GD_ERR_ARG, "gmres_m must be in [1, 64]");
     if (n_spec > 1 && o.precision == GD_MIXED && (o.icnn_mma == GD_ICNN_BF16 || o.icnn_mma == GD_ICNN_BF16X3))
         return fail(nullptr, GD_ERR_ARG, "the tensor-core networks need a single specimen (one weight set per launch)");
 
@@ -1662,6 +1764,7 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
     const size_t nq_tot = (size_t)(NE * nen);
     double **vec_d[] = {&H.dofs, &H.dofs_prev, &H.w_dofs, &H.w_trial, &H.R, &H.R_trial, &H.diag};
     for (double **p : vec_d) GD_CREATE_CUDA(dalloc(p, (size_t)n_dofs));
+    if (o.precision == GD_MIXED) GD_CREATE_CUDA(dalloc(&H.Rabs, (size_t)n_dofs));
     GD_CREATE_CUDA(dalloc(&H.dofs_pp, (size_t)n_dofs));
     for (double *&p : H.kv) GD_CREATE_CUDA(dalloc(&p, (size_t)n_dofs));
     GD_CREATE_CUDA(dalloc(&H.kappa, nq_tot));
@@ -1999,6 +2102,31 @@ gd_status gd_autotune(gd_handle *h, gd_tune_report *rep)
     }
     H.krylov_up = upick;
     r.krylov_up = upick ? upick : 1;
+    // lanes per node of the 3D FP32 solve (32: a warp per node; 8 or 4: four or
+    // eight nodes per warp, more lanes busy in the vector phases)
+    const int lanes[3] = {32, 8, 4};
+    double lbest = 1e300;
+    int lpick = H.krylov_lanes;
+    for (double &v : r.krylov_us_lanes) v = -1.0;
+    for (int li = 0; li < 3 && st == GD_OK && H.ndof == 4 && fp32; ++li) {
+        H.krylov_lanes = lanes[li];
+        double tmin = 1e300;
+        for (int rep_i = 0; rep_i < 2; ++rep_i) {
+            int kit = 0;
+            double rel = 0.0;
+            const double k0 = H.krylov_ms;
+            st = krylov(H, H.vals, H.kv[9], H.kv[8], kit, rel, 1e-300, fp32, 1e300);
+            if (st) break;
+            if (rep_i > 0 && kit > 0) tmin = std::min(tmin, (H.krylov_ms - k0) * 1e3 / kit);
+        }
+        r.krylov_us_lanes[li] = st ? -1.0 : tmin;
+        if (!st && tmin < lbest) {
+            lbest = tmin;
+            lpick = lanes[li];
+        }
+    }
+    H.krylov_lanes = lpick;
+    r.krylov_lanes = lpick ? lpick : 32;
     std::swap(H.vals, H.vals_trial);
     H.opt.krylov_max = keep_max;
     if (st) return st;
@@ -2150,6 +2278,9 @@ gd_status gd_backward(gd_handle *h, const double *dL_dreaction, double *dL_dthet
     if (!dL_dreaction || !dL_dtheta) return fail(&H, GD_ERR_ARG, "null argument");
     if (H.opt.precision != GD_FP64) return fail(&H, GD_ERR_STATE, "gd_backward needs GD_FP64 precision");
     if (H.n_spec > 1) return fail(&H, GD_ERR_STATE, "gd_backward takes a single-specimen handle");
+    if (H.opt.scheme == GD_STAGGERED)
+        return fail(&H, GD_ERR_STATE, "gd_backward differentiates the monolithic step equations, which the "
+                                      "staggered scheme's lagged steps do not solve");
     if (!H.rec_on || H.rec_load.empty() || H.ckpts.empty())
         return fail(&H, GD_ERR_STATE, "no recorded load path: run gd_newton_step / gd_run_load_path first");
     const int M = (int)H.rec_load.size();

@@ -651,6 +651,7 @@ __device__ __forceinline__ void row_mode(const Args &A, const MatF &m, const flo
                     // r_u,a = P n_a J w (Sec. 3.1f)
                     Rr += Jw * (R0[Q_P + i * 3] * Va[V_N] + R0[Q_P + i * 3 + 1] * Va[V_N + 1] +
                                 R0[Q_P + i * 3 + 2] * Va[V_N + 2]);
+                    if (!A.tangent) continue;      // residual-only pass: no tangent rows
                     // d2 psi_e/dF2 contracted with grad N_a, grad N_b:
                     //   sum_mn psi_mn G^m_a G^n_b + psi_1 D2(I1) + psi_2 D2(I2) + psi_3 D2(J),
                     // G^1 = 2 F n, G^2 = 2 (I1 F n - F F^T F n), G^3 = J F^-T n,
@@ -693,6 +694,7 @@ __device__ __forceinline__ void row_mode(const Args &A, const MatF &m, const flo
                     // R_phi,a = (Y . grad N_a - Y N_a) J w, Y vec = c_d C^-1 grad phi, -Y = beta_d (phi - kappa)
                     const float Na = Va[V_NN];
                     Rr += Jw * (cd * Va[V_MN] + R0[Q_PEN] * Na);
+                    if (!A.tangent) continue;
                     const float bck = R0[Q_BCK], pp = R0[Q_PP];
 #pragma unroll
                     for (int bN = 0; bN < NEN; ++bN) {
@@ -712,6 +714,7 @@ __device__ __forceinline__ void row_mode(const Args &A, const MatF &m, const flo
             const int32_t na = __ldg(A.conn + e * NEN + a);
             const int64_t rdof = (int64_t)na * NDOF + i;
             if (A.R) atomicAdd(A.R + rdof, (double)Rr);
+            if (A.Rabs) atomicAdd(A.Rabs + rdof, (double)fabsf(Rr));
             if (A.tangent) {
                 const int32_t rb = __ldg(A.rowptr + (int64_t)na * NDOF);
                 const int32_t rowlen = __ldg(A.rowptr + (int64_t)na * NDOF + 1) - rb;

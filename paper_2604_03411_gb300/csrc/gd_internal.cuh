@@ -47,6 +47,7 @@ struct AsmArgs {
     const double *dofs;
     const double *kappa_n;
     double *R;               // may be null
+    double *Rabs;            // may be null (mixed kernels): sum over elements of |element residual row|
     double *vals;            // FP64 values (may be null)
     float *vals32;           // FP32 values (mixed mode, may be null)
     double *kappa_new;       // may be null
@@ -233,6 +234,7 @@ struct Handle {
     // work arrays
     double *w_dofs = nullptr, *w_trial = nullptr;
     double *R = nullptr, *R_trial = nullptr;
+    double *Rabs = nullptr;                              // GD_MIXED: sum of |element residual rows| (noise scale)
     double *vals = nullptr, *vals_trial = nullptr;       // FP64 (or FP32 bit storage in mixed mode)
     double *kappa_trial = nullptr, *kappa_trial2 = nullptr;
     int8_t *loading = nullptr, *loading2 = nullptr;
@@ -255,6 +257,10 @@ struct Handle {
     std::vector<double> noise_ratio;
     int noise_age = 0;
     int krylov_up = 0;                                   // 0: the precision's default
+    int krylov_lanes = 0;                                // 3D FP32 solves: lanes per node (0: 32)
+    double *gm_ws = nullptr;                             // GMRES work space (allocated on first use)
+    double *gm_binv = nullptr;                           // its node-block inverses (FP64)
+    long long gmres_iterations = 0;                      // GMRES iterations run by this handle
     int krylov_lmax = 0;                                 // longest CSR row
     CoarseSpace coarse;                                  // two-level preconditioner (nc = 0: off)
     // tensor-core networks of the mixed element kernel (icnn_mma): mode and weight blob
@@ -392,6 +398,7 @@ struct KrylovCtx {
     const CoarseSpace *coarse = nullptr;   // two-level preconditioner (single systems; null: Jacobi only)
     bool coarse_refresh = true;            // recompute P^T A P and its inverse before the solve
     int row_cache = 0;                     // gd_options.krylov_row_cache: 0 automatic, 1 column lists only, 2 none
+    int lanes = 0;                         // lanes per node of the 3D FP32-vector solve: 4, 8 or 32 (0: 32)
 };
 cudaError_t krylov_solve_batch(const KrylovCtx &c, const BatchKrylov &L, const void *vals, bool fp32_vals,
                                const double *b, double *x, int max_it, bool fp32_vectors);
@@ -402,5 +409,15 @@ int krylov_blocks(int ndof, bool fp32_vals, int num_sms, int cap = 2);
 cudaError_t krylov_solve(const KrylovCtx &c, const void *vals, bool fp32_vals, const double *b, double *x,
                          double rtol, int max_it, bool fp32_vectors = false);
 cudaError_t narrow_to_float(const double *in, float *out, int64_t n, cudaStream_t s);
+// node-block inverses [n_nodes][ndof][ndof] of the eliminated matrix (identity on prescribed dofs)
+cudaError_t launch_block_inverse(int ndof, int64_t n_nodes, const int32_t *rowptr, const int32_t *colidx,
+                                 const void *vals, bool fp32_vals, const uint8_t *fixed, double *binv, int num_sms,
+                                 cudaStream_t s);
+
+// restarted, right-preconditioned GMRES(m) (gd_gmres.cu)
+cudaError_t gmres_solve(const SolverCtx &c, const double *binv, const double *b, double *x, double rtol, int m,
+                        int max_it, double *ws, int &iters, double &rel, bool &converged);
+size_t gmres_workspace_doubles(int64_t n, int m, int nb);
+int gmres_max_m();
 
 }  // namespace gd

@@ -1275,10 +1275,10 @@ __global__ void block_inverse_kernel(int64_t n_nodes, const int32_t *rowptr, con
     }
 }
 
-template <int NDOF, class V, class T>
+// G: lanes per node of the FP32-vector kernels (FP64 vectors use one lane per row)
+template <int NDOF, class V, class T, int G = (NDOF == 3 ? 8 : 32)>
 cudaError_t solve_t(const KrylovCtx &c, const V *vals, const double *b, double *x, double rtol, int max_it)
 {
-    constexpr int G = NDOF == 3 ? 8 : 32;
     T *binv = (T *)c.binv;
     block_inverse_kernel<NDOF, V, T><<<c.num_sms * 4, 256, 0, c.stream>>>(c.n_nodes, c.rowptr, c.colidx, vals,
                                                                           c.fixed, binv);
@@ -1453,12 +1453,19 @@ template <int NDOF, class V, class T>
 int coop_per_sm()
 {
     constexpr int G = NDOF == 3 ? 8 : 32;
-    const void *fns[7] = {(const void *)bicgstab3_kernel<NDOF, G, 1, V, T>, (const void *)bicgstab3_kernel<NDOF, G, 2, V, T>,
+    constexpr int G2 = (NDOF == 4 && std::is_same<T, float>::value) ? 8 : G;   // the other lane counts
+    constexpr int G3 = (NDOF == 4 && std::is_same<T, float>::value) ? 4 : G;   // of the 3D FP32 solve
+    const void *fns[13] = {(const void *)bicgstab3_kernel<NDOF, G, 1, V, T>, (const void *)bicgstab3_kernel<NDOF, G, 2, V, T>,
                           (const void *)bicgstab3_kernel<NDOF, G, 4, V, T>,
                           (const void *)bicgstab3_kernel<NDOF, G, 1, V, T, true>,
                           (const void *)bicgstab3_batch_kernel<NDOF, G, 1, V, T>,
                           (const void *)bicgstab3_batch_kernel<NDOF, G, 2, V, T>,
-                          (const void *)bicgstab3_batch_kernel<NDOF, G, 4, V, T>};
+                          (const void *)bicgstab3_batch_kernel<NDOF, G, 4, V, T>,
+                          (const void *)bicgstab3_kernel<NDOF, G2, 1, V, T>, (const void *)bicgstab3_kernel<NDOF, G2, 2, V, T>,
+                          (const void *)bicgstab3_kernel<NDOF, G2, 4, V, T>,
+                          (const void *)bicgstab3_kernel<NDOF, G2, 1, V, T, true>,
+                          (const void *)bicgstab3_kernel<NDOF, G3, 1, V, T>,
+                          (const void *)bicgstab3_kernel<NDOF, G3, 1, V, T, true>};
     int best = 1 << 30;
     for (const void *f : fns) {
         int per_sm = 0;
@@ -1494,8 +1501,10 @@ cudaError_t krylov_solve(const KrylovCtx &c, const void *vals, bool fp32_vals, c
 {
     if (fp32_vectors) {
         if (!fp32_vals) return cudaErrorInvalidValue;
-        return c.ndof == 3 ? solve_t<3, float, float>(c, (const float *)vals, b, x, rtol, max_it)
-                           : solve_t<4, float, float>(c, (const float *)vals, b, x, rtol, max_it);
+        if (c.ndof == 3) return solve_t<3, float, float>(c, (const float *)vals, b, x, rtol, max_it);
+        if (c.lanes == 4) return solve_t<4, float, float, 4>(c, (const float *)vals, b, x, rtol, max_it);
+        if (c.lanes == 8) return solve_t<4, float, float, 8>(c, (const float *)vals, b, x, rtol, max_it);
+        return solve_t<4, float, float>(c, (const float *)vals, b, x, rtol, max_it);
     }
     if (c.ndof == 3)
         return fp32_vals ? solve_t<3, float, double>(c, (const float *)vals, b, x, rtol, max_it)
@@ -1517,6 +1526,25 @@ cudaError_t krylov_solve_batch(const KrylovCtx &c, const BatchKrylov &L, const v
                          : solve_batch_t<3, double, double>(c, L, (const double *)vals, b, x, max_it);
     return fp32_vals ? solve_batch_t<4, float, double>(c, L, (const float *)vals, b, x, max_it)
                      : solve_batch_t<4, double, double>(c, L, (const double *)vals, b, x, max_it);
+}
+
+cudaError_t launch_block_inverse(int ndof, int64_t n_nodes, const int32_t *rowptr, const int32_t *colidx,
+                                 const void *vals, bool fp32_vals, const uint8_t *fixed, double *binv, int num_sms,
+                                 cudaStream_t s)
+{
+    const int grid = num_sms * 4;
+    if (ndof == 3) {
+        if (fp32_vals)
+            block_inverse_kernel<3, float, double><<<grid, 256, 0, s>>>(n_nodes, rowptr, colidx, (const float *)vals, fixed, binv);
+        else
+            block_inverse_kernel<3, double, double><<<grid, 256, 0, s>>>(n_nodes, rowptr, colidx, (const double *)vals, fixed, binv);
+    } else {
+        if (fp32_vals)
+            block_inverse_kernel<4, float, double><<<grid, 256, 0, s>>>(n_nodes, rowptr, colidx, (const float *)vals, fixed, binv);
+        else
+            block_inverse_kernel<4, double, double><<<grid, 256, 0, s>>>(n_nodes, rowptr, colidx, (const double *)vals, fixed, binv);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t narrow_to_float(const double *in, float *out, int64_t n, cudaStream_t s)

@@ -6,12 +6,15 @@ oracle's LU path in FP64 (1e-9) and in mixed precision (1e-4).
 
 Sec. 5.2 study: the 10 x 10 x 1 plate with the closed-form Neo-Hookean energy and the
 Ostwald loading function and the constants the paper lists (read as nondimensional),
-pulled to a large stretch, in all four combinations {local, non-local} x {staggered,
-monolithic}.  The deformation is uniform, so phi = kappa and all four reach the
-homogeneous state: each reaction curve equals the 3D uniaxial material point's P11 x
-area (FP64, 1e-8).  On a graded (non-uniform) mesh of the same plate the four
-curves are printed beside each other (the paper's mesh-dependence comparison; its
-figures are not available, so that part is reported, not pinned)."""
+pulled to a large stretch, in all four combinations {local, non-local} x {staggered
+(Sec. 3.2: history advanced after the nodal solve), monolithic}, each run until the
+largest damage reaches 0.995 or a step fails, as in the study.  On the uniform mesh
+and on a graded one every completed curve matches the oracle's path of the same
+scheme (FP64, 1e-8); on the uniform mesh the monolithic curves also equal the 3D
+uniaxial material point's P11 x area, and the non-local staggered run stays far
+below the monolithic damage (the paper's finding for a stiff penalty beta_d).  The
+curves are printed side by side (the paper's figures are not available, so the
+comparison between schemes is reported, not pinned)."""
 import numpy as np
 import pytest
 
@@ -59,43 +62,68 @@ def test_local_model_notched_plate_vs_oracle(env, precision):
 
 
 def run(B, prob, scheme):
-    o = tight(B, scheme=scheme, stagger_max=2000) if scheme == B.GD_STAGGERED else tight(B)
-    h = B.gd_create(prob, o)
-    reac, rep = B.gd_run_load_path(h)
-    assert rep.steps_done == prob.load.size
-    return reac, B.gd_get_fields(h, damage=True)
+    """Steps of the path until the largest damage reaches 0.995 or a step fails to
+    converge (the study's stopping rule): (reactions, max damage, failed, handle)."""
+    h = B.gd_create(prob, tight(B, scheme=scheme))
+    reac, dmax, failed = [], [], False
+    for _ in range(prob.load.size):
+        try:
+            rep = B.gd_newton_step(h)
+        except B.GDError as e:
+            if e.status != B.GD_ERR_NOT_CONVERGED:
+                raise
+            failed = True
+            break
+        reac.append(rep.reaction)
+        dmax.append(rep.max_damage)
+        if rep.max_damage >= 0.995:
+            break
+    return np.array(reac), np.array(dmax), failed, h
+
+
+def graded_plate(gamma):
+    prob = I.uniform_plate_e3(n=4, n_steps=30, u_max=25.0, gamma_d=gamma)
+    x = prob.mesh.coords
+    prob.mesh.coords = x + np.stack([0.8 * np.sin(np.pi * x[:, 0] / 10.0) * np.sin(np.pi * x[:, 1] / 10.0),
+                                     0.6 * np.sin(np.pi * x[:, 1] / 10.0) * np.sin(2 * np.pi * x[:, 0] / 10.0),
+                                     np.zeros(len(x))], axis=1)
+    return prob
 
 
 def test_uniform_deformation_four_schemes(env):
     torch, B, oracle = env
-    combos = {}
-    for gamma in (1.0, 0.0):
-        prob = I.uniform_plate_e3(n=4, n_steps=30, u_max=25.0, gamma_d=gamma)
-        for scheme in (B.GD_MONOLITHIC, B.GD_STAGGERED):
-            combos[(gamma, scheme)] = run(B, prob, scheme)
+    schemes = ((B.GD_MONOLITHIC, "monolithic"), (B.GD_STAGGERED, "staggered"))
+    out = {}
+    for mesh_kind in ("uniform", "graded"):
+        for gamma in (1.0, 0.0):
+            prob = (I.uniform_plate_e3(n=4, n_steps=30, u_max=25.0, gamma_d=gamma) if mesh_kind == "uniform"
+                    else graded_plate(gamma))
+            m = oracle.Model.from_problem(prob)
+            for scheme, name in schemes:
+                reac, dmax, failed, h = run(B, prob, scheme)
+                k = reac.size
+                assert k >= 5, (mesh_kind, gamma, name, "the first steps are elastic or mildly damaged")
+                ref = oracle.run_load_path(m, prob.mesh, prob.load[:k], rtol=1e-12, atol=1e-14, scheme=name)
+                dofs, kappa = B.gd_get_fields(h)
+                key = (mesh_kind, gamma, name)
+                assert rel_err(reac, ref["reaction"]) < 1e-8, (key, rel_err(reac, ref["reaction"]))
+                assert rel_err(np.ravel(kappa), np.ravel(ref["kappa"])) < 1e-8, key
+                out[key] = (reac, dmax, failed)
+    # uniform mesh, monolithic: the homogeneous state of the material point
     prob = I.uniform_plate_e3(n=4, n_steps=30, u_max=25.0)
     P11, lt, kap = oracle.material_point_uniaxial_3d(oracle.Model.from_problem(prob), 1.0 + prob.load)
     area = 10.0 * 1.0
-    d_end = 1.0 - np.exp(-prob.mat.eta_d * max(kap[-1] - prob.mat.kappa_d, 0.0))
-    assert d_end > 0.3, "the path should damage the plate"
-    for key, (reac, (dofs, kappa, dmg)) in combos.items():
-        assert rel_err(reac, P11 * area) < 1e-8, (key, rel_err(reac, P11 * area))
-        assert np.abs(kappa - kap[-1]).max() <= 1e-8 * max(1.0, kap[-1]), key
-    # non-uniform mesh: the four schemes side by side
-    graded = {}
     for gamma in (1.0, 0.0):
-        prob = I.uniform_plate_e3(n=4, n_steps=30, u_max=25.0, gamma_d=gamma)
-        x = prob.mesh.coords
-        prob.mesh.coords = x + np.stack([0.8 * np.sin(np.pi * x[:, 0] / 10.0) * np.sin(np.pi * x[:, 1] / 10.0),
-                                         0.6 * np.sin(np.pi * x[:, 1] / 10.0) * np.sin(2 * np.pi * x[:, 0] / 10.0),
-                                         np.zeros(len(x))], axis=1)
-        for scheme in (B.GD_MONOLITHIC, B.GD_STAGGERED):
-            graded[(gamma, scheme)] = run(B, prob, scheme)[0]
-    print("\nnon-uniform plate, reaction at 25%/50%/75%/100% of the path:")
-    for (gamma, scheme), reac in graded.items():
-        name = ("non-local" if gamma else "local") + (" staggered" if scheme == B.GD_STAGGERED else " monolithic")
-        q = [reac[int(f * (reac.size - 1))] for f in (0.25, 0.5, 0.75, 1.0)]
-        print(f"  {name:22s} " + "  ".join(f"{v:.6e}" for v in q))
-    # the staggered and monolithic schemes solve the same equations at convergence
-    for gamma in (1.0, 0.0):
-        assert rel_err(graded[(gamma, B.GD_STAGGERED)], graded[(gamma, B.GD_MONOLITHIC)]) < 1e-7
+        reac, dmax, failed = out[("uniform", gamma, "monolithic")]
+        assert rel_err(reac, P11[:reac.size] * area) < 1e-8, (gamma, rel_err(reac, P11[:reac.size] * area))
+    d_mono = out[("uniform", 1.0, "monolithic")][1]
+    assert d_mono[-1] > 0.3, "the path should damage the plate"
+    # non-local staggered: the penalty beta_d = 1000 holds kappa near the lagged phi
+    d_stag = out[("uniform", 1.0, "staggered")][1]
+    n = min(d_mono.size, d_stag.size)
+    assert d_stag[n - 1] < 0.5 * d_mono[n - 1], (d_stag[n - 1], d_mono[n - 1])
+    print("\nSec. 5.2 plate: steps done, final reaction, final max damage, stop reason")
+    for (mesh_kind, gamma, name), (reac, dmax, failed) in out.items():
+        label = f"{mesh_kind:8s} {'non-local' if gamma else 'local':9s} {name:10s}"
+        why = "no convergence" if failed else ("d = 0.995" if dmax[-1] >= 0.995 else "end of path")
+        print(f"  {label} {reac.size:3d}  {reac[-1]: .6e}  {dmax[-1]:.4f}  {why}")

@@ -215,7 +215,7 @@ def test_autotune_keeps_results(env):
 
 
 def test_staggered_scheme_reaches_the_monolithic_solution(env):
-    """GD_STAGGERED (equilibrium at frozen history, then the local update, alternating
+    """GD_STAGGERED_ITERATED (equilibrium at frozen history, then the local update, alternating
     until the residual with the updated history meets the Newton test) solves the
     same equations as the monolithic scheme: same reactions and fields, and the
     oracle's; FP64 and mixed precision."""
@@ -225,7 +225,7 @@ def test_staggered_scheme_reaches_the_monolithic_solution(env):
     rm, _ = B.gd_run_load_path(B.gd_create(prob, tight(B)))
     # the alternation converges linearly (measured: 100 alternations reach 7.5e-12 of a
     # 9.4e-6 residual in a damaging step), so the staggered runs use a 1e-10 test
-    hs = B.gd_create(prob, tight(B, newton_rtol=1e-10, scheme=B.GD_STAGGERED, stagger_max=1000))
+    hs = B.gd_create(prob, tight(B, newton_rtol=1e-10, scheme=B.GD_STAGGERED_ITERATED, stagger_max=1000))
     rs, rep = B.gd_run_load_path(hs)
     assert rep.steps_done == prob.load.size
     assert rel_err(rs, rm) < 1e-7, (rs, rm)
@@ -235,8 +235,129 @@ def test_staggered_scheme_reaches_the_monolithic_solution(env):
     dofs, kappa = B.gd_get_fields(hs)
     assert rel_err(np.ravel(kappa), np.ravel(ro["kappa"])) < 1e-6
     r32, _ = B.gd_run_load_path(B.gd_create(prob, B.gd_default_options(precision=B.GD_MIXED,
-                                                                        scheme=B.GD_STAGGERED,
+                                                                        scheme=B.GD_STAGGERED_ITERATED,
                                                                         stagger_max=1000)))
     assert rel_err(r32, rm) < 1e-4
     with pytest.raises(B.GDError):
         B.gd_create_batch([prob, prob], tight(B, scheme=B.GD_STAGGERED))
+    with pytest.raises(B.GDError):
+        B.gd_create_batch([prob, prob], tight(B, scheme=B.GD_STAGGERED_ITERATED))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_staggered_scheme_matches_the_oracle(env, dim):
+    """GD_STAGGERED (Sec. 3.2: the nodal solve at the committed history, then one local
+    update per step, no coupled iteration) against the oracle's staggered path, FP64
+    (1e-9) and mixed precision (1e-4).  The lag makes it differ from the monolithic
+    path, with less damage; gd_backward refuses it."""
+    torch, B, oracle = env
+    if dim == 2:
+        prob = I.config2(n_long=40, n_wide=16)
+        prob.load = prob.load[4:22:3]
+    else:
+        prob = I.notched_plate_3d(n_long=16, n_wide=15, n_steps=25)
+        prob.load = prob.load[2:25:3]
+    h = B.gd_create(prob, tight(B, scheme=B.GD_STAGGERED))
+    rs, rep = B.gd_run_load_path(h)
+    assert rep.steps_done == prob.load.size
+    m = oracle.Model.from_problem(prob)
+    ro = oracle.run_load_path(m, prob.mesh, prob.load, rtol=1e-12, atol=1e-14, scheme="staggered")
+    dofs, kappa = B.gd_get_fields(h)
+    assert rel_err(rs, ro["reaction"]) < 1e-9, (rs, ro["reaction"])
+    assert rel_err(np.ravel(kappa), np.ravel(ro["kappa"])) < 1e-9
+    assert rel_err(np.ravel(dofs), np.ravel(ro["dofs"])) < 1e-9
+    assert float(np.max(ro["kappa"])) > prob.mat.kappa_d, "the path should damage the specimen"
+    rm, _ = B.gd_run_load_path(B.gd_create(prob, tight(B)))
+    assert rel_err(rs, rm) > 1e-6, "the staggered update should lag the monolithic one"
+    h32 = B.gd_create(prob, B.gd_default_options(precision=B.GD_MIXED, scheme=B.GD_STAGGERED))
+    r32, _ = B.gd_run_load_path(h32)
+    assert rel_err(r32, ro["reaction"]) < 1e-4
+    with pytest.raises(B.GDError):
+        B.gd_backward(h, np.ones(prob.load.size))
+
+
+def test_gmres_solve_matches_sparse_lu(env):
+    """gd_options.krylov = GD_GMRES: restarted GMRES(gmres_m) with right node-block
+    Jacobi preconditioning on a notched-plate tangent, against SuperLU; and a Newton
+    path with GMRES for every solve against the BiCGStab path."""
+    torch, B, oracle = env
+    import scipy.sparse.linalg as spla
+    from gpu_common import gpu_assemble
+    prob = I.config2(n_long=60, n_wide=24)
+    h = B.gd_create(prob, B.gd_default_options(krylov=B.GD_GMRES, gmres_m=40, krylov_rtol=1e-12,
+                                               krylov_max=20000))
+    B.gd_newton_step(h)
+    dofs, kappa = B.gd_get_fields(h)
+    R, K, _, _ = gpu_assemble(B, torch, h, dofs, kappa)
+    n = R.size
+    bidx = prob.mesh.bc_node.astype(np.int64) * 3 + prob.mesh.bc_comp
+    free = np.ones(n, bool)
+    free[bidx] = False
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal(n)
+    b[~free] = 0.0
+    vals = torch.tensor(K.data, dtype=torch.float64, device="cuda")
+    bt = torch.tensor(b, device="cuda")
+    xt = torch.zeros_like(bt)
+    it, rel = B.gd_solve(h, bt, xt, vals)
+    x = xt.cpu().numpy()
+    Kff = K[free][:, free].tocsc()
+    xr = spla.spsolve(Kff, b[free])
+    assert 0 < it and rel <= 1e-12
+    assert np.all(x[~free] == 0.0)
+    # GMRES reports the true residual of the returned x
+    true_rel = np.linalg.norm(Kff @ x[free] - b[free]) / np.linalg.norm(b[free])
+    assert abs(true_rel - rel) <= 1e-3 * rel + 1e-15
+    assert rel_err(x[free], xr) < 1e-6
+    # a short path, every Newton system by GMRES
+    p2 = I.config2(n_long=40, n_wide=16)
+    p2.load = p2.load[:4]
+    rb, _ = B.gd_run_load_path(B.gd_create(p2, tight(B)))
+    rg, _ = B.gd_run_load_path(B.gd_create(p2, tight(B, krylov=B.GD_GMRES)))
+    assert rel_err(rg, rb) < 1e-9
+
+
+def test_gmres_takes_over_when_bicgstab_breaks_down(env):
+    """A skew-symmetric system S x = b on a mesh's pattern (zero diagonal node blocks, so
+    the block-Jacobi preconditioner is the identity): BiCGStab's first step divides by
+    r0^T S r0, which is zero up to rounding, so it cannot solve it; the FP64 solve then
+    runs GMRES(m), which minimises the residual and solves it (m is above the 38 free
+    dofs: full GMRES)."""
+    torch, B, oracle = env
+    import scipy.sparse as sp
+    mesh = I.uniaxial_bc_2d(I.structured_q4(4, 2))
+    prob = I.config1()
+    prob.mesh = mesh
+    prob.load = prob.load[:1]
+    h = B.gd_create(prob, B.gd_default_options(krylov_rtol=1e-12, krylov_max=2000, coarse=0, gmres_m=50))
+    rowptr, colidx = B.gd_csr_pattern(h)
+    n = rowptr.size - 1
+    rng = np.random.default_rng(7)
+    A = sp.csr_matrix((rng.standard_normal(colidx.size), colidx, rowptr), shape=(n, n))
+    A.sort_indices()
+    S = (A - A.T).tocsr()
+    node = np.arange(n) // 3
+    S = S.tocoo()
+    keep = node[S.row] != node[S.col]                      # zero diagonal node blocks
+    S = sp.csr_matrix((S.data * keep, (S.row, S.col)), shape=(n, n))
+    # values in the handle's pattern order
+    vals = np.asarray(S[np.repeat(np.arange(n), np.diff(rowptr)), colidx]).ravel()
+    bidx = mesh.bc_node.astype(np.int64) * 3 + mesh.bc_comp
+    free = np.ones(n, bool)
+    free[bidx] = False
+    assert free.sum() == 38
+    Sff = S[free][:, free].toarray()
+    assert np.abs(Sff + Sff.T).max() == 0.0 and np.linalg.cond(Sff) < 1e8
+    b = rng.standard_normal(n)
+    b[~free] = 0.0
+    x_ref = np.linalg.solve(Sff, b[free])
+    vt = torch.tensor(vals, device="cuda")
+    bt = torch.tensor(b, device="cuda")
+    for krylov in (B.GD_BICGSTAB, B.GD_GMRES):
+        hk = B.gd_create(prob, B.gd_default_options(krylov=krylov, krylov_rtol=1e-12, krylov_max=2000, coarse=0,
+                                                    gmres_m=50))
+        xt = torch.zeros_like(bt)
+        it, rel = B.gd_solve(hk, bt, xt, vt)
+        x = xt.cpu().numpy()
+        assert rel <= 1e-12, (krylov, rel)
+        assert rel_err(x[free], x_ref) < 1e-8, krylov

@@ -71,7 +71,9 @@ def test_notched_plate_3d_step_and_mesh_convergence(env):
             _, _, dmg = B.gd_get_fields(h, damage=True)
             peaks.append(float(np.max(reac)))
             rows.append((p.mesh.n_elems, steps, peaks[-1], float(reac[-1]), float(dmg.max()), float(np.median(dmg))))
-        assert abs(peaks[2] - peaks[1]) <= abs(peaks[1] - peaks[0]) + 1e-12 * abs(peaks[0]), (n_long, peaks)
+        # where the peak comes before the damage spreads, the three step sizes give the
+        # same peak to the Newton tolerance (1e-10 relative): allow that much
+        assert abs(peaks[2] - peaks[1]) <= abs(peaks[1] - peaks[0]) + 1e-10 * abs(peaks[0]), (n_long, peaks)
     print("\n elements steps  peak_reaction  final_reaction  d_max   d_median")
     for r in rows:
         print(f" {r[0]:8d} {r[1]:5d}  {r[2]:.6e}  {r[3]:.6e}  {r[4]:.4f}  {r[5]:.4f}")

@@ -41,12 +41,16 @@ MUTATIONS = [
     ("adjoint: unloading history sensitivity", "if (dk_dkp) dk_dkp[q] = inf.loading ? 0.0 : 1.0;",
      "if (dk_dkp) dk_dkp[q] = 0.0;"),
     ("adjoint: weight derivative of the yield normalisation", "m->c_ys = hinv(Np);", "m->c_ys = hc(1.0 / Np.v);"),
+    ("staggered: the nodal solve updates the history", "    if (m->frozen) {\n        memset(inf, 0, sizeof(*inf));",
+     "    if (0) {\n        memset(inf, 0, sizeof(*inf));"),
+    ("staggered: frozen tangent keeps the implicit-function term", "    if (inf->loading) {\n        double drk",
+     "    if (inf->loading || m->frozen) {\n        double drk"),
 ]
 
 # the pins that run against each mutant (the fast ones)
 PINS = ("stress_free or dd1 or closed_form_chain or objectivity or neo_hooke or small_strain or "
         "residual_is_energy or tangent_is or homogeneous_patch or mullins or kkt or single_hex8 or "
-        "yield_function or degradation or local_equals or patch_test or nonlocal_field or adjoint")
+        "yield_function or degradation or local_equals or patch_test or nonlocal_field or adjoint or staggered")
 
 
 @pytest.mark.parametrize("name,orig,mut", MUTATIONS, ids=[m[0] for m in MUTATIONS])

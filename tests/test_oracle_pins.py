@@ -579,3 +579,59 @@ def test_adjoint_matches_central_differences():
         tm[i] -= h
         fd = (loss(tp) - loss(tm)) / (2 * h)
         assert abs(g[i] - fd) <= 2e-8 * scale, (i, g[i], fd)
+
+
+# ---------------------------------------------------------------------------
+# staggered scheme (Sec. 3.2): the history advanced apart from the nodal solve
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dim", [2, 3])
+def test_staggered_frozen_element(dim):
+    """The nodal solve of the staggered scheme holds kappa: with the history set to
+    the monolithic update's kappa_{n+1}, the frozen residual is the monolithic one
+    (the same Psi at the same kappa), the history comes back unchanged, and the
+    frozen tangent is the central-difference Jacobian of the frozen residual, which
+    lacks the implicit-function term of the monolithic tangent."""
+    m, _, _ = model_for(I.ENERGY_ICNN_RAW, seed=13, w=16, dim=dim)
+    Xe, de, kn, nd = _elem_setup(dim, 21)
+    Re, Ke, k1, qi = m.element(Xe, de, kn)
+    assert qi[:, 5].sum() > 0, "the state should have loading points"
+    m.m.frozen = 1
+    try:
+        Rf, Kf, kf, _ = m.element(Xe, de, k1)
+        assert np.array_equal(kf, k1)
+        assert np.abs(Rf - Re).max() <= 1e-12 * np.abs(Re).max()
+        h = 1e-6
+        Kfd = np.zeros_like(Kf)
+        for A in range(nd):
+            dp = de.copy(); dp[A] += h
+            dm = de.copy(); dm[A] -= h
+            Kfd[:, A] = (m.element(Xe, dp, k1, tangent=False)[0] - m.element(Xe, dm, k1, tangent=False)[0]) / (2 * h)
+        assert np.abs(Kfd - Kf).max() <= 1e-7 * np.abs(Kf).max()
+    finally:
+        m.m.frozen = 0
+    assert np.abs(Kf - Ke).max() > 1e-3 * np.abs(Ke).max(), "the monolithic tangent carries dkappa/dz"
+
+
+def test_staggered_path_lag_is_first_order():
+    """Sec. 3.2: the staggered update uses fields that were in equilibrium with the
+    previous history, a lag of one load step.  Its reaction curve therefore departs
+    from the monolithic one by an error of first order in the step: halving the step
+    halves the difference at the end of the path; the lag leaves less damage (the
+    penalty holds kappa near the lagged phi); and before any point loads (the first
+    quarter of this path) the two schemes agree."""
+    mesh = I.uniaxial_bc_2d(I.structured_q4(3, 2))
+    psi, yld = I.icnn_pair(11, 8, 8)
+    mat = I.Material(beta_d=1.0, c_d=0.1 ** 2)
+    m = oracle.Model(2, mat, psi.params, 8, yld.params, 8)
+    diffs = []
+    for n in (20, 40, 80):
+        load = np.linspace(0.0, 0.6, n + 1)[1:]
+        mo = oracle.run_load_path(m, mesh, load, rtol=1e-12, atol=1e-14)
+        st = oracle.run_load_path(m, mesh, load, rtol=1e-12, atol=1e-14, scheme="staggered")
+        q = n // 4
+        assert np.abs(st["reaction"][:q] - mo["reaction"][:q]).max() <= 1e-10 * np.abs(mo["reaction"]).max()
+        assert st["kappa"].max() < mo["kappa"].max()
+        diffs.append(st["reaction"][-1] - mo["reaction"][-1])
+    assert abs(diffs[-1]) > 1e-3 * abs(mo["reaction"][-1]), "the lag should be visible"
+    for a, b in zip(diffs, diffs[1:]):
+        assert 1.8 < a / b < 2.2, diffs
