@@ -210,6 +210,11 @@ typedef struct gd_newton_report {
     int64_t yield_evals;       /* yield-network evaluations of the local solves (all launches) */
     int64_t kernel_launches;   /* device kernels this library launched for the step     */
     int32_t krylov_fp32_iterations; /* iterations of FP32 inner solves (the rest ran in FP64) */
+    int32_t noise_passes;      /* GD_MIXED: FP64 reference passes run to measure the noise floor */
+    double noise;              /* GD_MIXED: rounding-noise level of ||R_free|| at the last Newton
+                                  test (the test does not go below twice it); 0 in GD_FP64      */
+    double noise_ms;           /* device time of the FP64 reference passes (in the step time, not
+                                  in assembly_ms)                                              */
 } gd_newton_report;
 
 typedef struct gd_path_report {
@@ -422,7 +427,12 @@ gd_status gd_run_load_path(gd_handle *h, double *reaction, gd_path_report *rep);
  * checkpoint_every steps and recomputation in between).
  *   dL_dreaction [n_steps] host; dL_dtheta [n_psi + n_yield] host out.
  * The adjoint differentiates the monolithic step equations: GD_ERR_STATE for a
- * handle with scheme GD_STAGGERED (whose lagged steps solve other equations). */
+ * handle with scheme GD_STAGGERED (whose lagged steps solve other equations).
+ * GD_MIXED: the segments are recomputed in mixed precision as the forward ran; the
+ * adjoint systems use the FP64 element kernel's tangent at those states and FP64
+ * solves, so the gradient is the FP64 model's at the mixed path (its error against
+ * the FP64 path's gradient follows the mixed states' error; one extra FP64 value
+ * array of nnz entries is allocated on the first call). */
 gd_status gd_backward(gd_handle *h, const double *dL_dreaction, double *dL_dtheta);
 
 /* Copies the committed fields to host: dofs [n_nodes*ndof], kappa [n_elems*nq]

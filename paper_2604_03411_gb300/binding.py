@@ -21,10 +21,13 @@ GD_OK = 0
 STATUS = {0: "GD_OK", 1: "GD_ERR_ARG", 2: "GD_ERR_MESH", 3: "GD_ERR_CUDA", 4: "GD_ERR_OOM",
           5: "GD_ERR_NOT_CONVERGED", 6: "GD_ERR_NAN", 7: "GD_ERR_KRYLOV", 8: "GD_ERR_LOCAL_SOLVE",
           9: "GD_ERR_TIMEOUT", 10: "GD_ERR_STATE"}
+globals().update({name: code for code, name in STATUS.items()})
+GD_ENERGY_ICNN_RAW, GD_ENERGY_ICNN_ISO, GD_ENERGY_NEO_HOOKE = 0, 1, 2
 GD_FP64, GD_MIXED = 0, 1
 GD_ASM_RESIDUAL, GD_ASM_TANGENT = 0, 1
 GD_INNER_AUTO, GD_INNER_FP64, GD_INNER_REFINED = 0, 1, 2
 GD_MONOLITHIC, GD_STAGGERED, GD_STAGGERED_ITERATED = 0, 1, 2
+GD_BICGSTAB, GD_GMRES = 0, 1
 GD_ICNN_AUTO, GD_ICNN_CUDA_CORES, GD_ICNN_BF16, GD_ICNN_BF16X3 = 0, 1, 2, 3
 GD_NOALLOC_MAX_DOFS = 131072
 
@@ -73,7 +76,8 @@ class GdNewtonReport(ctypes.Structure):
                 ("residual0", ctypes.c_double), ("residual", ctypes.c_double), ("reaction", ctypes.c_double),
                 ("max_damage", ctypes.c_double), ("assembly_ms", ctypes.c_double), ("krylov_ms", ctypes.c_double),
                 ("yield_evals", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("krylov_fp32_iterations", ctypes.c_int32)]
+                ("krylov_fp32_iterations", ctypes.c_int32), ("noise_passes", ctypes.c_int32),
+                ("noise", ctypes.c_double), ("noise_ms", ctypes.c_double)]
 
 
 class GdPathReport(ctypes.Structure):

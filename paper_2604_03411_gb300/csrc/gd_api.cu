@@ -32,9 +32,11 @@ gd_status fail(gd::Handle *H, gd_status st, const std::string &msg)
 #define GD_CUDA(H, call)                                                                                   \
     do {                                                                                                   \
         cudaError_t e_ = (call);                                                                           \
-        if (e_ != cudaSuccess)                                                                             \
+        if (e_ != cudaSuccess) {                                                                           \
+            (void)cudaGetLastError(); /* consume a non-sticky error: it must not fail the next call */     \
             return fail((H), e_ == cudaErrorMemoryAllocation ? GD_ERR_OOM : GD_ERR_CUDA,                   \
                         std::string(#call) + ": " + cudaGetErrorString(e_));                               \
+        }                                                                                                  \
     } while (0)
 
 // counters[3] is set by the tensor-core element kernel when one of its bounded waits
@@ -104,6 +106,7 @@ void free_handle(gd::Handle &H)
     free_ckpts(H);
     dfree(H.perm_T);
     dfree(H.vals_T);
+    dfree(H.vals64);
     for (double *p : H.adj_v) dfree(p);
     dfree(H.kbar);
     dfree(H.kbar2);
@@ -233,6 +236,26 @@ gd_status assemble_pass(gd::Handle &H, const double *dofs, const double *kappa_n
     return GD_OK;
 }
 
+// FP64 residual and tangent of the FP64 element kernel into vals64 (FP64 values in
+// the handle's pattern), whatever the handle's precision: the adjoint of a GD_MIXED path
+gd_status assemble_tangent_fp64(gd::Handle &H, const double *dofs, const double *kappa_n, double *R, double *vals64,
+                                double *kappa_out, int8_t *loading)
+{
+    GD_CUDA(&H, cudaMemsetAsync(R, 0, sizeof(double) * H.n_dofs, H.stream));
+    GD_CUDA(&H, cudaMemsetAsync(vals64, 0, sizeof(double) * H.nnz, H.stream));
+    GD_CUDA(&H, cudaMemsetAsync(H.counters, 0, sizeof(int) * 8, H.stream));
+    GD_CUDA(&H, cudaEventRecord(H.ev0, H.stream));
+    gd::AsmArgs a = asm_args(H, dofs, kappa_n, R, nullptr, kappa_out, loading, 0);
+    a.vals = vals64;
+    a.vals32 = nullptr;
+    a.tangent = 1;
+    GD_CUDA(&H, gd::launch_assemble_fp64(H.dim, a, H.num_sms, H.stream, H.asm_tune));
+    ++H.launches;
+    GD_CUDA(&H, cudaEventRecord(H.ev1, H.stream));
+    ++H.assemblies;
+    return GD_OK;
+}
+
 double elapsed_ms(gd::Handle &H)
 {
     float ms = 0.0f;
@@ -275,7 +298,7 @@ enum MatKind { kTangent = 0, kTransposed = 1, kCallerMatrix = 2 };
 gd_status gmres(gd::Handle &H, const void *vals, const double *b, double *x, int &iters, double &rel, double rtol,
                 bool &converged)
 {
-    const bool fp32_vals = H.opt.precision == GD_MIXED;
+    const bool fp32_vals = H.opt.precision == GD_MIXED && !H.adj_fp64;
     const int m = std::max(1, std::min(H.opt.gmres_m, gd::gmres_max_m()));
     gd::SolverCtx c = solver_ctx(H, nullptr);
     if (fp32_vals) c.vals32 = (const float *)vals;
@@ -334,7 +357,7 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
         kind == kCallerMatrix || H.coarse_age < 0 || H.coarse_kind != kind || H.coarse_age >= kCoarseReuse;
     kc.coarse_refresh = refresh;
     GD_CUDA(&H, cudaEventRecord(H.kv0, H.stream));
-    bool fp32_vals = H.opt.precision == GD_MIXED;
+    bool fp32_vals = H.opt.precision == GD_MIXED && !H.adj_fp64;
     if (inner_fp32 && !fp32_vals) {
         GD_CUDA(&H, gd::narrow_to_float((const double *)vals, H.vals_f32, H.nnz, H.stream));
         ++H.launches;
@@ -533,7 +556,7 @@ gd_status krylov_batch(gd::Handle &H, const std::vector<double> &eta, const doub
     GD_CUDA(&H, cudaMemcpyAsync((void *)H.bk.rtol, eta.data(), sizeof(double) * S, cudaMemcpyHostToDevice, H.stream));
     GD_CUDA(&H, cudaEventRecord(H.kv0, H.stream));
     const void *vals = H.vals;
-    bool fp32_vals = H.opt.precision == GD_MIXED;
+    bool fp32_vals = H.opt.precision == GD_MIXED && !H.adj_fp64;
     if (inner_fp32 && !fp32_vals) {
         GD_CUDA(&H, gd::narrow_to_float((const double *)vals, H.vals_f32, H.nnz, H.stream));
         ++H.launches;
@@ -612,7 +635,6 @@ gd_status mixed_noise(gd::Handle &H, const double *R32, std::vector<double> &noi
     // the local solves start from the FP32 pass's kappa at this iterate
     gd_status st = assemble_pass(H, H.w_dofs, H.kappa, H.R_trial, nullptr, nullptr, nullptr, 0, true, H.kappa_trial);
     if (st) return st;
-    H.assembly_ms += elapsed_ms(H);
     gd::SolverCtx c = solver_ctx(H, nullptr);
     double *diff = H.kv[9];
     GD_CUDA(&H, gd::launch_residual(c, H.R_trial, R32, diff, H.scal + 32));
@@ -621,19 +643,23 @@ gd_status mixed_noise(gd::Handle &H, const double *R32, std::vector<double> &noi
     if (H.n_spec == 1) {
         GD_CUDA(&H, cudaMemcpyAsync(noise.data(), H.scal + 32, sizeof(double), cudaMemcpyDeviceToHost, H.stream));
         GD_CUDA(&H, cudaStreamSynchronize(H.stream));
-        return GD_OK;
+    } else {
+        std::vector<double> nx;
+        if ((st = norms_batch(H, diff, noise, nx))) return st;     // synchronises the stream
     }
-    std::vector<double> nx;
-    return norms_batch(H, diff, noise, nx);
+    H.noise_ms += elapsed_ms(H);        // the pass's events have completed
+    ++H.noise_passes;
+    return GD_OK;
 }
 
 // GD_MIXED noise level for the Newton test.  The rounding noise of the residual
-// scales with the element forces that cancel in it, so it is measured by the FP64
-// pass of mixed_noise on the first Newton solve (and after every new start of the
+// scales with the magnitudes of the terms that cancel in it, so it is measured by the
+// FP64 pass of mixed_noise on the first Newton solve (and after every new start of the
 // state) and every kNoiseEvery solves, and in between taken as the measured ratio to
-// the specimen's scale ||sum_e |R_e|||: the norm of the sum of the absolute element
-// residual rows, which the mixed kernels accumulate beside R (damage lowers the
-// reaction, but the element forces, and with them the noise, follow this norm).
+// the specimen's scale: the norm of the per-dof sums of the term magnitudes that the
+// mixed kernels accumulate beside R (|P_ij n_j| J w in the displacement rows;
+// |c_d C^-1 grad phi . grad N| J w + beta_d (|phi| + |kappa|) |N| J w in the damage rows,
+// whose phi - kappa cancels in FP32 however small the element residual gets).
 // The FP64 pass costs as much as several mixed passes.  A Newton solve whose line
 // search stalls on an estimate it did not measure itself measures it again (force =
 // true).
@@ -695,6 +721,7 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
         rep.iterations = it;
         rep.residual = nrm;
         if (!std::isfinite(nrm)) return fail(&H, GD_ERR_NAN, "non-finite residual in the Newton iteration");
+        H.last_noise = noise;
         if (nrm <= ntol) {
             rep.converged = 1;
             return GD_OK;
@@ -714,10 +741,17 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
         bool decreased = false;
         int ls_max = (H.opt.precision == GD_MIXED && nrm <= 8.0 * noise) ? std::min(2, H.opt.line_search_max)
                                                                          : H.opt.line_search_max;
+        bool at_floor = false;
         for (int ls = 0; ls <= ls_max; ++ls) {
             if (ls == 1 && H.opt.precision == GD_MIXED && !fresh) {
-                // the full step did not lower ||R_free||: measure the noise at this
-                // iterate before halving (the pass overwrites R_trial, recomputed below)
+                // the full step did not lower ||R_free||.  Within 8 times the estimated
+                // noise the iterate is at the floor of the mode; further away, measure the
+                // noise at this iterate before halving (the pass overwrites R_trial,
+                // recomputed below)
+                if (nrm <= 8.0 * noise) {
+                    at_floor = true;
+                    break;
+                }
                 std::vector<double> nz;
                 if ((st = noise_estimate(H, H.R, sc, nz, fresh, true))) return st;
                 noise = nz[0];
@@ -741,6 +775,14 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
             alpha *= 0.5;
             ++rep.line_search_cuts;
         }
+        if (at_floor) {
+            // the current iterate (H.w_dofs, H.R, H.kappa_trial) stands
+            rep.iterations = it + 1;
+            rep.residual = nrm;
+            rep.converged = 1;
+            H.last_noise = noise;
+            return GD_OK;
+        }
         std::swap(H.w_dofs, H.w_trial);
         std::swap(H.R, H.R_trial);
         std::swap(H.vals, H.vals_trial);
@@ -756,6 +798,7 @@ gd_status newton(gd::Handle &H, gd_newton_report &rep)
             rep.iterations = it + 1;
             rep.residual = nrm;
             rep.converged = 1;
+            H.last_noise = noise;
             return GD_OK;
         }
     }
@@ -835,6 +878,7 @@ gd_status newton_batch(gd::Handle &H, gd_newton_report &rep)
     for (int it = 0; it <= H.opt.newton_max; ++it) {
         rep.iterations = it;
         rep.residual = total(nf);
+        H.last_noise = noise.empty() ? 0.0 : *std::max_element(noise.begin(), noise.end());
         if (!std::isfinite(rep.residual)) return fail(&H, GD_ERR_NAN, "non-finite residual in the Newton iteration");
         bool all = true;
         for (int s = 0; s < S; ++s) {
@@ -1209,9 +1253,10 @@ gd_status advance(gd::Handle &H, double target, int depth, gd_newton_report &rep
     gd_status sp = predict(H, target);
     if (sp) return sp;
     gd_newton_report sub{};
-    const double a0 = H.assembly_ms, k0 = H.krylov_ms;
+    const double a0 = H.assembly_ms, k0 = H.krylov_ms, z0 = H.noise_ms;
     const int n0 = H.assemblies;
-    const long long l0 = H.launches;
+    const long long l0 = H.launches, p0 = H.noise_passes;
+    H.last_noise = 0.0;
     gd_status st = H.n_spec > 1                      ? newton_batch(H, sub)
                    : H.opt.scheme == GD_STAGGERED          ? newton_staggered(H, sub)
                    : H.opt.scheme == GD_STAGGERED_ITERATED ? newton_staggered_iterated(H, sub)
@@ -1222,6 +1267,9 @@ gd_status advance(gd::Handle &H, double target, int depth, gd_newton_report &rep
     rep.yield_evals += sub.yield_evals;
     rep.krylov_fp32_iterations += sub.krylov_fp32_iterations;
     rep.kernel_launches += H.launches - l0;
+    rep.noise_ms += H.noise_ms - z0;
+    rep.noise_passes += (int32_t)(H.noise_passes - p0);
+    rep.noise = H.last_noise;
     rep.iterations += sub.iterations;
     rep.krylov_iterations += sub.krylov_iterations;
     rep.line_search_cuts += sub.line_search_cuts;
@@ -1663,6 +1711,7 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
     do {                                                                                                   \
         cudaError_t e_ = (call);                                                                           \
         if (e_ != cudaSuccess) {                                                                           \
+            (void)cudaGetLastError();                                                                      \
             H.err = std::string(#call) + ": " + cudaGetErrorString(e_);                                    \
             return bail(e_ == cudaErrorMemoryAllocation ? GD_ERR_OOM : GD_ERR_CUDA);                       \
         }                                                                                                  \
@@ -1772,7 +1821,7 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
     GD_CREATE_CUDA(dalloc(&H.kappa_trial2, nq_tot));
     GD_CREATE_CUDA(dalloc(&H.loading, nq_tot));
     GD_CREATE_CUDA(dalloc(&H.loading2, nq_tot));
-    if (o.scheme == GD_STAGGERED) GD_CREATE_CUDA(dalloc(&H.kappa_stag, nq_tot));
+    if (o.scheme == GD_STAGGERED_ITERATED) GD_CREATE_CUDA(dalloc(&H.kappa_stag, nq_tot));
     GD_CREATE_CUDA(dalloc(&H.vals, (size_t)nnz));
     GD_CREATE_CUDA(dalloc(&H.vals_trial, (size_t)nnz));
     GD_CREATE_CUDA(dalloc(&H.counters, 8));
@@ -1904,6 +1953,7 @@ gd_status gd_set_params(gd_handle *h, const double *theta_psi, const double *the
     if (H.tc_blob) GD_CUDA(&H, gd::tc_build_blob(H.psi, H.yld, H.tc, H.tc_blob, H.stream));
     GD_CUDA(&H, cudaStreamSynchronize(H.stream));
     H.coarse_age = -1;                       // new networks, new tangents
+    H.noise_age = 0;                         // and a new rounding noise of the mixed residual
     return GD_OK;
 }
 
@@ -2276,7 +2326,6 @@ gd_status gd_backward(gd_handle *h, const double *dL_dreaction, double *dL_dthet
     if (!h) return fail(nullptr, GD_ERR_ARG, "null handle");
     gd::Handle &H = h->h;
     if (!dL_dreaction || !dL_dtheta) return fail(&H, GD_ERR_ARG, "null argument");
-    if (H.opt.precision != GD_FP64) return fail(&H, GD_ERR_STATE, "gd_backward needs GD_FP64 precision");
     if (H.n_spec > 1) return fail(&H, GD_ERR_STATE, "gd_backward takes a single-specimen handle");
     if (H.opt.scheme == GD_STAGGERED)
         return fail(&H, GD_ERR_STATE, "gd_backward differentiates the monolithic step equations, which the "
@@ -2287,6 +2336,8 @@ gd_status gd_backward(gd_handle *h, const double *dL_dreaction, double *dL_dthet
     const int64_t nq_tot = H.n_elems * H.nq;
     const int kseg = H.opt.checkpoint_every > 0 ? H.opt.checkpoint_every : 1;
     const int n_theta = H.psi.n_params + H.yld.n_params;
+    const bool mixed = H.opt.precision == GD_MIXED;
+    if (mixed && !H.vals64) GD_CUDA(&H, dalloc(&H.vals64, (size_t)H.nnz));
     // --- work space ---
     if (!H.perm_T) {
         std::vector<int32_t> perm((size_t)H.nnz);
@@ -2367,9 +2418,16 @@ gd_status gd_backward(gd_handle *h, const double *dL_dreaction, double *dL_dthet
             const int step = H.rec_step[c - 1];
             const double fbar = step >= 0 ? dL_dreaction[step - H.rec_start_step] : 0.0;
             const double *d_c = seg_d(c - c0), *k_c = seg_k(c - c0), *k_p = seg_k(c - c0 - 1);
-            // tangent at the converged state of commit c
-            if ((st = assemble_pass(H, d_c, k_p, H.R_trial, H.vals, H.kappa_trial2, H.loading2, 1))) break;
-            GD_CUDA(&H, gd::launch_gather(H.vals, H.perm_T, H.vals_T, H.nnz, H.stream));
+            // tangent at the converged state of commit c (GD_MIXED: the FP64 element
+            // kernel's tangent at the mixed path's state; the adjoint systems are FP64)
+            if (mixed) {
+                if ((st = assemble_tangent_fp64(H, d_c, k_p, H.R_trial, H.vals64, H.kappa_trial2, H.loading2)))
+                    break;
+                GD_CUDA(&H, gd::launch_gather(H.vals64, H.perm_T, H.vals_T, H.nnz, H.stream));
+            } else {
+                if ((st = assemble_pass(H, d_c, k_p, H.R_trial, H.vals, H.kappa_trial2, H.loading2, 1))) break;
+                GD_CUDA(&H, gd::launch_gather(H.vals, H.perm_T, H.vals_T, H.nnz, H.stream));
+            }
             // source (dkappa/dd)^T kbar
             GD_CUDA(&H, cudaMemsetAsync(S, 0, sizeof(double) * H.n_dofs, H.stream));
             gd::AdjArgs A;
@@ -2396,7 +2454,10 @@ gd_status gd_backward(gd_handle *h, const double *dL_dreaction, double *dL_dthet
             if (fbar != 0.0) GD_CUDA(&H, gd::launch_spmv(cT, er, y, 0));
             GD_CUDA(&H, gd::launch_adj_rhs(H.n_dofs, S, fbar != 0.0 ? y : nullptr, fbar, H.fixed, rhs, H.stream));
             // K^T lambda = rhs on the free dofs (FP64, refined against the true residual)
-            if ((st = krylov_true(H, H.vals_T, rhs, lam, H.opt.krylov_rtol))) break;
+            H.adj_fp64 = true;
+            st = krylov_true(H, H.vals_T, rhs, lam, H.opt.krylov_rtol);
+            H.adj_fp64 = false;
+            if (st) break;
             GD_CUDA(&H, gd::launch_axpby(H.n_dofs, w, lam, fbar, er, H.stream));
             A.mode = 1;
             A.w = w;

@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(32 * KW) asm_fp64_kernel(AsmArgs A)
             for (int p = 0; p < 32; ++p) {
                 if (e0 + p / NQ >= A.n_elems) break;
                 double y[3] = {sIn[p * 4], sIn[p * 4 + 1], sIn[p * 4 + 2]}, out[10];
-                psi_net_unit(psi_of(A, spec_of(A, e0 + p / NQ)), y, out, sBuf, lane);
+                psi_net_unit(psi_of(A, spec_of(A, e0 + p / NQ)), y, out, sBuf, lane, A.tangent != 0);
                 if (lane == 0)
 #pragma unroll
                     for (int c = 0; c < 10; ++c) sOut[p * 10 + c] = out[c];
@@ -317,15 +317,21 @@ __global__ void __launch_bounds__(32 * KW) asm_fp64_kernel(AsmArgs A)
                 // The root in FP32 (the lazily bracketed Newton iteration of the mixed
                 // kernel, from the warm start), then FP64: one value-only evaluation and
                 // a Newton step with the FP32 slope (its relative error, ~1e-7, times a
-                // residual of ~1e-6 leaves ~1e-13), then one full evaluation and a last
+                // correction of ~1e-6 leaves ~1e-13), then one full evaluation and a last
                 // Newton step; the slope and G' of that evaluation feed the tangent (they
                 // change by ~1e-12 relative over the last step).  Where the FP32 root is not
-                // close enough, the FP64 bracketed iteration takes over from it.
+                // close enough, the FP64 bracketed iteration takes over from it.  Both
+                // iterations also stop on the next Newton correction |r / r'| (the step test
+                // of the safeguarded Newton-bisection; FP32: 2e-6 relative, FP64: 4 ulp) once
+                // the root is bracketed within 1e-2 relative or the iteration converges from
+                // one side: near full damage r' grows like 1 / f_d, and r itself cannot get
+                // below its rounding.  (A wide bracket does not qualify: far past the root,
+                // where f_d underflows, r' is huge and the correction meaningless.)
                 const float kg = A.kappa_guess ? (float)__ldg(A.kappa_guess + e0 * NQ + p) : (float)kn;
                 float k32 = (float)kn;
                 int n32 = 0;
                 const bool ok32 = e32::bracketed_newton(yn, mf, nf, (float)ppe, (float)pphi, (float)kn, kg, k32, r32,
-                                                        dr32, Gp32, n32, fbuf, lane);
+                                                        dr32, Gp32, n32, fbuf, lane, true);
                 bool done = false;
                 if (ok32 && isfinite(k32) && (double)k32 >= kn && dr32 < 0.0f) {
                     const double sc = fabs((double)k32) > 1.0 ? fabs((double)k32) : 1.0;
@@ -361,10 +367,14 @@ __global__ void __launch_bounds__(32 * KW) asm_fp64_kernel(AsmArgs A)
                         have_hi = true;
                     }
                     double dx_prev = have_hi ? hi - lo : 1.0e30, dx = dx_prev;
+                    bool took_newton = false;
                     int it;
                     for (it = 0; it < m.local_max; ++it) {
                         const double scale = fabs(kappa) > 1.0 ? fabs(kappa) : 1.0;
-                        if (fabs(r) <= 1e-13 * scale || (have_hi && (hi - lo) <= 4.0 * 2.220446049250313e-16 * scale))
+                        const double ulp4 = 4.0 * 2.220446049250313e-16 * scale;
+                        if (fabs(r) <= 1e-13 * scale || (have_hi && (hi - lo) <= ulp4)) break;
+                        if (fabs(r) <= ulp4 * fabs(dr) &&
+                            (have_hi ? (hi - lo) <= 1e-2 * scale : (took_newton && fabs(2.0 * r) <= fabs(dx * dr))))
                             break;
                         const double newton = kappa - r / dr;
                         bool take;
@@ -376,6 +386,7 @@ __global__ void __launch_bounds__(32 * KW) asm_fp64_kernel(AsmArgs A)
                             take = dr < 0.0 && newton > lo && (newton - kappa) <= cap;
                         }
                         dx_prev = dx;
+                        took_newton = take;
                         if (take) {
                             dx = kappa - newton;
                             kappa = newton;

@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) asm_tc_kernel(AsmArgs A, TcArgs
         const float kn = valid ? (float)__ldg(A.kappa_n + e_me * NQ + q) : 0.0f;
         const double kn_d = valid ? __ldg(A.kappa_n + e_me * NQ + q) : 0.0;
         float kappa = kn, Gp = 0.0f, dr = -1.0f, r = 0.0f, lo = kn, hi = kn, dx = 1e30f, dx_prev = 1e30f;
-        bool loading = false, fail = false, have_hi = false;
+        bool loading = false, fail = false, have_hi = false, took_newton = false;
         int it = 0, n_eval = 0;
         int state = (valid && !frozen) ? 1 : 0;      // 1 trial at kappa_n, 2 warm start, 3 iteration
         if (frozen) kappa = valid ? (float)__ldg(A.kappa_fixed + e_me * NQ + q) : 0.0f;
@@ -593,6 +593,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) asm_tc_kernel(AsmArgs A, TcArgs
                     state = 0;
                 } else if (fabsf(r) <= tol_r * scale || (have_hi && (hi - lo) <= tol_br * scale)) {
                     state = 0;
+                } else if (fabsf(r) <= 0.1f * tol_r * scale * fabsf(dr) &&
+                           (have_hi ? (hi - lo) <= 1e-2f * scale
+                                    : (took_newton && fabsf(2.0f * r) <= fabsf(dx * dr)))) {
+                    // the next Newton correction is within a tenth of the tolerance, with the
+                    // root bracketed within 1e-2 or the iteration converging from one side
+                    // (near full damage r' grows like 1 / f_d and |r| stays at its rounding)
+                    state = 0;
                 } else {
                     const float newton = kappa - r / dr;
                     bool take;
@@ -603,6 +610,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) asm_tc_kernel(AsmArgs A, TcArgs
                         take = dr < 0.0f && newton > lo && (newton - kappa) <= cap;
                     }
                     dx_prev = dx;
+                    took_newton = take;
                     if (take) {
                         dx = kappa - newton;
                         kappa = newton;

@@ -112,7 +112,8 @@ __device__ __forceinline__ int sym6(int i, int j)
 //   g_k = dh2_k/dx,  v = W2^T (w3 o sp'(h2)),
 // so layer 2 costs 4 forward columns and 1 reverse column per point.
 // Every lane returns the full result.
-__device__ void psi_net_unit(const DevNet &net, const double *x, double *out10, double *buf, int lane)
+__device__ void psi_net_unit(const DevNet &net, const double *x, double *out10, double *buf, int lane,
+                             bool hess = true)
 {
     const int w = net.width;
     const double *W1 = net.p, *b1 = W1 + 3 * w, *W2 = b1 + w, *A2 = W2 + w * w, *b2 = A2 + 3 * w, *w3 = b2 + w,
@@ -173,8 +174,10 @@ __device__ void psi_net_unit(const DevNet &net, const double *x, double *out10, 
         }
     }
     __syncwarp();
+    // the Hessian's layer-1 term (one reverse column through layer 2): only where the
+    // caller needs second derivatives (hess = false: out10[4..9] lack it)
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < 2 && hess; ++t) {
         int j = lane + 32 * t;
         if (j < w) {
             double v = 0.0;

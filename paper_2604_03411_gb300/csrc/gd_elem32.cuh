@@ -136,7 +136,8 @@ enum : int {
     Q_PP = 68,       // beta_d (1 - dkappa/dphi)
     Q_PEN = 69,      // beta_d (phi - kappa)
     Q_J = 70,        // det F
-    Q_REC = 71
+    Q_PENM = 71,     // beta_d (|phi| + |kappa|): the magnitude that the penalty's FP32 rounding scales with
+    Q_REC = 72
 };
 // ---- per (point, node) vector record ----
 enum : int { V_N = 0, V_NN = 3, V_F = 4, V_G2 = 7, V_NT = 10, V_PN = 13, V_MN = 16, V_REC = 17 };
@@ -224,9 +225,15 @@ __device__ __forceinline__ void r_slope(const DevNet &yld, const MatF &m, const 
 // bracket of 4 FP32 ulps), r, dr and Gp are evaluated there, n_eval counts the
 // evaluations; false when local_max iterations did not reach it.  Every lane takes
 // the same path (r and dr are warp-reduced).
+// step_test: also stop when the next Newton correction |r / r'| is within the tolerance
+// and either the root is bracketed within 1e-2 relative or the iteration is converging
+// from one side (the last step a Newton step at least twice as long).  For a starting
+// point that FP64 refines: near full damage r' grows like 1 / f_d and |r| cannot get
+// below its FP32 rounding; far past the root, where f_d underflows, r' is huge, so a
+// wide bracket never qualifies.
 __device__ __forceinline__ bool bracketed_newton(const DevNet &yn, const MatF &m, const NcF &ncp, float pe, float phi,
                                                  float kn, float kg, float &kappa, float &r, float &dr, float &Gp,
-                                                 int &n_eval, float *buf, int lane)
+                                                 int &n_eval, float *buf, int lane, bool step_test = false)
 {
     // Newton iteration on r(kappa) = G(q(kappa)) - kappa from kappa_n (r > 0 there)
     // or from the warm-start guess, bracketing lazily: lo keeps the last point with
@@ -246,10 +253,14 @@ __device__ __forceinline__ bool bracketed_newton(const DevNet &yn, const MatF &m
         have_hi = true;
     }
     float dx_prev = have_hi ? hi - lo : 1.0e30f, dx = dx_prev;
+    bool took_newton = false;
     int it;
     for (it = 0; it < m.local_max; ++it) {
         const float scale = fabsf(kappa) > 1.0f ? fabsf(kappa) : 1.0f;
         if (fabsf(r) <= 2e-6f * scale || (have_hi && (hi - lo) <= 4.0f * kEpsF * scale)) break;
+        if (step_test && fabsf(r) <= 2e-6f * scale * fabsf(dr) &&
+            (have_hi ? (hi - lo) <= 1e-2f * scale : (took_newton && fabsf(2.0f * r) <= fabsf(dx * dr))))
+            break;
         const float newton = kappa - r / dr;
         bool take;
         if (have_hi) {
@@ -260,6 +271,7 @@ __device__ __forceinline__ bool bracketed_newton(const DevNet &yn, const MatF &m
             take = dr < 0.0f && newton > lo && (newton - kappa) <= cap;
         }
         dx_prev = dx;
+        took_newton = take;
         if (take) {
             dx = kappa - newton;
             kappa = newton;
@@ -581,6 +593,7 @@ __device__ __forceinline__ void stress_records(const MatF &m, const float (&F)[3
     rec[Q_FDK] = fdp * dkdphi;
     rec[Q_PP] = m.beta_d * (1.0f - dkdphi);
     rec[Q_PEN] = m.beta_d * (phi - kappa);
+    rec[Q_PENM] = m.beta_d * (fabsf(phi) + fabsf(kappa));
     rec[Q_J] = J;
     if (!valid) rec[Q_JW] = 0.0f;
 }
@@ -639,7 +652,7 @@ __device__ __forceinline__ void row_mode(const Args &A, const MatF &m, const flo
         float Kr[ND];
 #pragma unroll
         for (int c = 0; c < ND; ++c) Kr[c] = 0.0f;
-        float Rr = 0.0f;
+        float Rr = 0.0f, Mr = 0.0f;      // Mr: sum of the magnitudes of the row's terms (A.Rabs)
         const float cd = m.c_d;
         if (active) {
             for (int qq = 0; qq < NQ; ++qq) {
@@ -649,8 +662,10 @@ __device__ __forceinline__ void row_mode(const Args &A, const MatF &m, const flo
                 const float Jw = R0[Q_JW];
                 if (i < DIM) {
                     // r_u,a = P n_a J w (Sec. 3.1f)
-                    Rr += Jw * (R0[Q_P + i * 3] * Va[V_N] + R0[Q_P + i * 3 + 1] * Va[V_N + 1] +
-                                R0[Q_P + i * 3 + 2] * Va[V_N + 2]);
+                    const float t0 = R0[Q_P + i * 3] * Va[V_N], t1 = R0[Q_P + i * 3 + 1] * Va[V_N + 1],
+                                t2 = R0[Q_P + i * 3 + 2] * Va[V_N + 2];
+                    Rr += Jw * (t0 + t1 + t2);
+                    if (A.Rabs) Mr += Jw * (fabsf(t0) + fabsf(t1) + fabsf(t2));
                     if (!A.tangent) continue;      // residual-only pass: no tangent rows
                     // d2 psi_e/dF2 contracted with grad N_a, grad N_b:
                     //   sum_mn psi_mn G^m_a G^n_b + psi_1 D2(I1) + psi_2 D2(I2) + psi_3 D2(J),
@@ -694,6 +709,7 @@ __device__ __forceinline__ void row_mode(const Args &A, const MatF &m, const flo
                     // R_phi,a = (Y . grad N_a - Y N_a) J w, Y vec = c_d C^-1 grad phi, -Y = beta_d (phi - kappa)
                     const float Na = Va[V_NN];
                     Rr += Jw * (cd * Va[V_MN] + R0[Q_PEN] * Na);
+                    if (A.Rabs) Mr += Jw * (fabsf(cd * Va[V_MN]) + R0[Q_PENM] * fabsf(Na));
                     if (!A.tangent) continue;
                     const float bck = R0[Q_BCK], pp = R0[Q_PP];
 #pragma unroll
@@ -714,7 +730,7 @@ __device__ __forceinline__ void row_mode(const Args &A, const MatF &m, const flo
             const int32_t na = __ldg(A.conn + e * NEN + a);
             const int64_t rdof = (int64_t)na * NDOF + i;
             if (A.R) atomicAdd(A.R + rdof, (double)Rr);
-            if (A.Rabs) atomicAdd(A.Rabs + rdof, (double)fabsf(Rr));
+            if (A.Rabs) atomicAdd(A.Rabs + rdof, (double)Mr);
             if (A.tangent) {
                 const int32_t rb = __ldg(A.rowptr + (int64_t)na * NDOF);
                 const int32_t rowlen = __ldg(A.rowptr + (int64_t)na * NDOF + 1) - rb;

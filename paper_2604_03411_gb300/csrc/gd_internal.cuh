@@ -47,7 +47,8 @@ struct AsmArgs {
     const double *dofs;
     const double *kappa_n;
     double *R;               // may be null
-    double *Rabs;            // may be null (mixed kernels): sum over elements of |element residual row|
+    double *Rabs;            // may be null (mixed kernels): per dof, the summed magnitudes of the terms of
+                             // the element residual rows (the scale of their FP32 rounding)
     double *vals;            // FP64 values (may be null)
     float *vals32;           // FP32 values (mixed mode, may be null)
     double *kappa_new;       // may be null
@@ -261,6 +262,9 @@ struct Handle {
     double *gm_ws = nullptr;                             // GMRES work space (allocated on first use)
     double *gm_binv = nullptr;                           // its node-block inverses (FP64)
     long long gmres_iterations = 0;                      // GMRES iterations run by this handle
+    long long noise_passes = 0;                          // GD_MIXED FP64 reference passes run
+    double noise_ms = 0.0;                               // their device time
+    double last_noise = 0.0;                             // noise level of the last Newton test
     int krylov_lmax = 0;                                 // longest CSR row
     CoarseSpace coarse;                                  // two-level preconditioner (nc = 0: off)
     // tensor-core networks of the mixed element kernel (icnn_mma): mode and weight blob
@@ -289,6 +293,10 @@ struct Handle {
     std::vector<Checkpoint> ckpts;
     // adjoint work space (allocated by the first gd_backward)
     int32_t *perm_T = nullptr;
+    // GD_MIXED adjoint: FP64 tangent of the FP64 element kernel at the mixed path's states,
+    // and the switch that makes the solvers read FP64 values in a mixed handle
+    double *vals64 = nullptr;
+    bool adj_fp64 = false;
     double *vals_T = nullptr, *adj_v[6] = {}, *kbar = nullptr, *kbar2 = nullptr, *theta_bar = nullptr,
            *glob = nullptr, *seg = nullptr;
     int seg_cap = 0;

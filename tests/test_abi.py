@@ -176,3 +176,16 @@ def test_batch_create_rejects_bad_specimens(B):
     with pytest.raises(B.GDError) as ei:
         B.gd_create_batch(good[:1] + [I.Problem("f", flipped, *I.icnn_pair(6, 4, 4), mat, good[0].load)])
     assert ei.value.status == 2
+
+
+def test_binding_constants_match_header_enums(B):
+    """Every GD_* enumerator of include/gd.h has the same value in the binding."""
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gd.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    seen = 0
+    for body in re.findall(r"enum\s*(?:gd_status\s*)?\{(.*?)\}", hdr, flags=re.S):
+        for name, val in re.findall(r"(GD_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+            assert hasattr(B, name), name
+            assert getattr(B, name) == int(val), name
+            seen += 1
+    assert seen >= 30

@@ -236,3 +236,24 @@ def test_adjoint_cfg4_notched_plate(env):
         # (measured ~5e-9 absolute, 1e-7 of the largest), so those are held to 1e-6 of
         # the largest component
         assert abs(g[i] - fd) <= 1e-5 * max(abs(fd), 0.1 * scale), (i, g[i], fd)
+
+
+def test_mixed_precision_gradient(env):
+    """gd_backward on a GD_MIXED path (recomputed in mixed precision, FP64 adjoint
+    systems at its states) against the FP64 path's gradient: the stated mixed
+    tolerance of the gradient is 1e-3 relative to the largest component."""
+    torch, B, oracle = env
+    prob = small_problem()
+    r = {}
+    for prec in (B.GD_FP64, B.GD_MIXED):
+        o = opts(B) if prec == B.GD_FP64 else B.gd_default_options(precision=B.GD_MIXED, checkpoint_every=2)
+        h = B.gd_create(prob, o)
+        reac, rep = B.gd_run_load_path(h)
+        assert rep.step_cuts == 0
+        w = np.linspace(1.0, 2.0, reac.size)
+        r[prec] = (reac, B.gd_backward(h, w))
+    g64, g32 = r[B.GD_FP64][1], r[B.GD_MIXED][1]
+    err = np.abs(g32 - g64).max() / np.abs(g64).max()
+    rerr = np.abs(r[B.GD_MIXED][0] - r[B.GD_FP64][0]).max() / np.abs(r[B.GD_FP64][0]).max()
+    print(f"mixed vs FP64: reaction {rerr:.2e}, gradient {err:.2e} (largest component)")
+    assert err < 1e-3, err
