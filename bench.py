@@ -306,10 +306,14 @@ def element_roofline(reps, probs, n_elems_all, fp64, icnn, peaks):
     return out
 
 
-def timed_run(args, B, torch, probs, batch, precision, stream, flush, n_path, steps, warmup, tune=True):
+def timed_run(args, B, torch, probs, batch, precision, stream, flush, n_path, steps, warmup, tune=True,
+              schedule=None):
     """W untimed load steps, gd_autotune, then K steps timed with CUDA events on the
-    library's stream, the L2 flushed between them.  Returns the handle, the reports
-    and the timings."""
+    library's stream, the L2 flushed between them.  Returns the handle, the reports,
+    the timings, the saved state, the tuning, the step function and the restart
+    schedule (one flag per warm-up and timed step: the path restarted before it).
+    schedule: restart flags to follow instead of deciding (the other precision then
+    runs exactly the same load steps)."""
     import numpy as np
     prec = B.GD_FP64 if precision == "fp64" else B.GD_MIXED
     opts = B.gd_default_options(precision=prec, cuda_stream=stream.cuda_stream,
@@ -322,14 +326,22 @@ def timed_run(args, B, torch, probs, batch, precision, stream, flush, n_path, st
     n_nodes_all = sum(p.mesh.n_nodes for p in probs)
     n_elems_all = sum(p.mesh.n_elems for p in probs)
     mesh0 = probs[0].mesh
-    state = {"next": 0, "dmax": 0.0}
+    state = {"next": 0, "dmax": 0.0, "k": 0}
+    flags = []
 
     def step():
         # the path restarts from the undeformed state when it runs out or once a step
         # has brought the largest damage to D_STOP (the uniform-deformation runs of
         # Sec. 5.2 stop there: beyond it the block carries no load and the steps only
         # probe a vanishing stiffness)
-        if state["next"] >= n_path or state["dmax"] >= D_STOP:
+        k = state["k"]
+        state["k"] += 1
+        if schedule is not None and k < len(schedule):
+            restart = schedule[k]
+        else:
+            restart = state["next"] >= n_path or state["dmax"] >= D_STOP
+        flags.append(bool(restart))
+        if restart:
             B.gd_set_state(h, np.zeros(n_nodes_all * mesh0.ndof), np.zeros((n_elems_all, mesh0.nq)), 0)
             state["next"] = 0
         r = B.gd_newton_step(h)
@@ -360,7 +372,7 @@ def timed_run(args, B, torch, probs, batch, precision, stream, flush, n_path, st
         evs[k][1].record(stream)
     torch.cuda.synchronize()
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    return h, reps, total_ms, saved, tuning, step
+    return h, reps, total_ms, saved, tuning, step, list(flags)
 
 
 def run_gd(args):
@@ -400,7 +412,8 @@ def run_gd(args):
         dist.barrier()
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    h, reps, total_ms, saved, tuning, step = timed_run(args, B, torch, probs, batch, args.precision, stream, flush,
+    h, reps, total_ms, saved, tuning, step, sched = timed_run(args, B, torch, probs, batch, args.precision, stream,
+                                                             flush,
                                                       n_path, args.steps, args.warmup)
     clk = clocks.stop()
     coarse_aggs, coarse_n = B.gd_coarse_info(h)
@@ -454,7 +467,9 @@ def run_gd(args):
     e2e_units = 0
     for k in range(args.steps):
         flush.zero_()
-        if nxt >= n_path or dmax >= D_STOP:      # the path's end, as in the timed loop
+        kk = args.warmup + k
+        restart = sched[kk] if kk < len(sched) else (nxt >= n_path or dmax >= D_STOP)
+        if restart:                                # the path's end, as in the timed loop
             d_host[:] = 0.0
             k_host[:] = 0.0
             nxt = 0
@@ -498,16 +513,29 @@ def run_gd(args):
     # --- the other precision over the same load steps ---
     if not args.no_compare:
         other = "fp64" if args.precision == "mixed" else "mixed"
-        h2, reps2, ms2, _, _, _ = timed_run(args, B, torch, probs, batch, other, stream, flush, n_path, args.steps,
-                                            args.warmup, tune=True)
+        # the same load steps: the restarts follow the first run's schedule
+        h2, reps2, ms2, _, _, _, _ = timed_run(args, B, torch, probs, batch, other, stream, flush, n_path, args.steps,
+                                               args.warmup, tune=True, schedule=sched)
         useful2 = sum(r.iterations + 1 + 2 * r.step_cuts for r in reps2)
         sub = {"value": n_qp * useful2 / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2 / args.steps}
         sub.update(summary(reps2, ms2, other))
         if not batch:
             r_mixed = np.array([r.reaction for r in (reps if args.precision == "mixed" else reps2)])
             r_fp64 = np.array([r.reaction for r in (reps2 if args.precision == "mixed" else reps)])
-            line["reaction_rel_err_mixed_vs_fp64"] = float(np.max(np.abs(r_mixed - r_fp64)) /
-                                                          max(np.max(np.abs(r_fp64)), 1e-300))
+            scale = max(np.max(np.abs(r_fp64)), 1e-300)
+            line["reaction_rel_err_mixed_vs_fp64"] = float(np.max(np.abs(r_mixed - r_fp64)) / scale)
+            # by the damage the step reached: near d = 1 the reaction is a few percent of
+            # its peak and the mixed residual's rounding floor decides its last digits
+            dmx = np.array([r.max_damage for r in (reps2 if args.precision == "mixed" else reps)])
+            bins = {}
+            for name, lo, hi in (("d<0.9", -1.0, 0.9), ("0.9<=d<0.99", 0.9, 0.99), ("d>=0.99", 0.99, 2.0)):
+                sel = (dmx >= lo) & (dmx < hi)
+                if sel.any():
+                    bins[name] = {"steps": int(sel.sum()),
+                                  "of_peak": float(np.max(np.abs(r_mixed - r_fp64)[sel]) / scale),
+                                  "of_step": float(np.max(np.abs(r_mixed - r_fp64)[sel] /
+                                                          np.maximum(np.abs(r_fp64[sel]), 1e-300)))}
+            line["reaction_err_by_damage"] = bins
         line[other] = sub
         line["speedup_mixed_over_fp64"] = (value / sub["value"]) if args.precision == "mixed" else (sub["value"] / value)
         del h2
