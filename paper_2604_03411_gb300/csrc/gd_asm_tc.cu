@@ -191,9 +191,11 @@ __device__ __forceinline__ void mma_product(uint32_t d, uint32_t a_hi, uint32_t 
 
 struct Shared {
     uint8_t *blob, *tiles;
-    uint64_t *bar;                       // [0] weight copy, [1] MMA completion
+    uint64_t *bar;                       // [0] weight copy, [1] MMA completion, [2] weight slot
     uint32_t tbase;
     uint32_t phase;                      // parity of the next MMA completion to wait for
+    uint32_t slot_phase;                 // parity of the next slot copy to wait for
+    bool slot_pending;                   // a slot copy was issued and not yet waited for
     bool ok;
 };
 
@@ -205,6 +207,32 @@ __device__ __forceinline__ void wait_mma(Shared &S, const TcArgs &T)
         atomicOr(T.status, 1);
     }
     S.phase ^= 1u;
+}
+
+// The weight slot: with both networks on the tensor cores, W2^T (the energy network's
+// reverse product) and V2 (the yield network) take turns in one region of shared memory,
+// refilled from the L2-resident blob by a bulk copy per batch of 128 points (32 KB per
+// batch at width 64, split operands), which lets two CTAs share an SM.
+// Every thread calls these at the same program point (CTA-uniform).
+__device__ __forceinline__ void slot_wait(Shared &S, const TcArgs &T)
+{
+    if (!S.slot_pending) return;
+    if (!mbar_wait(S.bar + 2, S.slot_phase)) {
+        S.ok = false;
+        atomicOr(T.status, 1);
+    }
+    S.slot_phase ^= 1u;
+    S.slot_pending = false;
+}
+// issue the copy of `bytes` from the global blob at `src_off` into the slot (thread 0);
+// the slot must be free: no product reading it in flight, no copy pending
+__device__ __forceinline__ void slot_fill(Shared &S, const TcArgs &T, int src_off, int bytes, int tid)
+{
+    if (tid == 0) {
+        mbar_expect_tx(S.bar + 2, (uint32_t)bytes);
+        bulk_g2s(S.blob + T.s_slot, T.blob + src_off, (uint32_t)bytes, S.bar + 2);
+    }
+    S.slot_pending = true;
 }
 
 // ---------------------------------------------------------------- energy network
@@ -254,11 +282,11 @@ __device__ void energy_net_tc(Shared &S, const TcArgs &T, const float (&y)[3], f
 {
     const TcLayout &L = T.L;
     const int w = L.we, wp = L.wpe;
-    const float *e32 = reinterpret_cast<const float *>(S.blob + L.off_e32);
+    const float *e32 = reinterpret_cast<const float *>(S.blob + T.s_e32);
     const float *W1 = e32, *b1 = e32 + 3 * w, *A2 = e32 + 4 * w, *b2 = e32 + 7 * w, *w3 = e32 + 8 * w,
                 *a3 = e32 + 9 * w;
     uint8_t *t0 = S.tiles, *t1 = S.tiles + T.tile_bytes;
-    const uint32_t a0 = saddr(t0), a1 = saddr(t1), bw = saddr(S.blob + L.off_w2f), br = saddr(S.blob + L.off_w2r);
+    const uint32_t a0 = saddr(t0), a1 = saddr(t1), bw = saddr(S.blob), br = saddr(S.blob + T.s_slot);
     const uint32_t lane_base = S.tbase + ((uint32_t)(warp * 32) << 16);
     constexpr int ROUNDS = SPLIT ? 4 : 2;
     // ---- forward columns: type t lands in tensor-memory columns [t wp, (t+1) wp)
@@ -326,7 +354,8 @@ __device__ void energy_net_tc(Shared &S, const TcArgs &T, const float (&y)[3], f
             if (SPLIT) st_row8_lo(t1, tid, k0 / 8 + h8, wp, v8);
         }
     }
-    // ---- reverse column v = W2^T u into columns [0, wp)
+    // ---- reverse column v = W2^T u into columns [0, wp) (W2^T in the weight slot)
+    slot_wait(S, T);
     tc_before();
     fence_async_smem();
     __syncthreads();
@@ -337,6 +366,8 @@ __device__ void energy_net_tc(Shared &S, const TcArgs &T, const float (&y)[3], f
     }
     wait_mma(S, T);
     tc_after();
+    // the reverse product has read W2^T: the yield network's V2 takes the slot
+    if (T.slot_mode == 3) slot_fill(S, T, L.off_v2f, T.v2_bytes, tid);
     for (int j0 = 0; j0 < wp; j0 += 16) {
         float v[16];
         tmem_ld16(lane_base + (uint32_t)j0, v);
@@ -411,11 +442,12 @@ __device__ void yield_tc(Shared &S, const TcArgs &T, const NcF &nc, float q, boo
 {
     const TcLayout &L = T.L;
     const int w = L.wy, wp = L.wpy;
-    const float *y32 = reinterpret_cast<const float *>(S.blob + L.off_y32);
+    const float *y32 = reinterpret_cast<const float *>(S.blob + T.s_y32);
     const float *B2 = y32 + 2 * w, *c2 = y32 + 3 * w, *v3 = y32 + 4 * w, *b3 = y32 + 5 * w;
     uint8_t *t0 = S.tiles, *t1 = S.tiles + T.tile_bytes;
-    const uint32_t a0 = saddr(t0), a1 = saddr(t1), bv = saddr(S.blob + L.off_v2f);
+    const uint32_t a0 = saddr(t0), a1 = saddr(t1), bv = saddr(S.blob + T.s_slot);
     constexpr int ROUNDS = SPLIT ? 2 : 1;
+    slot_wait(S, T);                     // V2 in the weight slot
     for (int r = 0; r < ROUNDS; ++r) {
         if (r > 0) wait_mma(S, T);
         if (need) yield_l1<SPLIT>(y32, w, wp, q, r, t0, t1, tid);
@@ -473,8 +505,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) asm_tc_kernel(AsmArgs A, TcArgs
     S.tiles = tc_smem + T.tiles_off;
     S.bar = reinterpret_cast<uint64_t *>(tc_smem + T.bar_off);
     S.phase = 0;
+    S.slot_phase = 0;
+    S.slot_pending = false;
     S.ok = true;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(S.bar + 2);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(S.bar + 3);
     float *ws = reinterpret_cast<float *>(tc_smem + T.warp_off) + warp * T.warp_floats;
     float *sX = ws;                                  // [EPW][NEN][DIM]
     float *sD = sX + EPW * NEN * DIM;                // [EPW][NEN][NDOF]
@@ -486,6 +520,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) asm_tc_kernel(AsmArgs A, TcArgs
     if (tid == 0) {
         mbar_init(S.bar, 1);
         mbar_init(S.bar + 1, 1);
+        mbar_init(S.bar + 2, 1);
         mbar_fence_init();
     }
     if (warp == 0) tmem_alloc(tslot, (uint32_t)T.ncols);
@@ -493,10 +528,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) asm_tc_kernel(AsmArgs A, TcArgs
     __syncthreads();
     tc_after();
     S.tbase = *tslot;
-    // weight tiles and per-unit vectors: one bulk copy
+    // W2, the per-unit vectors and a resident slot (W2^T or V2): bulk copies on one barrier
     if (tid == 0) {
-        mbar_expect_tx(S.bar, (uint32_t)T.L.bytes);
-        bulk_g2s(S.blob, T.blob, (uint32_t)T.L.bytes, S.bar);
+        const int resident = (T.slot_mode == 1 || T.slot_mode == 2) ? T.slot_bytes : 0;
+        mbar_expect_tx(S.bar, (uint32_t)(T.fwd_bytes + T.vec_bytes + resident));
+        if (T.fwd_bytes > 0) bulk_g2s(S.blob, T.blob + T.L.off_w2f, (uint32_t)T.fwd_bytes, S.bar);
+        bulk_g2s(S.blob + T.s_e32, T.blob + T.L.off_e32, (uint32_t)T.vec_bytes, S.bar);
+        if (T.slot_mode == 1) bulk_g2s(S.blob + T.s_slot, T.blob + T.L.off_w2r, (uint32_t)T.rev_bytes, S.bar);
+        if (T.slot_mode == 2) bulk_g2s(S.blob + T.s_slot, T.blob + T.L.off_v2f, (uint32_t)T.v2_bytes, S.bar);
     }
     if (!mbar_wait(S.bar, 0)) {
         S.ok = false;
@@ -508,6 +547,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) asm_tc_kernel(AsmArgs A, TcArgs
     const int64_t per_cta = 4 * EPW;
     const int64_t n_cb = (A.n_elems + per_cta - 1) / per_cta;
     for (int64_t cb = blockIdx.x; cb < n_cb; cb += gridDim.x) {
+        // W2^T into the weight slot for this batch's reverse product: the previous batch's
+        // yield products have completed (each was waited for); a V2 copy it never used is
+        // consumed first
+        if (T.slot_mode == 3) {
+            slot_wait(S, T);
+            slot_fill(S, T, T.L.off_w2r, T.rev_bytes, tid);
+        }
         const int64_t e0 = (cb * 4 + warp) * EPW;
         load_nodes<DIM>(A, e0, sX, sD, lane);
         __syncwarp();
@@ -643,6 +689,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) asm_tc_kernel(AsmArgs A, TcArgs
         __syncthreads();
         row_mode<DIM>(A, m, sRec, sVec, e0, lane);
     }
+    slot_wait(S, T);                     // no copy into shared memory outlives the CTA
     tc_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(S.tbase, (uint32_t)T.ncols);
@@ -749,8 +796,23 @@ cudaError_t launch_tc_t(const AsmArgs &a, const TcLaunch &c, cudaStream_t s)
     int ncols = 32;
     while (ncols < need_cols) ncols *= 2;
     T.ncols = ncols;
-    // shared memory: blob | two operand tiles (also the row-mode vectors) | per-warp scratch | barriers
-    size_t off = ((size_t)c.L.bytes + 1023) / 1024 * 1024;
+    // weights in shared memory: W2 | the slot (W2^T and/or V2) | FP32 vectors
+    const bool energy_tc = a.mat.energy != GD_ENERGY_NEO_HOOKE && c.L.we > 0;
+    const bool yield_tc_on = c.L.wy > 0 && a.kappa_fixed == nullptr;    // frozen history: no local solve
+    T.fwd_bytes = energy_tc ? c.L.off_w2r - c.L.off_w2f : 0;
+    T.rev_bytes = c.L.off_v2f - c.L.off_w2r;
+    T.v2_bytes = c.L.off_e32 - c.L.off_v2f;
+    T.vec_bytes = c.L.bytes - c.L.off_e32;
+    T.slot_mode = energy_tc ? (yield_tc_on ? 3 : 1) : (yield_tc_on ? 2 : 0);
+    T.slot_bytes = T.slot_mode == 3 ? (T.rev_bytes > T.v2_bytes ? T.rev_bytes : T.v2_bytes)
+                   : T.slot_mode == 1 ? T.rev_bytes
+                   : T.slot_mode == 2 ? T.v2_bytes
+                                      : 0;
+    T.s_slot = T.fwd_bytes;
+    T.s_e32 = T.s_slot + T.slot_bytes;
+    T.s_y32 = T.s_e32 + (c.L.off_y32 - c.L.off_e32);
+    // shared memory: weights | two operand tiles (also the row-mode vectors) | per-warp scratch | barriers
+    size_t off = ((size_t)(T.s_e32 + T.vec_bytes) + 1023) / 1024 * 1024;
     T.tiles_off = (int)off;
     T.tile_bytes = 128 * (wpmax > 0 ? wpmax : 16) * 2;
     const size_t vec_bytes = (size_t)4 * G_::EPR * G_::NQ * G_::NEN * V_REC * sizeof(float);
@@ -779,9 +841,26 @@ cudaError_t launch_tc_t(const AsmArgs &a, const TcLaunch &c, cudaStream_t s)
     auto fn = asm_tc_kernel<DIM, SPLIT>;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // all of the unified L1/shared storage as shared memory: two CTAs of ~108 KB
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    // resident CTAs per SM from the shared memory (with the per-block reservation), the
+    // registers and the tensor memory; the occupancy query is taken as a lower bound (it
+    // has answered 1 where two CTAs fit).  The grid-stride loop is correct for any grid.
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTcThreads, smem);
     if (e != cudaSuccess) return e;
+    {
+        cudaFuncAttributes fa{};
+        int reserved = 0;
+        e = cudaFuncGetAttributes(&fa, fn);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        if (e != cudaSuccess) return e;
+        const int regs_cta = ((fa.numRegs * 32 + 255) / 256 * 256) * (kTcThreads / 32);
+        int fit = (int)((size_t)smem_sm / (smem + (size_t)fa.sharedSizeBytes + (size_t)reserved));
+        if (regs_cta > 0 && 65536 / regs_cta < fit) fit = 65536 / regs_cta;
+        if (fit > per_sm) per_sm = fit;
+    }
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (per_sm > tmem_cap) per_sm = tmem_cap;
     const int64_t per_cta = 4 * G_::EPW;

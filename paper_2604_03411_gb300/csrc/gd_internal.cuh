@@ -118,6 +118,10 @@ struct TcArgs {
     float tol_r, tol_br;         // local-solve stopping tests (residual, bracket) relative to max(1, kappa)
     int ncols;                   // tensor-memory columns per CTA
     int tiles_off, tile_bytes, warp_off, warp_floats, bar_off;   // shared-memory layout
+    // weights in shared memory: W2 at 0 (fwd_bytes), one slot (slot_bytes) at s_slot for
+    // W2^T or V2, the FP32 vectors at s_e32 / s_y32 (vec_bytes from the blob's off_e32)
+    int fwd_bytes, rev_bytes, v2_bytes, s_slot, slot_bytes, s_e32, s_y32, vec_bytes;
+    int slot_mode;               // 0: none, 1: W2^T resident, 2: V2 resident, 3: W2^T then V2 per batch
 };
 struct TcLaunch {
     TcLayout L;
