@@ -55,6 +55,12 @@ D_STOP = 0.995                      # damage at which a load path ends (Sec. 5.2
 # MEASURED_PEAKS.json.
 FP64_PEAK_TFLOPS = 1.19
 FP32_PEAK_TFLOPS = 72.8
+# DRAM traffic of the 3D FP32-vector Krylov kernel with 8 lanes per node (the launch the
+# bench's autotune picks), dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture
+# of 40-iteration launches on the 48^3 cube (profiles/krylov_fp32_cube48_traffic.txt):
+# 629 MB per iteration against 545 MB of algorithmic bytes.  The traffic of other sizes is
+# scaled by the algorithmic bytes, which the capture and the full-size launch share.
+KRYLOV_G8_TRAFFIC_PER_ALG = 25.153e9 / 40 / 545192728
 
 
 def parse():
@@ -236,7 +242,7 @@ def run_reference(args):
 ICNN = {"auto": 0, "cuda": 1, "bf16": 2, "bf16x3": 3}
 
 
-def krylov_roofline(reps, nnz, n_dofs, n_nodes, ndof, kry_ms, peaks, fp32_inner):
+def krylov_roofline(reps, nnz, n_dofs, n_nodes, ndof, kry_ms, peaks, fp32_inner, lanes=0):
     """Algorithmic bytes and FLOPs of the persistent Krylov launches (one per Newton
     system).  One BiCGStab iteration (three-barrier form): two products with the
     values, the column list once per node block, the row pointers, the gathered x
@@ -257,8 +263,13 @@ def krylov_roofline(reps, nnz, n_dofs, n_nodes, ndof, kry_ms, peaks, fp32_inner)
               "algorithmic_bytes_per_launch": iter_b * ipl, "algorithmic_flops_per_launch": iter_f * ipl,
               "bytes_per_iteration": iter_b}
     if fp32_inner or iter_b > 129e6:
+        traffic = None
+        if fp32_inner and ndof == 4 and lanes == 8:
+            traffic = KRYLOV_G8_TRAFFIC_PER_ALG * iter_b * ipl
+            common["traffic_source"] = ("ncu dram bytes of the 8-lane FP32 kernel on the 48^3 cube, "
+                                        "scaled by algorithmic bytes")
         return dict(common, bound="hbm", achieved=hbm, peak=peaks["hbm_gbs"], unit="GB/s",
-                    frac=hbm / peaks["hbm_gbs"], traffic=None, peak_source=f"{peaks['kind']} copy bandwidth",
+                    frac=hbm / peaks["hbm_gbs"], traffic=traffic, peak_source=f"{peaks['kind']} copy bandwidth",
                     alu_view={"achieved_tflops": alu, "fp64_peak": FP64_PEAK_TFLOPS})
     return dict(common, bound="alu", achieved=alu, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
                 frac=alu / FP64_PEAK_TFLOPS, traffic=None, peak_source="measured FP64 FMA rate",
@@ -440,7 +451,8 @@ def run_gd(args):
         asm_ms = sum(r.assembly_ms for r in reps)
         kry_ms = sum(r.krylov_ms for r in reps)
         fp32_inner = sum(r.krylov_fp32_iterations for r in reps) * 2 > krylov
-        kroof = krylov_roofline(reps, nnz, n_nodes_all * ndof, n_nodes_all, ndof, kry_ms, peaks, fp32_inner)
+        lanes = (tuning or {}).get("krylov_lanes_per_node", 0) if precision == args.precision else 0
+        kroof = krylov_roofline(reps, nnz, n_nodes_all * ndof, n_nodes_all, ndof, kry_ms, peaks, fp32_inner, lanes)
         eroof = element_roofline(reps, probs, n_elems_all, precision == "fp64", icnn, peaks)
         dominant = kroof if kry_ms >= asm_ms else eroof
         return {"newton_step_ms": total_ms / max(newton, 1), "newton_iterations": newton,
