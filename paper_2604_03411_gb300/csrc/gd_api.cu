@@ -2134,12 +2134,12 @@ gd_status gd_autotune(gd_handle *h, gd_tune_report *rep)
     H.krylov_grid = gd::krylov_blocks(H.ndof, H.opt.precision == GD_MIXED, H.num_sms, kpick);
     if (H.krylov_grid < 1) H.krylov_grid = keep_grid;
     r.krylov_ctas_per_sm = kpick;
-    // node groups per product round at the chosen grid (the two-level kernel has one)
+    // node groups per product round at the chosen grid (the two-level kernel: 1 or 2)
     const int ups[3] = {1, 2, 4};
     double ubest = 1e300;
     int upick = H.krylov_up;
     for (double &v : r.krylov_us_up) v = -1.0;
-    for (int ui = 0; ui < 3 && st == GD_OK && H.coarse.nc == 0; ++ui) {
+    for (int ui = 0; ui < (H.coarse.nc > 0 ? 2 : 3) && st == GD_OK; ++ui) {
         H.krylov_up = ups[ui];
         double tmin = 1e300;
         for (int rep_i = 0; rep_i < 2; ++rep_i) {

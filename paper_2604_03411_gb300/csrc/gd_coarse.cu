@@ -267,6 +267,95 @@ __global__ void __launch_bounds__(256) coarse_assemble_kernel(int64_t n_nodes, c
     }
 }
 
+// Ac = P^T A P, one warp per node row block, through shared memory (rows of at most
+// kCaMaxLen columns): the lanes first form, for every column j of the node's rows, the
+// aggregate a_j of its node, g_j[m] = sum_d P_i[d][m] A[(i,d), j] and the column's
+// basis values P_j[m2]; lane 0 numbers the distinct aggregates of the row (a few: the
+// aggregates are compact); then every lane sums g_j[m] P_j[m2] over the columns of
+// each aggregate for its (m, m2) pairs (49 pairs in 3D: two per lane) and adds each
+// sum into Ac once.  FP32 products and sums inside a row, FP64 accumulation across
+// rows: the coarse matrix is inverted in FP32 and only preconditions.
+constexpr int kCaMaxLen = 256;
+constexpr int kCaWarps = 8;
+
+template <int NDOF, int NM>
+size_t coarse_asm_smem(int lmax)
+{
+    return (size_t)kCaWarps * ((size_t)lmax * (3 * sizeof(int32_t) + 2 * NM * sizeof(float)));
+}
+
+template <int NDOF, int NM, class V>
+__global__ void __launch_bounds__(32 * kCaWarps) coarse_assemble_smem_kernel(int64_t n_nodes, const int32_t *rowptr,
+                                                                           const int32_t *colidx, const V *vals,
+                                                                           const int32_t *agg, const int32_t *coff,
+                                                                           const float *P, int nc, int lmax,
+                                                                           double *Ac)
+{
+    extern __shared__ __align__(16) unsigned char ca_smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned char *wbase = ca_smem + (size_t)wib * ((size_t)lmax * (3 * sizeof(int32_t) + 2 * NM * sizeof(float)));
+    float *gs = reinterpret_cast<float *>(wbase);                 // [lmax][NM]
+    float *ps = gs + (size_t)lmax * NM;                           // [lmax][NM]
+    int32_t *aj_s = reinterpret_cast<int32_t *>(ps + (size_t)lmax * NM);   // [lmax] aggregate of column j
+    int32_t *slot = aj_s + lmax;                                  // [lmax] its index among the distinct ones
+    int32_t *dist = slot + lmax;                                  // [lmax] distinct aggregates
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr int NP = NM * NM;
+    for (int64_t i = gw; i < n_nodes; i += nw) {
+        const int32_t base = rowptr[i * NDOF], len = rowptr[i * NDOF + 1] - base;
+        const int32_t ai = agg[i], oi = coff[ai], ni = coff[ai + 1] - oi;
+        float pi[NDOF][NM];
+#pragma unroll
+        for (int d = 0; d < NDOF; ++d)
+#pragma unroll
+            for (int m = 0; m < NM; ++m) pi[d][m] = P[(i * NDOF + d) * NM + m];
+        for (int32_t j = lane; j < len; j += 32) {
+            const int32_t col = colidx[base + j];
+            const int32_t jn = col / NDOF, e = col - jn * NDOF;
+            float g[NM];
+#pragma unroll
+            for (int m = 0; m < NM; ++m) g[m] = 0.0f;
+#pragma unroll
+            for (int d = 0; d < NDOF; ++d) {
+                const float a = (float)vals[base + d * len + j];
+#pragma unroll
+                for (int m = 0; m < NM; ++m) g[m] += pi[d][m] * a;
+            }
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                gs[j * NM + m] = g[m];
+                ps[j * NM + m] = P[((int64_t)jn * NDOF + e) * NM + m];
+            }
+            aj_s[j] = agg[jn];
+        }
+        __syncwarp();
+        int nd = 0;
+        if (lane == 0) {
+            for (int32_t j = 0; j < len; ++j) {
+                const int32_t a = aj_s[j];
+                int k = 0;
+                while (k < nd && dist[k] != a) ++k;
+                if (k == nd) dist[nd++] = a;
+                slot[j] = k;
+            }
+        }
+        nd = __shfl_sync(0xffffffffu, nd, 0);
+        __syncwarp();
+        for (int k = 0; k < nd; ++k) {
+            const int32_t a2 = dist[k], o2 = coff[a2], n2 = coff[a2 + 1] - o2;
+            for (int pr = lane; pr < NP; pr += 32) {
+                const int m = pr / NM, m2 = pr - m * NM;
+                float acc = 0.0f;
+                for (int32_t j = 0; j < len; ++j)
+                    if (slot[j] == k) acc += gs[j * NM + m] * ps[j * NM + m2];
+                if (m < ni && m2 < n2 && acc != 0.0f) atomicAdd(&Ac[(int64_t)(oi + m) * nc + o2 + m2], (double)acc);
+            }
+        }
+        __syncwarp();       // the next row rewrites the warp's records
+    }
+}
+
 constexpr int kGjRows = 16;      // rows per panel
 constexpr int kGjThreads = 512;  // threads per CTA; C columns per thread (nc <= C kGjThreads)
 
@@ -394,9 +483,33 @@ __global__ void __launch_bounds__(kGjThreads) coarse_invert_kernel(const double 
 
 }  // namespace
 
+template <int NDOF, int NM>
+cudaError_t launch_coarse_asm_smem(const CoarseSpace &cs, int64_t n_nodes, const int32_t *rowptr,
+                                   const int32_t *colidx, const void *vals, bool fp32_vals, int lmax, int num_sms,
+                                   cudaStream_t s)
+{
+    const size_t smem = coarse_asm_smem<NDOF, NM>(lmax);
+    const void *fn = fp32_vals ? (const void *)coarse_assemble_smem_kernel<NDOF, NM, float>
+                               : (const void *)coarse_assemble_smem_kernel<NDOF, NM, double>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * kCaWarps, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = num_sms * per_sm;
+    if (fp32_vals)
+        coarse_assemble_smem_kernel<NDOF, NM, float><<<grid, 32 * kCaWarps, smem, s>>>(
+            n_nodes, rowptr, colidx, (const float *)vals, cs.agg, cs.coff, cs.P, cs.nc, lmax, cs.Ac);
+    else
+        coarse_assemble_smem_kernel<NDOF, NM, double><<<grid, 32 * kCaWarps, smem, s>>>(
+            n_nodes, rowptr, colidx, (const double *)vals, cs.agg, cs.coff, cs.P, cs.nc, lmax, cs.Ac);
+    return cudaGetLastError();
+}
+
 cudaError_t coarse_setup(const CoarseSpace &cs, int ndof, int64_t n_nodes, const int32_t *rowptr,
                          const int32_t *colidx, const void *vals, bool fp32_vals, bool want_x64, int num_sms,
-                         cudaStream_t s)
+                         cudaStream_t s, int lmax)
 {
     const int nc = cs.nc;
     cudaError_t e = cudaMemsetAsync(cs.Ac, 0, sizeof(double) * (size_t)nc * nc, s);
@@ -404,7 +517,11 @@ cudaError_t coarse_setup(const CoarseSpace &cs, int ndof, int64_t n_nodes, const
     e = cudaMemsetAsync(cs.status, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     const int grid = num_sms * 8;
-    if (ndof == 3) {
+    if (lmax > 0 && lmax <= kCaMaxLen) {
+        e = ndof == 3 ? launch_coarse_asm_smem<3, 4>(cs, n_nodes, rowptr, colidx, vals, fp32_vals, lmax, num_sms, s)
+                      : launch_coarse_asm_smem<4, 7>(cs, n_nodes, rowptr, colidx, vals, fp32_vals, lmax, num_sms, s);
+        if (e != cudaSuccess) return e;
+    } else if (ndof == 3) {
         if (fp32_vals)
             coarse_assemble_kernel<3, 4, float><<<grid, 256, 0, s>>>(n_nodes, rowptr, colidx, (const float *)vals,
                                                                      cs.agg, cs.coff, cs.P, nc, cs.Ac);

@@ -387,9 +387,10 @@ int32_t coarse_aggregate(int64_t n_nodes, int ndof, const std::vector<int32_t> &
 void coarse_basis(int dim, int64_t n_nodes, const double *coords, const uint8_t *fixed,
                   const std::vector<int32_t> &agg, int32_t n_agg, std::vector<float> &P, std::vector<int32_t> &coff);
 // Ac = P^T A P for the tangent values vals, X32 = Ac^-1 (and X64 when want_x64)
+// lmax: the longest row (columns); rows up to 256 columns take the shared-memory kernel
 cudaError_t coarse_setup(const CoarseSpace &cs, int ndof, int64_t n_nodes, const int32_t *rowptr,
                          const int32_t *colidx, const void *vals, bool fp32_vals, bool want_x64, int num_sms,
-                         cudaStream_t s);
+                         cudaStream_t s, int lmax = 0);
 
 // persistent cooperative Krylov solve (gd_krylov.cu)
 struct KrylovCtx {

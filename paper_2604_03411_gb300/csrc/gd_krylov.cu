@@ -1324,7 +1324,7 @@ cudaError_t solve_t(const KrylovCtx &c, const V *vals, const double *b, double *
         const CoarseSpace &cs = *c.coarse;
         if (c.coarse_refresh) {
             e = coarse_setup(cs, NDOF, c.n_nodes, c.rowptr, c.colidx, vals, std::is_same<V, float>::value, true,
-                             c.num_sms, c.stream);
+                             c.num_sms, c.stream, c.lmax);
             if (e != cudaSuccess) return e;
         }
         e = cudaMemsetAsync(cs.rc, 0, sizeof(T) * 2 * (size_t)cs.nc, c.stream);
@@ -1343,8 +1343,9 @@ cudaError_t solve_t(const KrylovCtx &c, const V *vals, const double *b, double *
     if (e != cudaSuccess) return e;
     void *args[] = {&A};
     const int up = c.up ? c.up : 1;
-    // the two-level variant interleaves one node group per lane
-    const void *fn = co        ? (const void *)bicgstab3_kernel<NDOF, G, 1, V, T, true>
+    // the two-level variant takes one or two node groups per lane and product round
+    const void *fn = co        ? (up == 2 ? (const void *)bicgstab3_kernel<NDOF, G, 2, V, T, true>
+                                          : (const void *)bicgstab3_kernel<NDOF, G, 1, V, T, true>)
                      : up == 1 ? (const void *)bicgstab3_kernel<NDOF, G, 1, V, T>
                      : up == 4 ? (const void *)bicgstab3_kernel<NDOF, G, 4, V, T>
                                : (const void *)bicgstab3_kernel<NDOF, G, 2, V, T>;
@@ -1455,7 +1456,7 @@ int coop_per_sm()
     constexpr int G = NDOF == 3 ? 8 : 32;
     constexpr int G2 = (NDOF == 4 && std::is_same<T, float>::value) ? 8 : G;   // the other lane counts
     constexpr int G3 = (NDOF == 4 && std::is_same<T, float>::value) ? 4 : G;   // of the 3D FP32 solve
-    const void *fns[13] = {(const void *)bicgstab3_kernel<NDOF, G, 1, V, T>, (const void *)bicgstab3_kernel<NDOF, G, 2, V, T>,
+    const void *fns[16] = {(const void *)bicgstab3_kernel<NDOF, G, 1, V, T>, (const void *)bicgstab3_kernel<NDOF, G, 2, V, T>,
                           (const void *)bicgstab3_kernel<NDOF, G, 4, V, T>,
                           (const void *)bicgstab3_kernel<NDOF, G, 1, V, T, true>,
                           (const void *)bicgstab3_batch_kernel<NDOF, G, 1, V, T>,
@@ -1465,7 +1466,10 @@ int coop_per_sm()
                           (const void *)bicgstab3_kernel<NDOF, G2, 4, V, T>,
                           (const void *)bicgstab3_kernel<NDOF, G2, 1, V, T, true>,
                           (const void *)bicgstab3_kernel<NDOF, G3, 1, V, T>,
-                          (const void *)bicgstab3_kernel<NDOF, G3, 1, V, T, true>};
+                          (const void *)bicgstab3_kernel<NDOF, G3, 1, V, T, true>,
+                          (const void *)bicgstab3_kernel<NDOF, G, 2, V, T, true>,
+                          (const void *)bicgstab3_kernel<NDOF, G2, 2, V, T, true>,
+                          (const void *)bicgstab3_kernel<NDOF, G3, 2, V, T, true>};
     int best = 1 << 30;
     for (const void *f : fns) {
         int per_sm = 0;
