@@ -379,8 +379,7 @@ gd_status gd_coarse_basis(const gd_mesh *mesh, int32_t target_nodes, int32_t *ag
  * GD_NOALLOC_MAX_DOFS dofs (about 13.7 MB), held by every GPU that loads the
  * library until the process exits; larger systems are rejected with GD_ERR_ARG.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Every call
- * on a device shares the one array and rewrites all of it that it reads, so
+ * device current).  Every call on a device shares the one array and rewrites all of it that it reads, so
  * calls that overlap on the GPU (other streams, other host threads) race: run
  * them one after another.  Errors: GD_ERR_ARG, GD_ERR_CUDA, GD_ERR_KRYLOV; the
  * message is available from gd_last_error(NULL) on the calling thread. */
