@@ -55,12 +55,11 @@ D_STOP = 0.995                      # damage at which a load path ends (Sec. 5.2
 # MEASURED_PEAKS.json.
 FP64_PEAK_TFLOPS = 1.19
 FP32_PEAK_TFLOPS = 72.8
-# DRAM traffic of the 3D FP32-vector Krylov kernel with 8 lanes per node (the launch the
-# bench's autotune picks), dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture
-# of 40-iteration launches on the 48^3 cube (profiles/krylov_fp32_cube48_traffic.txt):
-# 629 MB per iteration against 545 MB of algorithmic bytes.  The traffic of other sizes is
-# scaled by the algorithmic bytes, which the capture and the full-size launch share.
-KRYLOV_G8_TRAFFIC_PER_ALG = 25.153e9 / 40 / 545192728
+# DRAM traffic of the 3D FP32-vector Krylov kernel with 8 lanes per node, from an ncu capture
+# of 40-iteration launches on the 48^3 cube (profiles/krylov_fp32_cube48_traffic.txt): 629 MB
+# per iteration against 545 MB of algorithmic bytes.  The capture predates the kernel's
+# four-CTA build, so it is not reported as this kernel's traffic (None) until retaken.
+KRYLOV_G8_TRAFFIC_PER_ALG = None
 
 
 def parse():
@@ -264,7 +263,7 @@ def krylov_roofline(reps, nnz, n_dofs, n_nodes, ndof, kry_ms, peaks, fp32_inner,
               "bytes_per_iteration": iter_b}
     if fp32_inner or iter_b > 129e6:
         traffic = None
-        if fp32_inner and ndof == 4 and lanes == 8:
+        if KRYLOV_G8_TRAFFIC_PER_ALG and fp32_inner and ndof == 4 and lanes == 8:
             traffic = KRYLOV_G8_TRAFFIC_PER_ALG * iter_b * ipl
             common["traffic_source"] = ("ncu dram bytes of the 8-lane FP32 kernel on the 48^3 cube, "
                                         "scaled by algorithmic bytes")

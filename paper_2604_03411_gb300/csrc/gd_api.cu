@@ -346,7 +346,8 @@ gd_status krylov(gd::Handle &H, const void *vals, const double *b, double *x, in
     kc.red = H.red;
     kc.out = H.scal + 24;
     kc.stream = H.stream;
-    kc.blocks = H.krylov_grid;
+    // the FP32-vector kernels run on a grid of their own (built for more CTAs per SM)
+    kc.blocks = (inner_fp32 && H.krylov_grid32 > 0) ? H.krylov_grid32 : H.krylov_grid;
     kc.num_sms = H.num_sms;
     kc.up = H.krylov_up;
     kc.lmax = H.krylov_lmax;
@@ -1835,6 +1836,7 @@ static gd_status create_impl(int32_t n_spec, const gd_mesh *meshes, const gd_icn
     GD_CREATE_CUDA(dalloc(&H.vals_f32, (size_t)nnz));
     GD_CREATE_CUDA(dalloc(&H.kx, (size_t)n_dofs));
     H.krylov_grid = gd::krylov_blocks(ndof, o.precision == GD_MIXED, H.num_sms);
+    H.krylov_grid32 = gd::krylov_blocks_fp32(ndof, H.num_sms, H.krylov_cpsm32);
     if (H.krylov_grid < 1) {
         H.err = "no cooperative grid fits on this device";
         return bail(GD_ERR_CUDA);
@@ -2108,12 +2110,17 @@ gd_status gd_autotune(gd_handle *h, gd_tune_report *rep)
     // right-hand side: ones on the free dofs (the committed residual may be zero)
     GD_CUDA(&H, gd::launch_fill(H.kv[9], 1.0, H.n_dofs, H.stream));
     ++H.launches;
+    const int keep_grid32 = H.krylov_grid32;
+    int kpick32 = H.krylov_cpsm32;
     for (int cap = 1; cap <= 4; ++cap) {
-        const int grid = gd::krylov_blocks(H.ndof, H.opt.precision == GD_MIXED, H.num_sms, cap);
+        // the solve timed here runs with FP32 vectors in GD_MIXED: tune that grid
+        const int grid = fp32 ? gd::krylov_blocks_fp32(H.ndof, H.num_sms, cap)
+                              : gd::krylov_blocks(H.ndof, H.opt.precision == GD_MIXED, H.num_sms, cap);
         if (grid != cap * H.num_sms) continue;       // not co-resident at this width
         if ((size_t)grid > (size_t)4 * H.num_sms) continue;
-        H.krylov_grid = grid;
         if (grid > H.red_blocks) continue;           // beyond the reduction buffers
+        if (fp32) H.krylov_grid32 = grid;
+        else H.krylov_grid = grid;
         double tmin = 1e300;
         for (int rep_i = 0; rep_i < 2; ++rep_i) {
             int kit = 0;
@@ -2127,13 +2134,22 @@ gd_status gd_autotune(gd_handle *h, gd_tune_report *rep)
         r.krylov_us[cap - 1] = tmin;
         if (tmin < kbest) {
             kbest = tmin;
-            kpick = cap;
+            if (fp32) kpick32 = cap;
+            else kpick = cap;
         }
     }
-    H.krylov_cpsm = kpick;
-    H.krylov_grid = gd::krylov_blocks(H.ndof, H.opt.precision == GD_MIXED, H.num_sms, kpick);
-    if (H.krylov_grid < 1) H.krylov_grid = keep_grid;
-    r.krylov_ctas_per_sm = kpick;
+    if (fp32) {
+        H.krylov_cpsm32 = kpick32;
+        H.krylov_grid32 = gd::krylov_blocks_fp32(H.ndof, H.num_sms, kpick32);
+        if (H.krylov_grid32 < 1) H.krylov_grid32 = keep_grid32;
+        H.krylov_grid = keep_grid;
+        r.krylov_ctas_per_sm = kpick32;
+    } else {
+        H.krylov_cpsm = kpick;
+        H.krylov_grid = gd::krylov_blocks(H.ndof, H.opt.precision == GD_MIXED, H.num_sms, kpick);
+        if (H.krylov_grid < 1) H.krylov_grid = keep_grid;
+        r.krylov_ctas_per_sm = kpick;
+    }
     // node groups per product round at the chosen grid (the two-level kernel: 1 or 2)
     const int ups[3] = {1, 2, 4};
     double ubest = 1e300;

@@ -251,12 +251,14 @@ struct Handle {
     float *vals_f32 = nullptr;                           // FP32 tangent copy for the inner solve (FP64 mode)
     double *kx = nullptr;                                // FP32 iterate storage
     int krylov_grid = 0;
+    int krylov_grid32 = 0;                               // single-system solves with FP32 vectors
     double *red = nullptr;                               // device reduction buffers
     double *scal = nullptr;                              // device scalars
     int red_blocks = 0;
     // launch shapes (gd_autotune)
     AsmTune asm_tune;
     int krylov_cpsm = 2;
+    int krylov_cpsm32 = 4;
     // GD_MIXED: measured FP32 residual noise per unit force scale, and load steps until
     // it is measured again
     std::vector<double> noise_ratio;
@@ -417,6 +419,8 @@ cudaError_t krylov_solve_batch(const KrylovCtx &c, const BatchKrylov &L, const v
                                const double *b, double *x, int max_it, bool fp32_vectors);
 // cooperative grid of the Krylov kernels: SMs x co-resident CTAs per SM (at most cap)
 int krylov_blocks(int ndof, bool fp32_vals, int num_sms, int cap = 2);
+// the same for the single-system kernels with FP32 vectors (built for four CTAs per SM)
+int krylov_blocks_fp32(int ndof, int num_sms, int cap = 4);
 // Solves K x = b on the free dofs; the result and statistics land in x and c.out.
 // fp32_vectors: the iteration runs on FP32 values and vectors (dot products stay FP64).
 cudaError_t krylov_solve(const KrylovCtx &c, const void *vals, bool fp32_vals, const double *b, double *x,

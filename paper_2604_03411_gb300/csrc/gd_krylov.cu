@@ -362,8 +362,10 @@ __device__ __forceinline__ T node_apply(const T *binv, int64_t nd_wide, bool nod
     return fixed ? T(0) : out;
 }
 
+// FP32 vectors: built for four CTAs per SM (64 registers; the two-level variants spill
+// up to 80 bytes), FP64 vectors for two
 template <int NDOF, int G, int UP, class V, class T, bool CO = false>
-__global__ void __launch_bounds__(kThreads, 2) bicgstab3_kernel(KArgs<V, T> A)
+__global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 4 : 2) bicgstab3_kernel(KArgs<V, T> A)
 {
     using M = RowMap<NDOF, G, T>;
     constexpr int LPN = M::LPN, NPW = M::NPW;
@@ -1486,6 +1488,40 @@ __global__ void narrow_kernel(const double *in, float *out, int64_t n)
 }
 
 }  // namespace
+
+template <int NDOF>
+int coop_per_sm_fp32()
+{
+    constexpr int G = NDOF == 3 ? 8 : 32;
+    constexpr int G2 = NDOF == 4 ? 8 : G, G3 = NDOF == 4 ? 4 : G;
+    const void *fns[] = {
+        (const void *)bicgstab3_kernel<NDOF, G, 1, float, float>, (const void *)bicgstab3_kernel<NDOF, G, 2, float, float>,
+        (const void *)bicgstab3_kernel<NDOF, G, 4, float, float>,
+        (const void *)bicgstab3_kernel<NDOF, G, 1, float, float, true>,
+        (const void *)bicgstab3_kernel<NDOF, G, 2, float, float, true>,
+        (const void *)bicgstab3_kernel<NDOF, G2, 1, float, float>, (const void *)bicgstab3_kernel<NDOF, G2, 2, float, float>,
+        (const void *)bicgstab3_kernel<NDOF, G2, 4, float, float>,
+        (const void *)bicgstab3_kernel<NDOF, G2, 1, float, float, true>,
+        (const void *)bicgstab3_kernel<NDOF, G2, 2, float, float, true>,
+        (const void *)bicgstab3_kernel<NDOF, G3, 1, float, float>, (const void *)bicgstab3_kernel<NDOF, G3, 2, float, float>,
+        (const void *)bicgstab3_kernel<NDOF, G3, 4, float, float>,
+        (const void *)bicgstab3_kernel<NDOF, G3, 1, float, float, true>,
+        (const void *)bicgstab3_kernel<NDOF, G3, 2, float, float, true>};
+    int best = 1 << 30;
+    for (const void *f : fns) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kThreads, 0) != cudaSuccess) return 0;
+        if (per_sm < best) best = per_sm;
+    }
+    return best;
+}
+
+int krylov_blocks_fp32(int ndof, int num_sms, int cap)
+{
+    int per_sm = ndof == 3 ? coop_per_sm_fp32<3>() : coop_per_sm_fp32<4>();
+    if (cap > 0 && per_sm > cap) per_sm = cap;
+    return per_sm * num_sms;
+}
 
 int krylov_blocks(int ndof, bool fp32_vals, int num_sms, int cap)
 {
