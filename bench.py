@@ -213,14 +213,26 @@ def cpu_baseline(prob, seconds, seed=7, threads=0, single=True):
     return out
 
 
+def run_config(args, desc, batch, world):
+    """The workload's configuration as both arms report it (no measured quantities)."""
+    precision = args.precision or ("mixed" if (batch or args.workload == "cube") else "fp64")
+    icnn = args.icnn if args.icnn != "auto" else ("cuda" if batch else "bf16x3")
+    return dict(desc, precision=precision, icnn_mma=icnn if precision == "mixed" else None,
+                parallelism=f"specimen-shards{world}" if batch else f"replicas{world}",
+                inner_solve=args.inner, l2="flushed between timed steps (512 MB write)",
+                path_end=f"restart from the undeformed state when the path runs out or max damage >= {D_STOP}")
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return 0
     prob, desc = make_workload(args.workload, cube_n=args.cube_n)
-    if isinstance(prob, list):
+    batch = isinstance(prob, list)
+    config = run_config(args, desc, batch, world)
+    if batch:
         prob = max(prob, key=lambda p: p.mesh.n_elems)
-        desc = dict(desc, oracle_sample="largest specimen")
     vals = []
     per_step = max(1.0, 120.0 / max(1, args.steps + args.warmup))
     for k in range(args.warmup + args.steps):
@@ -230,9 +242,9 @@ def run_reference(args):
     v = sum(c["value"] for c in vals) / len(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": desc,
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[-1]["cores"], "kind": "oracle",
-                             "sample": vals[-1]["sample"]},
+                             "sample": vals[-1]["sample"] + (" (the largest specimen)" if batch else "")},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -510,11 +522,8 @@ def run_gd(args):
         "dtype": "f64" if args.precision == "fp64" else ("bf16x3+f32+f64" if icnn == "bf16x3" else
                                                          "bf16+f32+f64" if icnn == "bf16" else "f32+f64"),
         "data": "synthetic (seeded mesh, seeded ICNN weights)",
-        "config": dict(desc, precision=args.precision, icnn_mma=icnn if args.precision == "mixed" else None,
-                       parallelism=f"specimen-shards{world}" if batch else f"replicas{world}",
-                       inner_solve=args.inner, coarse_unknowns=coarse_n, coarse_aggregates=coarse_aggs,
-                       l2="flushed between timed steps (512 MB write)",
-                       path_end=f"restart from the undeformed state when the path runs out or max damage >= {D_STOP}"),
+        "config": run_config(args, desc, batch, world),
+        "coarse": {"unknowns": coarse_n, "aggregates": coarse_aggs},
     }
     line.update({k: v for k, v in main.items() if k != "gpu_launches"})
     line["e2e"] = e2e
